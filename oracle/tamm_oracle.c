@@ -1,0 +1,524 @@
+/*
+ * FP64 CPU oracle for block-sparse tensor contractions (TAMM, arXiv:2201.01257).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the test suite, the smoke check and the
+ * benchmark's CPU-baseline leg may load this file's library.  It shares no
+ * code with the GPU library: index spaces, tiling, the nonzero-block rule and
+ * the contraction loops are written here from the paper's definitions, in the
+ * plainest form that can be checked by eye.
+ *
+ *   - Index spaces and tilings (Sec. III.A, Fig. "tensor_const"): a space is a
+ *     range of orbitals made of contiguous groups; a tiled space cuts every
+ *     group into tiles of a fixed size (last tile of a group takes the
+ *     remainder) or into an explicit list of sizes covering every group.
+ *   - Block sparsity (Sec. III.A, spin attributes; Sec. III.B, sparsity-aware
+ *     allocation): a block, i.e. a tuple of tiles one per mode, is stored only
+ *     when the sum of the spins of the upper modes equals that of the lower
+ *     modes, and, for the irrep rule, when the product (XOR in D2h) of the tile
+ *     irreps is the totally symmetric irrep 0.  Stored blocks are laid out one
+ *     after another in lexicographic tile order, each row-major over the
+ *     tensor's modes in declared order.
+ *   - Operations (Sec. III.A, grammar figure "tensor_ops"):
+ *       C(lc) = beta*C + alpha * A(la) * B(lb)   (MultOp, Einstein summation
+ *                                                over labels in A and B only)
+ *       C(lc) = beta*C + alpha * A(la)           (AddOp with label permutation)
+ *       E     = alpha * sum A(la) * B(lb)        (full contraction to a scalar)
+ *       ||T||  Frobenius norm over stored entries (utility norm)
+ *     beta is 0 for "=" and 1 for "+=" ("-=" is a negative alpha).
+ *
+ * Summation order is fixed: contracted tile tuples in lexicographic order
+ * (first contracted label slowest), then contracted elements in row-major
+ * order, so every result is deterministic.  OpenMP runs over output blocks.
+ */
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#include <math.h>
+
+#define OR_MAX_MODES 8
+#define OR_MAX_LABELS 16
+
+enum { OR_OK = 0, OR_EINVAL = -1, OR_ENOMEM = -2 };
+enum { OR_SYM_DENSE = 0, OR_SYM_SPIN = 1, OR_SYM_SPIN_IRREP = 2 };
+
+typedef struct {
+  int n_tiles;
+  int64_t n;
+  int64_t* off;
+  int64_t* size;
+  int* spin;
+  int* irrep;
+} ospace;
+
+typedef struct {
+  int nm, n_upper, sym;
+  const ospace* sp[OR_MAX_MODES];
+  int64_t n_blocks;
+  int64_t* tiles;  /* n_blocks * nm tile indices */
+  int64_t* off;    /* n_blocks element offsets */
+  int64_t* lookup; /* dense tile-tuple index -> block index or -1 */
+  int64_t n_tuples;
+  int64_t n_elems;
+} otensor;
+
+/* ------------------------------------------------------------------ spaces */
+
+ospace* oracle_space_create(int n_groups, const int64_t* gsize, const int* gspin, const int* girrep,
+                            int64_t fixed_tile, int n_tiles_in, const int64_t* tile_sizes) {
+  if (n_groups <= 0) return NULL;
+  int cap = 0;
+  if (fixed_tile > 0) {
+    for (int g = 0; g < n_groups; ++g) {
+      if (gsize[g] < 0) return NULL;
+      cap += (int)((gsize[g] + fixed_tile - 1) / fixed_tile);
+    }
+  } else {
+    if (n_tiles_in <= 0 || !tile_sizes) return NULL;
+    cap = n_tiles_in;
+  }
+  ospace* s = (ospace*)calloc(1, sizeof(ospace));
+  s->off = (int64_t*)calloc(cap > 0 ? cap : 1, sizeof(int64_t));
+  s->size = (int64_t*)calloc(cap > 0 ? cap : 1, sizeof(int64_t));
+  s->spin = (int*)calloc(cap > 0 ? cap : 1, sizeof(int));
+  s->irrep = (int*)calloc(cap > 0 ? cap : 1, sizeof(int));
+  int t = 0;
+  int64_t pos = 0;
+  for (int g = 0; g < n_groups; ++g) {
+    int64_t left = gsize[g];
+    while (left > 0) {
+      int64_t ts;
+      if (fixed_tile > 0) {
+        ts = left < fixed_tile ? left : fixed_tile;
+      } else {
+        if (t >= n_tiles_in || tile_sizes[t] <= 0 || tile_sizes[t] > left) goto bad; /* straddles a group */
+        ts = tile_sizes[t];
+      }
+      s->off[t] = pos;
+      s->size[t] = ts;
+      s->spin[t] = gspin[g];
+      s->irrep[t] = girrep ? girrep[g] : 0;
+      pos += ts;
+      left -= ts;
+      ++t;
+    }
+  }
+  if (fixed_tile <= 0 && t != n_tiles_in) goto bad;
+  s->n_tiles = t;
+  s->n = pos;
+  return s;
+bad:
+  free(s->off);
+  free(s->size);
+  free(s->spin);
+  free(s->irrep);
+  free(s);
+  return NULL;
+}
+
+void oracle_space_destroy(ospace* s) {
+  if (!s) return;
+  free(s->off);
+  free(s->size);
+  free(s->spin);
+  free(s->irrep);
+  free(s);
+}
+
+int oracle_space_ntiles(const ospace* s) { return s->n_tiles; }
+int64_t oracle_space_size(const ospace* s) { return s->n; }
+
+void oracle_space_tile(const ospace* s, int t, int64_t* off, int64_t* size, int* spin, int* irrep) {
+  *off = s->off[t];
+  *size = s->size[t];
+  *spin = s->spin[t];
+  *irrep = s->irrep[t];
+}
+
+/* ----------------------------------------------------------------- tensors */
+
+static int block_allowed(const otensor* T, const int64_t* tt) {
+  if (T->sym == OR_SYM_DENSE) return 1;
+  int up = 0, lo = 0, x = 0;
+  for (int m = 0; m < T->nm; ++m) {
+    int sp = T->sp[m]->spin[tt[m]];
+    if (m < T->n_upper) up += sp; else lo += sp;
+    x ^= T->sp[m]->irrep[tt[m]];
+  }
+  if (up != lo) return 0;
+  if (T->sym == OR_SYM_SPIN_IRREP && x != 0) return 0;
+  return 1;
+}
+
+otensor* oracle_tensor_create(int nm, const ospace* const* sp, int n_upper, int sym) {
+  if (nm <= 0 || nm > OR_MAX_MODES || n_upper < 0 || n_upper > nm) return NULL;
+  if (sym < OR_SYM_DENSE || sym > OR_SYM_SPIN_IRREP) return NULL;
+  otensor* T = (otensor*)calloc(1, sizeof(otensor));
+  T->nm = nm;
+  T->n_upper = n_upper;
+  T->sym = sym;
+  int64_t nt = 1;
+  for (int m = 0; m < nm; ++m) {
+    T->sp[m] = sp[m];
+    nt *= sp[m]->n_tiles;
+  }
+  T->n_tuples = nt;
+  T->lookup = (int64_t*)malloc(sizeof(int64_t) * (size_t)nt);
+  int64_t nb = 0;
+  int64_t tt[OR_MAX_MODES];
+  for (int64_t lin = 0; lin < nt; ++lin) {
+    int64_t r = lin;
+    for (int m = nm - 1; m >= 0; --m) {
+      tt[m] = r % sp[m]->n_tiles;
+      r /= sp[m]->n_tiles;
+    }
+    T->lookup[lin] = block_allowed(T, tt) ? nb++ : -1;
+  }
+  T->n_blocks = nb;
+  T->tiles = (int64_t*)malloc(sizeof(int64_t) * (size_t)(nb * nm + 1));
+  T->off = (int64_t*)malloc(sizeof(int64_t) * (size_t)(nb + 1));
+  int64_t pos = 0;
+  for (int64_t lin = 0; lin < nt; ++lin) {
+    int64_t b = T->lookup[lin];
+    if (b < 0) continue;
+    int64_t r = lin, sz = 1;
+    for (int m = nm - 1; m >= 0; --m) {
+      tt[m] = r % sp[m]->n_tiles;
+      r /= sp[m]->n_tiles;
+    }
+    for (int m = 0; m < nm; ++m) {
+      T->tiles[b * nm + m] = tt[m];
+      sz *= sp[m]->size[tt[m]];
+    }
+    T->off[b] = pos;
+    pos += sz;
+  }
+  T->off[nb] = pos;
+  T->n_elems = pos;
+  return T;
+}
+
+void oracle_tensor_destroy(otensor* T) {
+  if (!T) return;
+  free(T->lookup);
+  free(T->tiles);
+  free(T->off);
+  free(T);
+}
+
+int64_t oracle_tensor_nblocks(const otensor* T) { return T->n_blocks; }
+int64_t oracle_tensor_nelems(const otensor* T) { return T->n_elems; }
+
+void oracle_tensor_blocks(const otensor* T, int64_t* tiles, int64_t* off) {
+  memcpy(tiles, T->tiles, sizeof(int64_t) * (size_t)(T->n_blocks * T->nm));
+  memcpy(off, T->off, sizeof(int64_t) * (size_t)T->n_blocks);
+}
+
+/* Block index for a tile tuple, or -1 when the block is not stored. */
+static int64_t find_block(const otensor* T, const int64_t* tt) {
+  int64_t lin = 0;
+  for (int m = 0; m < T->nm; ++m) lin = lin * T->sp[m]->n_tiles + tt[m];
+  return T->lookup[lin];
+}
+
+int64_t oracle_tensor_find_block(const otensor* T, const int64_t* tt) { return find_block(T, tt); }
+
+/* ------------------------------------------------------------------ labels */
+
+typedef struct {
+  int n;                      /* distinct labels */
+  char name[OR_MAX_LABELS];
+  const ospace* sp[OR_MAX_LABELS];
+  int posC[OR_MAX_LABELS], posA[OR_MAX_LABELS], posB[OR_MAX_LABELS]; /* mode position or -1 */
+} labelset;
+
+static int label_id(labelset* L, char c) {
+  for (int i = 0; i < L->n; ++i)
+    if (L->name[i] == c) return i;
+  if (L->n >= OR_MAX_LABELS) return -1;
+  L->name[L->n] = c;
+  L->sp[L->n] = NULL;
+  L->posC[L->n] = L->posA[L->n] = L->posB[L->n] = -1;
+  return L->n++;
+}
+
+/* Register the labels of one tensor; `which` selects the position array. */
+static int add_labels(labelset* L, const otensor* T, const char* l, int which) {
+  if (!T || !l || (int)strlen(l) != T->nm) return OR_EINVAL;
+  for (int m = 0; m < T->nm; ++m) {
+    int id = label_id(L, l[m]);
+    if (id < 0) return OR_EINVAL;
+    int* pos = which == 0 ? L->posC : (which == 1 ? L->posA : L->posB);
+    if (pos[id] >= 0) return OR_EINVAL; /* a label twice in one tensor */
+    pos[id] = m;
+    if (L->sp[id] && L->sp[id] != T->sp[m]) return OR_EINVAL; /* label bound to two spaces */
+    L->sp[id] = T->sp[m];
+  }
+  return OR_OK;
+}
+
+/* ---------------------------------------------------------------- contract */
+
+static void strides_of(const otensor* T, const int64_t* tt, int64_t* st) {
+  int64_t s = 1;
+  for (int m = T->nm - 1; m >= 0; --m) {
+    st[m] = s;
+    s *= T->sp[m]->size[tt[m]];
+  }
+}
+
+typedef struct {
+  labelset L;
+  int nk;               /* contracted labels, in order of appearance in A */
+  int k_ids[OR_MAX_LABELS];
+} cplan;
+
+static int contract_plan(cplan* P, const otensor* C, const char* lc, const otensor* A, const char* la,
+                         const otensor* B, const char* lb) {
+  memset(P, 0, sizeof(*P));
+  if (add_labels(&P->L, C, lc, 0) || add_labels(&P->L, A, la, 1) || add_labels(&P->L, B, lb, 2))
+    return OR_EINVAL;
+  for (int i = 0; i < P->L.n; ++i) {
+    int c = P->L.posC[i] >= 0, a = P->L.posA[i] >= 0, b = P->L.posB[i] >= 0;
+    if (c && (a == b)) return OR_EINVAL;   /* output label in both inputs or in none */
+    if (!c && !(a && b)) return OR_EINVAL; /* summed label must be in both inputs */
+  }
+  for (int m = 0; m < A->nm; ++m) {
+    int id = label_id(&P->L, la[m]);
+    if (P->L.posC[id] < 0) P->k_ids[P->nk++] = id;
+  }
+  return OR_OK;
+}
+
+/* Compute the box [lo, lo+ext) of stored C block `cb` into out (row-major over the box). */
+static int contract_box(const cplan* P, double alpha, const otensor* C, double beta, const otensor* A,
+                        const otensor* B, const double* a, const double* b, int64_t cb, const int64_t* lo,
+                        const int64_t* ext, const double* c_in, double* out) {
+  const labelset* L = &P->L;
+  int64_t tile[OR_MAX_LABELS];
+  const int64_t* ct = C->tiles + cb * C->nm;
+  int64_t box_n = 1;
+  for (int m = 0; m < C->nm; ++m) {
+    if (lo[m] < 0 || ext[m] < 0 || lo[m] + ext[m] > C->sp[m]->size[ct[m]]) return OR_EINVAL;
+    box_n *= ext[m];
+  }
+  int cid[OR_MAX_MODES]; /* label id of each C mode */
+  for (int i = 0; i < L->n; ++i) tile[i] = -1;
+  for (int i = 0; i < L->n; ++i)
+    if (L->posC[i] >= 0) {
+      tile[i] = ct[L->posC[i]];
+      cid[L->posC[i]] = i;
+    }
+
+  double* acc = (double*)calloc((size_t)(box_n > 0 ? box_n : 1), sizeof(double));
+  if (!acc) return OR_ENOMEM;
+
+  int64_t nkt = 1;
+  for (int k = 0; k < P->nk; ++k) nkt *= L->sp[P->k_ids[k]]->n_tiles;
+
+  for (int64_t kt = 0; kt < nkt; ++kt) {
+    int64_t r = kt;
+    for (int k = P->nk - 1; k >= 0; --k) {
+      int id = P->k_ids[k];
+      tile[id] = r % L->sp[id]->n_tiles;
+      r /= L->sp[id]->n_tiles;
+    }
+    int64_t at[OR_MAX_MODES], bt[OR_MAX_MODES];
+    for (int i = 0; i < L->n; ++i) {
+      if (L->posA[i] >= 0) at[L->posA[i]] = tile[i];
+      if (L->posB[i] >= 0) bt[L->posB[i]] = tile[i];
+    }
+    int64_t ab = find_block(A, at), bb = find_block(B, bt);
+    if (ab < 0 || bb < 0) continue;
+    int64_t sa[OR_MAX_MODES], sb[OR_MAX_MODES];
+    strides_of(A, at, sa);
+    strides_of(B, bt, sb);
+    /* per-label strides into A and B, and contracted extents */
+    int64_t strA[OR_MAX_LABELS], strB[OR_MAX_LABELS];
+    for (int i = 0; i < L->n; ++i) {
+      strA[i] = L->posA[i] >= 0 ? sa[L->posA[i]] : 0;
+      strB[i] = L->posB[i] >= 0 ? sb[L->posB[i]] : 0;
+    }
+    int64_t kext[OR_MAX_LABELS];
+    int64_t kn = 1;
+    for (int k = 0; k < P->nk; ++k) {
+      kext[k] = L->sp[P->k_ids[k]]->size[tile[P->k_ids[k]]];
+      kn *= kext[k];
+    }
+    /* offsets of every contracted element (row-major over the contracted labels) in A and B */
+    int64_t* kofs = (int64_t*)malloc(sizeof(int64_t) * (size_t)(2 * kn + 2));
+    if (!kofs) {
+      free(acc);
+      return OR_ENOMEM;
+    }
+    for (int64_t k = 0; k < kn; ++k) {
+      int64_t rk = k, ka = 0, kb = 0;
+      for (int q = P->nk - 1; q >= 0; --q) {
+        int64_t x = rk % kext[q];
+        rk /= kext[q];
+        ka += x * strA[P->k_ids[q]];
+        kb += x * strB[P->k_ids[q]];
+      }
+      kofs[2 * k] = ka;
+      kofs[2 * k + 1] = kb;
+    }
+    const double* ablk = a + A->off[ab];
+    const double* bblk = b + B->off[bb];
+    int64_t cidx[OR_MAX_MODES];
+    for (int64_t e = 0; e < box_n; ++e) {
+      int64_t rr = e;
+      for (int m = C->nm - 1; m >= 0; --m) {
+        cidx[m] = lo[m] + rr % ext[m];
+        rr /= ext[m];
+      }
+      int64_t abase = 0, bbase = 0;
+      for (int m = 0; m < C->nm; ++m) {
+        abase += cidx[m] * strA[cid[m]];
+        bbase += cidx[m] * strB[cid[m]];
+      }
+      double s = acc[e];
+      for (int64_t k = 0; k < kn; ++k) s += ablk[abase + kofs[2 * k]] * bblk[bbase + kofs[2 * k + 1]];
+      acc[e] = s;
+    }
+    free(kofs);
+  }
+  for (int64_t e = 0; e < box_n; ++e) {
+    double prev = (beta != 0.0 && c_in) ? beta * c_in[e] : 0.0;
+    out[e] = prev + alpha * acc[e];
+  }
+  free(acc);
+  return OR_OK;
+}
+
+/* Full contraction over every stored block of C (in place on c). */
+int oracle_contract(double alpha, const otensor* C, const char* lc, double beta, const otensor* A,
+                    const char* la, const otensor* B, const char* lb, double* c, const double* a,
+                    const double* b) {
+  cplan P;
+  if (contract_plan(&P, C, lc, A, la, B, lb)) return OR_EINVAL;
+  int err = OR_OK;
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int64_t cb = 0; cb < C->n_blocks; ++cb) {
+    int64_t lo[OR_MAX_MODES], ext[OR_MAX_MODES];
+    const int64_t* ct = C->tiles + cb * C->nm;
+    for (int m = 0; m < C->nm; ++m) {
+      lo[m] = 0;
+      ext[m] = C->sp[m]->size[ct[m]];
+    }
+    double* cblk = c + C->off[cb];
+    int e = contract_box(&P, alpha, C, beta, A, B, a, b, cb, lo, ext, cblk, cblk);
+    if (e) {
+#pragma omp atomic write
+      err = e;
+    }
+  }
+  return err;
+}
+
+/* One box of one C block; c_box_in holds the box's current C values (ignored when beta == 0). */
+int oracle_contract_box(double alpha, const otensor* C, const char* lc, double beta, const otensor* A,
+                        const char* la, const otensor* B, const char* lb, const double* a, const double* b,
+                        int64_t cb, const int64_t* lo, const int64_t* ext, const double* c_box_in,
+                        double* out) {
+  cplan P;
+  if (contract_plan(&P, C, lc, A, la, B, lb)) return OR_EINVAL;
+  if (cb < 0 || cb >= C->n_blocks) return OR_EINVAL;
+  return contract_box(&P, alpha, C, beta, A, B, a, b, cb, lo, ext, c_box_in, out);
+}
+
+/* --------------------------------------------------------------------- add */
+
+int oracle_add(double alpha, const otensor* C, const char* lc, double beta, const otensor* A, const char* la,
+               double* c, const double* a) {
+  labelset L;
+  memset(&L, 0, sizeof(L));
+  if (add_labels(&L, C, lc, 0) || add_labels(&L, A, la, 1)) return OR_EINVAL;
+  for (int i = 0; i < L.n; ++i)
+    if ((L.posC[i] >= 0) != (L.posA[i] >= 0)) return OR_EINVAL;
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int64_t cb = 0; cb < C->n_blocks; ++cb) {
+    const int64_t* ct = C->tiles + cb * C->nm;
+    int64_t at[OR_MAX_MODES], sa[OR_MAX_MODES], perm[OR_MAX_MODES];
+    for (int m = 0; m < C->nm; ++m) {
+      int id = -1;
+      for (int i = 0; i < L.n; ++i)
+        if (L.posC[i] == m) id = i;
+      perm[m] = L.posA[id]; /* A mode holding C mode m's label */
+      at[L.posA[id]] = ct[m];
+    }
+    int64_t ab = find_block(A, at);
+    double* cblk = c + C->off[cb];
+    int64_t n = C->off[cb + 1] - C->off[cb];
+    if (ab < 0) {
+      for (int64_t e = 0; e < n; ++e) cblk[e] = beta != 0.0 ? beta * cblk[e] : 0.0;
+      continue;
+    }
+    strides_of(A, at, sa);
+    const double* ablk = a + A->off[ab];
+    for (int64_t e = 0; e < n; ++e) {
+      int64_t r = e, ai = 0;
+      for (int m = C->nm - 1; m >= 0; --m) {
+        int64_t x = r % C->sp[m]->size[ct[m]];
+        r /= C->sp[m]->size[ct[m]];
+        ai += x * sa[perm[m]];
+      }
+      double prev = beta != 0.0 ? beta * cblk[e] : 0.0;
+      cblk[e] = prev + alpha * ablk[ai];
+    }
+  }
+  return OR_OK;
+}
+
+/* ------------------------------------------------------------------ energy */
+
+int oracle_energy(double alpha, const otensor* A, const char* la, const otensor* B, const char* lb,
+                  const double* a, const double* b, double* result) {
+  labelset L;
+  memset(&L, 0, sizeof(L));
+  if (add_labels(&L, A, la, 1) || add_labels(&L, B, lb, 2)) return OR_EINVAL;
+  for (int i = 0; i < L.n; ++i)
+    if ((L.posA[i] >= 0) != (L.posB[i] >= 0)) return OR_EINVAL;
+  double* part = (double*)calloc((size_t)(A->n_blocks + 1), sizeof(double));
+  if (!part) return OR_ENOMEM;
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int64_t ab = 0; ab < A->n_blocks; ++ab) {
+    const int64_t* at = A->tiles + ab * A->nm;
+    int64_t bt[OR_MAX_MODES], sb[OR_MAX_MODES], perm[OR_MAX_MODES];
+    for (int m = 0; m < A->nm; ++m) {
+      int id = -1;
+      for (int i = 0; i < L.n; ++i)
+        if (L.posA[i] == m) id = i;
+      perm[m] = L.posB[id];
+      bt[L.posB[id]] = at[m];
+    }
+    int64_t bb = find_block(B, bt);
+    if (bb < 0) continue;
+    strides_of(B, bt, sb);
+    const double* ablk = a + A->off[ab];
+    const double* bblk = b + B->off[bb];
+    int64_t n = A->off[ab + 1] - A->off[ab];
+    double s = 0.0;
+    for (int64_t e = 0; e < n; ++e) {
+      int64_t r = e, bi = 0;
+      for (int m = A->nm - 1; m >= 0; --m) {
+        int64_t x = r % A->sp[m]->size[at[m]];
+        r /= A->sp[m]->size[at[m]];
+        bi += x * sb[perm[m]];
+      }
+      s += ablk[e] * bblk[bi];
+    }
+    part[ab] = s;
+  }
+  double s = 0.0;
+  for (int64_t ab = 0; ab < A->n_blocks; ++ab) s += part[ab];
+  free(part);
+  *result = alpha * s;
+  return OR_OK;
+}
+
+/* -------------------------------------------------------------------- norm */
+
+double oracle_norm(const otensor* T, const double* x) {
+  double s = 0.0;
+  for (int64_t e = 0; e < T->n_elems; ++e) s += x[e] * x[e];
+  return sqrt(s);
+}
