@@ -1,0 +1,208 @@
+/*
+ * tamm_gb300.h -- C ABI of a single-GPU (GB300, sm_103a) library for
+ * contractions of tiled, spin/irrep block-sparse tensors, following TAMM
+ * (Tensor Algebra for Many-body Methods, arXiv:2201.01257).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *  - Plain C types only.  "device" pointers are CUDA device addresses of the
+ *    context's device; "host" pointers are ordinary host memory.
+ *  - Every call returns a tamm_status.  No C++ exception crosses this ABI.  On
+ *    failure the context keeps a message for tamm_last_error().
+ *  - Asynchrony: every operation is enqueued on the context's CUDA stream and
+ *    returns at once, except the calls that hand a host result back
+ *    (tamm_energy, tamm_norm, tamm_sync), which synchronise the stream first.
+ *  - Device-side failures (a bounded wait that ran out, a bounds check in the
+ *    checked build) are recorded in a device status word and reported by the
+ *    next synchronising call as TAMM_ETIMEOUT / TAMM_ECHECK.  Kernels never
+ *    trap.
+ *  - Tensors store only their nonzero blocks (sparsity-aware allocation,
+ *    Sec. III.B): blocks in lexicographic tile order (mode 0 slowest), each
+ *    block row-major over the modes in declared order, packed one after
+ *    another in a single FP64 buffer.
+ *  - Labels are single characters, one per mode.  A label found in A and B but
+ *    not in C is summed (Einstein convention, Sec. IV.A); every label of C
+ *    must occur in exactly one of A, B; a label must name the same tamm_space
+ *    object everywhere it occurs.
+ *  - There is no CPU execution path.  A precision the device cannot run returns
+ *    TAMM_EUNSUPPORTED; nothing is silently downgraded.
+ */
+#ifndef TAMM_GB300_H
+#define TAMM_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define TAMM_API __attribute__((visibility("default")))
+#else
+#define TAMM_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int tamm_status;
+#define TAMM_OK 0
+#define TAMM_EINVAL 1       /* bad argument: labels, spaces, sizes, null pointers */
+#define TAMM_ENOMEM 2       /* the allocator returned NULL */
+#define TAMM_ECUDA 3        /* a CUDA runtime/driver call failed */
+#define TAMM_EUNSUPPORTED 4 /* valid request this build/device cannot run */
+#define TAMM_ETIMEOUT 5     /* a bounded device-side wait ran out */
+#define TAMM_ECHECK 6       /* a device-side bounds check failed (checked build) */
+
+/* Block-sparsity rule of a tensor (Sec. III.A: spin attributes on tiles and a
+ * user-definable non-zero check). */
+#define TAMM_SYM_DENSE 0      /* every block stored */
+#define TAMM_SYM_SPIN 1       /* sum of spins of the upper modes == that of the lower modes */
+#define TAMM_SYM_SPIN_IRREP 2 /* spin rule and XOR of tile irreps == 0 (D2h, totally symmetric) */
+
+/* Arithmetic of a contraction's block products. */
+#define TAMM_PREC_F64 0        /* FP64 throughout */
+#define TAMM_PREC_OZAKI_BF16 1 /* FP64 operands split into BF16 integer slices, tensor-core products with
+                                  exact FP32 accumulation per chunk, FP64 reconstruction */
+#define TAMM_PREC_OZAKI_I8 2   /* INT8 slices: sm_103a has no tcgen05 kind::i8, always TAMM_EUNSUPPORTED */
+
+typedef struct tamm_ctx tamm_ctx;
+typedef struct tamm_space tamm_space;
+typedef struct tamm_tensor tamm_tensor;
+
+/* Stream-ordered device allocator: return `bytes` of device memory usable by
+ * work enqueued on `stream` after this call, or NULL.  `release` may be
+ * called with memory still in use by work already enqueued on `stream`; the
+ * allocator must not hand it out to other streams before that work ends
+ * (cudaFreeAsync and PyTorch's caching allocator both behave this way). */
+typedef void* (*tamm_alloc_fn)(size_t bytes, void* stream, void* user);
+typedef void (*tamm_free_fn)(void* ptr, size_t bytes, void* stream, void* user);
+
+/* ---------------------------------------------------------------- context */
+
+/* Execution context (Sec. III.A/III.B "execution context": where and how
+ * operations run).  `device` is a CUDA ordinal; `stream` a cudaStream_t (NULL
+ * = the legacy default stream).  `alloc`/`release` may both be NULL, in which
+ * case cudaMallocAsync/cudaFreeAsync on the stream are used for scratch.  The
+ * context owns its scratch and plan caches; the caller owns the stream.
+ * `device` = -1 makes a host-only context: spaces, tensors' block tables and
+ * tamm_contract_flops work, every call that needs the device returns
+ * TAMM_ECUDA.  Errors: TAMM_EINVAL (null out), TAMM_ECUDA (bad device). */
+TAMM_API tamm_status tamm_ctx_create(int device, void* stream, tamm_alloc_fn alloc, tamm_free_fn release, void* user,
+                            tamm_ctx** out);
+/* Change the stream later calls enqueue on (scratch stays stream-ordered by
+ * synchronising the old stream first). */
+TAMM_API tamm_status tamm_ctx_set_stream(tamm_ctx* ctx, void* stream);
+/* Waits for the stream, frees scratch and plans.  NULL is ignored. */
+TAMM_API void tamm_ctx_destroy(tamm_ctx* ctx);
+/* Message of the last failed call on this context ("" if none); owned by ctx. */
+TAMM_API const char* tamm_last_error(const tamm_ctx* ctx);
+/* Synchronise the stream and report any device-side status (TAMM_ETIMEOUT,
+ * TAMM_ECHECK) recorded since the last synchronising call, then clear it. */
+TAMM_API tamm_status tamm_sync(tamm_ctx* ctx);
+
+/* ----------------------------------------------------------- index spaces */
+
+/* Tiled index space (Sec. III.A, Fig. "tensor_const": IndexSpace with named
+ * sub-ranges, TiledIndexSpace with fixed or explicit tile sizes; spin sub-spaces
+ * as in Sec. IV.A eq. "tamm_cc-Spin").  The space is `n_groups` contiguous
+ * groups of orbitals; group g has `group_size[g]` orbitals, spin
+ * `group_spin[g]` (+1 alpha, -1 beta) and irrep `group_irrep[g]` in 0..7 (NULL
+ * = all 0).  Tiling: if `fixed_tile` > 0 each group is cut into tiles of that
+ * size, the last tile of a group taking the remainder; otherwise the
+ * `n_tiles` sizes in `tile_sizes` are laid over the groups in order and must
+ * cover each group exactly (a tile never straddles a group).
+ * Errors: TAMM_EINVAL on any inconsistency. */
+TAMM_API tamm_status tamm_space_create(tamm_ctx* ctx, int n_groups, const int64_t* group_size, const int* group_spin,
+                              const int* group_irrep, int n_tiles, const int64_t* tile_sizes, int64_t fixed_tile,
+                              tamm_space** out);
+/* Number of tiles and of orbitals. */
+TAMM_API tamm_status tamm_space_info(const tamm_space* s, int* n_tiles, int64_t* n);
+/* Copy per-tile offset, size, spin and irrep into host arrays of n_tiles entries (any may be NULL). */
+TAMM_API tamm_status tamm_space_tiles(const tamm_space* s, int64_t* offset, int64_t* size, int* spin, int* irrep);
+/* Spaces must outlive every tensor built on them.  NULL is ignored. */
+TAMM_API void tamm_space_destroy(tamm_space* s);
+
+/* ---------------------------------------------------------------- tensors */
+
+/* Block-sparse FP64 tensor (Sec. III.A "Tensor<T>{tIS...}"; Sec. III.B
+ * sparsity-aware allocation).  `n_modes` (1..8) spaces; the first `n_upper`
+ * modes are "upper" for the spin rule; `symmetry` is a TAMM_SYM_* rule.  Only
+ * metadata is built here; device storage is attached by tamm_tensor_bind or
+ * tamm_tensor_allocate.  Errors: TAMM_EINVAL. */
+TAMM_API tamm_status tamm_tensor_create(tamm_ctx* ctx, int n_modes, tamm_space* const* modes, int n_upper, int symmetry,
+                               tamm_tensor** out);
+/* Tensor over the same spaces as `like` with its modes reordered: mode m of the
+ * new tensor is mode perm[m] of `like` (perm a permutation of 0..n_modes-1),
+ * and it stores exactly the images of like's stored blocks.  This is the layout
+ * of a transposed copy (Sec. III.A tensor transpose), e.g. a product kept in
+ * GEMM order.  Errors: TAMM_EINVAL. */
+TAMM_API tamm_status tamm_tensor_create_permuted(tamm_ctx* ctx, const tamm_tensor* like, const int* perm,
+                                                 tamm_tensor** out);
+/* Number of stored blocks and of stored FP64 elements. */
+TAMM_API tamm_status tamm_tensor_info(const tamm_tensor* t, int64_t* n_blocks, int64_t* n_elems);
+/* Host copies of the block table: `block_tiles` (n_blocks * n_modes tile
+ * indices) and `block_offsets` (n_blocks element offsets); either may be NULL. */
+TAMM_API tamm_status tamm_tensor_blocks(const tamm_tensor* t, int64_t* block_tiles, int64_t* block_offsets);
+/* Attach caller-owned device memory of n_elems doubles (8-byte aligned; 256-byte
+ * alignment recommended).  The caller keeps ownership and must keep it alive
+ * while work using the tensor is in flight. */
+TAMM_API tamm_status tamm_tensor_bind(tamm_tensor* t, double* device_data);
+/* Allocate n_elems doubles through the context allocator (freed by destroy). */
+TAMM_API tamm_status tamm_tensor_allocate(tamm_tensor* t);
+/* Device pointer of the tensor's packed data (NULL if unbound). */
+TAMM_API double* tamm_tensor_data(const tamm_tensor* t);
+/* NULL is ignored.  Storage obtained by tamm_tensor_allocate is released
+ * stream-ordered on the context's stream. */
+TAMM_API void tamm_tensor_destroy(tamm_tensor* t);
+
+/* ------------------------------------------------------------- operations */
+
+/* MultOp (Sec. III.A, grammar figure "tensor_ops", the rule alpha * A * B):
+ *     C(lc) = beta * C(lc) + alpha * sum_{summed labels} A(la) * B(lb)
+ * over the stored blocks of C.  beta must be 0 ("=") or 1 ("+="); "-=" is a
+ * negative alpha.  Each nonzero block pair becomes an operand index
+ * permutation where the block layout needs it, a dense block GEMM and an
+ * accumulation into the output block.  `precision` is a TAMM_PREC_*; for
+ * TAMM_PREC_OZAKI_BF16, `slices` is the number of BF16 slices per operand
+ * (3..8; 0 = automatic, 6).  C must not alias A or B.
+ * Errors: TAMM_EINVAL (labels/spaces/beta), TAMM_EUNSUPPORTED (precision),
+ * TAMM_ENOMEM, TAMM_ECUDA. */
+TAMM_API tamm_status tamm_contract(tamm_ctx* ctx, double alpha, tamm_tensor* C, const char* lc, double beta,
+                          const tamm_tensor* A, const char* la, const tamm_tensor* B, const char* lb, int precision,
+                          int slices);
+
+/* Nonzero-block flop count 2*M*N*K summed over the block pairs of the same
+ * contraction (host only, no device work). */
+TAMM_API tamm_status tamm_contract_flops(tamm_ctx* ctx, const tamm_tensor* C, const char* lc, const tamm_tensor* A,
+                                const char* la, const tamm_tensor* B, const char* lb, double* flops);
+
+/* AddOp with label permutation (Sec. III.A, grammar rule alpha * A):
+ *     C(lc) = beta * C(lc) + sum_t alpha[t] * A(la[t])
+ * for `n_terms` (1..4) label orders of the same tensor A (each a permutation of
+ * lc), in one pass over C.  With n_terms = 4, lc = "abij" and
+ * la = {"abij","baij","abji","baji"}, alpha = {1,-1,-1,1} it applies the
+ * antisymmetriser P(ab)P(ij).  beta must be 0 or 1.  C must not alias A.
+ * Errors: TAMM_EINVAL. */
+TAMM_API tamm_status tamm_add(tamm_ctx* ctx, tamm_tensor* C, const char* lc, double beta, const tamm_tensor* A,
+                     int n_terms, const char* const* la, const double* alpha);
+
+/* Full contraction to a scalar (Sec. III.A: inner products / reductions):
+ *     result = alpha * sum over all entries A(la) * B(lb)
+ * with lb a permutation of la.  FP64, deterministic summation order.
+ * `result_host` receives the value after the stream is synchronised.
+ * Errors: TAMM_EINVAL, TAMM_ECUDA, TAMM_ETIMEOUT/TAMM_ECHECK (pending device status). */
+TAMM_API tamm_status tamm_energy(tamm_ctx* ctx, double alpha, const tamm_tensor* A, const char* la, const tamm_tensor* B,
+                        const char* lb, double* result_host);
+/* Same, asynchronous: writes the value to `result_device` (one double of device memory). */
+TAMM_API tamm_status tamm_energy_async(tamm_ctx* ctx, double alpha, const tamm_tensor* A, const char* la,
+                              const tamm_tensor* B, const char* lb, double* result_device);
+
+/* Frobenius norm over the stored entries (Sec. III.A utility routines: norm).
+ * FP64, deterministic.  Synchronises. */
+TAMM_API tamm_status tamm_norm(tamm_ctx* ctx, const tamm_tensor* t, double* result_host);
+TAMM_API tamm_status tamm_norm_async(tamm_ctx* ctx, const tamm_tensor* t, double* result_device);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TAMM_GB300_H */

@@ -1,0 +1,226 @@
+// FP64 kernels: permuted add (AddOp), block-sparse FP64 GEMM (MultOp, plain
+// precision), and deterministic reductions (energy, norm).
+//
+// GB300 has a small FP64 pipe, so the FP64 GEMM is arithmetic-bound at any
+// reasonable tile; it is a register-tiled DFMA kernel (64x64 CTA tile, 4x4 per
+// thread, K step 16) over a device task list grouped by output block.  Each CTA
+// owns one output tile and sums every block pair of its group in a fixed order,
+// so results are deterministic and need no atomics.
+#include "tamm_internal.h"
+
+namespace tamm {
+namespace {
+
+struct Alpha4 {
+  double v[kMaxAddTerms];
+};
+
+// dst = beta*dst + sum_t alpha_t * src(perm_t), one chunk of one block per CTA.
+__global__ void __launch_bounds__(256) add_kernel(double* __restrict__ dst, const double* __restrict__ src,
+                                                  const AddBlock* __restrict__ blocks,
+                                                  const ChunkItem* __restrict__ items, int n_terms, double beta,
+                                                  Alpha4 alpha) {
+  const ChunkItem it = items[blockIdx.x];
+  const AddBlock& B = blocks[it.block];
+  const int64_t end = min(B.n, it.start + (int64_t)kChunk);
+  const int nm = B.nm;
+  for (int64_t e = it.start + threadIdx.x; e < end; e += blockDim.x) {
+    int32_t idx[kMaxKernelModes];
+    int64_t r = e;
+    for (int m = nm - 1; m >= 0; --m) {
+      idx[m] = (int32_t)(r % B.dim[m]);
+      r /= B.dim[m];
+    }
+    double acc = 0.0;
+    for (int t = 0; t < n_terms; ++t) {
+      if (B.src_off[t] < 0) continue;
+      int64_t s = B.src_off[t];
+      for (int m = 0; m < nm; ++m) s += (int64_t)idx[m] * B.sstride[t][m];
+      acc = fma(alpha.v[t], src[s], acc);
+    }
+    double* d = dst + B.dst_off + e;
+    *d = beta != 0.0 ? fma(beta, *d, acc) : acc;
+  }
+}
+
+template <int NT>
+__device__ double block_sum(double v) {
+  __shared__ double red[NT / 32];
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x / 32, l = threadIdx.x % 32;
+  if (l == 0) red[w] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x < 32) {
+    s = threadIdx.x < NT / 32 ? red[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  }
+  return s;  // valid in thread 0
+}
+
+// partials[item] = sum over the chunk of a[x] * b[perm(x)]
+__global__ void __launch_bounds__(256) energy_partials_kernel(const double* __restrict__ a,
+                                                              const double* __restrict__ b,
+                                                              const AddBlock* __restrict__ blocks,
+                                                              const ChunkItem* __restrict__ items,
+                                                              double* __restrict__ partials) {
+  const ChunkItem it = items[blockIdx.x];
+  const AddBlock& B = blocks[it.block];
+  const int64_t end = min(B.n, it.start + (int64_t)kChunk);
+  const int nm = B.nm;
+  double acc = 0.0;
+  if (B.src_off[0] >= 0) {
+    for (int64_t e = it.start + threadIdx.x; e < end; e += blockDim.x) {
+      int64_t r = e, s = B.src_off[0];
+      for (int m = nm - 1; m >= 0; --m) {
+        s += (r % B.dim[m]) * (int64_t)B.sstride[0][m];
+        r /= B.dim[m];
+      }
+      acc = fma(a[B.dst_off + e], b[s], acc);
+    }
+  }
+  double s = block_sum<256>(acc);
+  if (threadIdx.x == 0) partials[blockIdx.x] = s;
+}
+
+__global__ void __launch_bounds__(256) sumsq_partials_kernel(const double* __restrict__ x, int64_t n,
+                                                             int64_t per, double* __restrict__ partials) {
+  const int64_t lo = (int64_t)blockIdx.x * per;
+  const int64_t hi = min(n, lo + per);
+  double acc = 0.0;
+  for (int64_t e = lo + threadIdx.x; e < hi; e += blockDim.x) acc = fma(x[e], x[e], acc);
+  double s = block_sum<256>(acc);
+  if (threadIdx.x == 0) partials[blockIdx.x] = s;
+}
+
+__global__ void __launch_bounds__(1024) reduce_final_kernel(const double* __restrict__ p, int64_t n, double alpha,
+                                                            int take_sqrt, double* __restrict__ out) {
+  double acc = 0.0;
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) acc += p[i];
+  double s = block_sum<1024>(acc);
+  if (threadIdx.x == 0) *out = take_sqrt ? sqrt(s) : alpha * s;
+}
+
+// ------------------------------------------------------------------ FP64 GEMM
+
+constexpr int BM = kGemmTileM, BN = kGemmTileN, BK = 16;
+
+__global__ void __launch_bounds__(256) gemm_f64_kernel(const double* __restrict__ A, const double* __restrict__ Bm,
+                                                       double* __restrict__ C, const GemmGroup* __restrict__ groups,
+                                                       const GemmTask* __restrict__ tasks,
+                                                       const GemmItem* __restrict__ items, double alpha,
+                                                       double beta) {
+  __shared__ double As[BK][BM + 1];
+  __shared__ double Bs[BK][BN];
+  const GemmItem it = items[blockIdx.x];
+  const GemmGroup g = groups[it.group];
+  const int tid = threadIdx.x;
+  const int tx = tid % 16, ty = tid / 16;
+  // loader coordinates: A tile 64 x 16 (4 consecutive k per thread), B tile 16 x 64 (4 consecutive n)
+  const int ar = tid / 4, ac = (tid % 4) * 4;
+  const int bk = tid / 16, bn = (tid % 16) * 4;
+  const int M = g.M, N = g.N;
+  double acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+
+  for (int t = g.task_begin; t < g.task_end; ++t) {
+    const GemmTask tk = tasks[t];
+    const int K = tk.K;
+    const double* a = A + tk.a_off;
+    const double* b = Bm + tk.b_off;
+    double ra[4], rb[4];
+    auto load = [&](int k0) {
+      const int row = it.m0 + ar;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int k = k0 + ac + q;
+        ra[q] = (row < M && k < K) ? __ldg(a + (int64_t)row * K + k) : 0.0;
+      }
+      const int kk = k0 + bk;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int col = it.n0 + bn + q;
+        rb[q] = (kk < K && col < N) ? __ldg(b + (int64_t)kk * N + col) : 0.0;
+      }
+    };
+    load(0);
+    for (int k0 = 0; k0 < K; k0 += BK) {
+      __syncthreads();
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        As[ac + q][ar] = ra[q];
+        Bs[bk][bn + q] = rb[q];
+      }
+      __syncthreads();
+      if (k0 + BK < K) load(k0 + BK);
+#pragma unroll
+      for (int k = 0; k < BK; ++k) {
+        double av[4], bv[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) av[i] = As[k][ty + 16 * i];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) bv[j] = Bs[k][tx + 16 * j];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) acc[i][j] = fma(av[i], bv[j], acc[i][j]);
+      }
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int row = it.m0 + ty + 16 * i;
+    if (row >= M) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int col = it.n0 + tx + 16 * j;
+      if (col >= N) continue;
+      double* c = C + g.c_off + (int64_t)row * N + col;
+      *c = beta != 0.0 ? fma(beta, *c, alpha * acc[i][j]) : alpha * acc[i][j];
+    }
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_add(tamm_ctx* ctx, double* dst, const double* src, const AddBlock* blocks,
+                       const ChunkItem* items, int64_t n_items, int n_terms, double beta, const double* alpha_host) {
+  if (n_items == 0) return cudaSuccess;
+  Alpha4 al{};
+  for (int t = 0; t < n_terms; ++t) al.v[t] = alpha_host[t];
+  add_kernel<<<(unsigned)n_items, 256, 0, ctx->stream>>>(dst, src, blocks, items, n_terms, beta, al);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_energy_partials(tamm_ctx* ctx, const double* a, const double* b, const AddBlock* blocks,
+                                   const ChunkItem* items, int64_t n_items, double* partials) {
+  if (n_items == 0) return cudaSuccess;
+  energy_partials_kernel<<<(unsigned)n_items, 256, 0, ctx->stream>>>(a, b, blocks, items, partials);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sumsq_partials(tamm_ctx* ctx, const double* x, int64_t n, double* partials, int64_t n_parts) {
+  if (n_parts == 0) return cudaSuccess;
+  const int64_t per = (n + n_parts - 1) / n_parts;
+  sumsq_partials_kernel<<<(unsigned)n_parts, 256, 0, ctx->stream>>>(x, n, per, partials);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_reduce_final(tamm_ctx* ctx, const double* partials, int64_t n, double alpha, int take_sqrt,
+                                double* out_device) {
+  reduce_final_kernel<<<1, 1024, 0, ctx->stream>>>(partials, n, alpha, take_sqrt, out_device);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gemm_f64(tamm_ctx* ctx, const double* a, const double* b, double* c, const GemmGroup* groups,
+                            const GemmTask* tasks, const GemmItem* items, int64_t n_items, double alpha,
+                            double beta) {
+  if (n_items == 0) return cudaSuccess;
+  gemm_f64_kernel<<<(unsigned)n_items, 256, 0, ctx->stream>>>(a, b, c, groups, tasks, items, alpha, beta);
+  return cudaGetLastError();
+}
+
+}  // namespace tamm

@@ -1,0 +1,501 @@
+// C ABI of the block-sparse contraction library: contexts, tiled index spaces,
+// block-sparse tensors, and the host planner that turns a labelled operation
+// into device task lists (Sec. III.A operations; Sec. III.B sparsity-aware
+// block storage).  All device work is enqueued on the context's stream.
+#include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <stdexcept>
+
+#include "tamm_internal.h"
+#include "tamm_plan.h"
+
+using namespace tamm;
+
+// ------------------------------------------------------------------ errors
+
+namespace tamm {
+
+Error::Error(tamm_status s, const char* fmt, ...) : status(s) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  msg = buf;
+}
+
+void cuda_check(cudaError_t e, const char* what) {
+  if (e != cudaSuccess) throw Error(TAMM_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+}  // namespace tamm
+
+template <class F>
+static tamm_status guarded(tamm_ctx* ctx, F&& f) {
+  try {
+    f();
+    if (ctx) ctx->last_error.clear();
+    return TAMM_OK;
+  } catch (const Error& e) {
+    if (ctx) ctx->last_error = e.msg;
+    return e.status;
+  } catch (const std::bad_alloc&) {
+    if (ctx) ctx->last_error = "host allocation failed";
+    return TAMM_ENOMEM;
+  } catch (const std::exception& e) {
+    if (ctx) ctx->last_error = e.what();
+    return TAMM_EINVAL;
+  }
+}
+
+// --------------------------------------------------------------- allocation
+
+namespace tamm {
+
+void require_device(tamm_ctx* ctx) {
+  if (ctx->host_only) throw Error(TAMM_ECUDA, "host-only context (device -1) cannot run device work");
+}
+
+void* ctx_alloc(tamm_ctx* ctx, size_t bytes) {
+  require_device(ctx);
+  if (bytes == 0) bytes = 256;
+  void* p = nullptr;
+  if (ctx->allocator.alloc) {
+    p = ctx->allocator.alloc(bytes, (void*)ctx->stream, ctx->allocator.user);
+  } else {
+    cudaError_t e = cudaMallocAsync(&p, bytes, ctx->stream);
+    if (e != cudaSuccess) {
+      (void)cudaGetLastError();
+      p = nullptr;
+    }
+  }
+  if (!p) throw Error(TAMM_ENOMEM, "device allocation of %zu bytes failed", bytes);
+  return p;
+}
+
+void ctx_free(tamm_ctx* ctx, void* p, size_t bytes) {
+  if (!p) return;
+  if (ctx->allocator.release) {
+    ctx->allocator.release(p, bytes, (void*)ctx->stream, ctx->allocator.user);
+  } else {
+    cudaFreeAsync(p, ctx->stream);
+  }
+}
+
+void* ctx_scratch(tamm_ctx* ctx, size_t bytes) {
+  bytes = (bytes + 255) & ~size_t(255);
+  if (ctx->scratch.bytes < bytes) {
+    const size_t grow = std::max(bytes, ctx->scratch.bytes + ctx->scratch.bytes / 4);
+    ctx_free(ctx, ctx->scratch.ptr, ctx->scratch.bytes);
+    ctx->scratch.ptr = nullptr;
+    ctx->scratch.bytes = 0;
+    ctx->scratch.ptr = ctx_alloc(ctx, grow);
+    ctx->scratch.bytes = grow;
+  }
+  return ctx->scratch.ptr;
+}
+
+double* ctx_reduce_buffer(tamm_ctx* ctx, size_t n) {
+  if (ctx->reduce_cap < n) {
+    ctx_free(ctx, ctx->d_reduce, ctx->reduce_cap * sizeof(double));
+    ctx->d_reduce = nullptr;
+    ctx->reduce_cap = 0;
+    ctx->d_reduce = (double*)ctx_alloc(ctx, n * sizeof(double));
+    ctx->reduce_cap = n;
+  }
+  return ctx->d_reduce;
+}
+
+Plan::~Plan() {
+  for (auto& b : bufs) ctx_free(ctx, b.ptr, b.bytes);
+}
+
+void* Plan::upload_bytes(const void* host, size_t bytes) {
+  void* d = ctx_alloc(ctx, bytes);
+  bufs.push_back({d, bytes});
+  if (bytes) cuda_check(cudaMemcpyAsync(d, host, bytes, cudaMemcpyHostToDevice, ctx->stream), "plan upload");
+  return d;
+}
+
+}  // namespace tamm
+
+// ---------------------------------------------------------------- context
+
+extern "C" tamm_status tamm_ctx_create(int device, void* stream, tamm_alloc_fn alloc, tamm_free_fn release,
+                                       void* user, tamm_ctx** out) {
+  if (!out) return TAMM_EINVAL;
+  *out = nullptr;
+  if ((alloc == nullptr) != (release == nullptr)) return TAMM_EINVAL;
+  tamm_ctx* ctx = new (std::nothrow) tamm_ctx();
+  if (!ctx) return TAMM_ENOMEM;
+  tamm_status st = guarded(ctx, [&] {
+    ctx->device = device;
+    if (device < 0) {  // host-only context: metadata, plans and flop counts, no device work
+      ctx->host_only = true;
+      return;
+    }
+    cuda_check(cudaSetDevice(device), "cudaSetDevice");
+    ctx->stream = (cudaStream_t)stream;
+    ctx->allocator = {alloc, release, user};
+    cuda_check(cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, device), "attribute");
+    ctx->d_status = (int*)ctx_alloc(ctx, 256);
+    cuda_check(cudaMemsetAsync(ctx->d_status, 0, sizeof(int), ctx->stream), "memset status");
+    cuda_check(cudaMallocHost(&ctx->h_result, 64), "cudaMallocHost");
+  });
+  if (st != TAMM_OK) {
+    tamm_ctx_destroy(ctx);
+    return st;
+  }
+  *out = ctx;
+  return TAMM_OK;
+}
+
+extern "C" tamm_status tamm_ctx_set_stream(tamm_ctx* ctx, void* stream) {
+  if (!ctx) return TAMM_EINVAL;
+  return guarded(ctx, [&] {
+    require_device(ctx);
+    cuda_check(cudaStreamSynchronize(ctx->stream), "stream sync");
+    ctx->stream = (cudaStream_t)stream;
+  });
+}
+
+extern "C" void tamm_ctx_destroy(tamm_ctx* ctx) {
+  if (!ctx) return;
+  if (ctx->host_only) {
+    delete ctx;
+    return;
+  }
+  cudaSetDevice(ctx->device);
+  ctx->plans.clear();
+  ctx_free(ctx, ctx->scratch.ptr, ctx->scratch.bytes);
+  ctx_free(ctx, ctx->d_reduce, ctx->reduce_cap * sizeof(double));
+  ctx_free(ctx, ctx->d_status, 256);
+  cudaStreamSynchronize(ctx->stream);
+  if (ctx->h_result) cudaFreeHost(ctx->h_result);
+  (void)cudaGetLastError();
+  delete ctx;
+}
+
+extern "C" const char* tamm_last_error(const tamm_ctx* ctx) { return ctx ? ctx->last_error.c_str() : ""; }
+
+namespace tamm {
+// Synchronise and turn a recorded device status into an error.
+void sync_and_check(tamm_ctx* ctx) {
+  cuda_check(cudaStreamSynchronize(ctx->stream), "stream synchronize");
+  int st = 0;
+  cuda_check(cudaMemcpy(&st, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost), "status read");
+  if (st != 0) {
+    cuda_check(cudaMemset(ctx->d_status, 0, sizeof(int)), "status clear");
+    if (st == TAMM_ETIMEOUT) throw Error(TAMM_ETIMEOUT, "a bounded device-side wait ran out");
+    throw Error(st, "device-side check failed (status %d)", st);
+  }
+}
+}  // namespace tamm
+
+extern "C" tamm_status tamm_sync(tamm_ctx* ctx) {
+  if (!ctx) return TAMM_EINVAL;
+  return guarded(ctx, [&] {
+    require_device(ctx);
+    sync_and_check(ctx);
+  });
+}
+
+// ----------------------------------------------------------------- spaces
+
+extern "C" tamm_status tamm_space_create(tamm_ctx* ctx, int n_groups, const int64_t* group_size,
+                                         const int* group_spin, const int* group_irrep, int n_tiles,
+                                         const int64_t* tile_sizes, int64_t fixed_tile, tamm_space** out) {
+  if (!ctx || !out) return TAMM_EINVAL;
+  *out = nullptr;
+  return guarded(ctx, [&] {
+    if (n_groups <= 0 || !group_size || !group_spin) throw Error(TAMM_EINVAL, "space: need at least one group");
+    if (fixed_tile <= 0 && (n_tiles <= 0 || !tile_sizes))
+      throw Error(TAMM_EINVAL, "space: give a fixed tile size or an explicit tile list");
+    std::unique_ptr<tamm_space> s(new tamm_space());
+    s->ctx = ctx;
+    s->id = ctx->next_id++;
+    int t = 0;
+    int64_t pos = 0;
+    for (int g = 0; g < n_groups; ++g) {
+      if (group_size[g] < 0) throw Error(TAMM_EINVAL, "space: negative group size");
+      if (group_spin[g] != 1 && group_spin[g] != -1) throw Error(TAMM_EINVAL, "space: spin must be +1 or -1");
+      const int irr = group_irrep ? group_irrep[g] : 0;
+      if (irr < 0 || irr > 7) throw Error(TAMM_EINVAL, "space: irrep must be in 0..7");
+      int64_t left = group_size[g];
+      while (left > 0) {
+        int64_t ts;
+        if (fixed_tile > 0) {
+          ts = std::min(left, fixed_tile);
+        } else {
+          if (t >= n_tiles) throw Error(TAMM_EINVAL, "space: tile list does not cover group %d", g);
+          ts = tile_sizes[t];
+          if (ts <= 0 || ts > left) throw Error(TAMM_EINVAL, "space: tile %d straddles group %d", t, g);
+        }
+        s->off.push_back(pos);
+        s->size.push_back(ts);
+        s->spin.push_back(group_spin[g]);
+        s->irrep.push_back(irr);
+        pos += ts;
+        left -= ts;
+        ++t;
+      }
+    }
+    if (fixed_tile <= 0 && t != n_tiles) throw Error(TAMM_EINVAL, "space: %d tile sizes given, %d used", n_tiles, t);
+    if (t == 0) throw Error(TAMM_EINVAL, "space: empty");
+    s->n_tiles = t;
+    s->n = pos;
+    *out = s.release();
+  });
+}
+
+extern "C" tamm_status tamm_space_info(const tamm_space* s, int* n_tiles, int64_t* n) {
+  if (!s) return TAMM_EINVAL;
+  if (n_tiles) *n_tiles = s->n_tiles;
+  if (n) *n = s->n;
+  return TAMM_OK;
+}
+
+extern "C" tamm_status tamm_space_tiles(const tamm_space* s, int64_t* offset, int64_t* size, int* spin,
+                                        int* irrep) {
+  if (!s) return TAMM_EINVAL;
+  for (int t = 0; t < s->n_tiles; ++t) {
+    if (offset) offset[t] = s->off[t];
+    if (size) size[t] = s->size[t];
+    if (spin) spin[t] = s->spin[t];
+    if (irrep) irrep[t] = s->irrep[t];
+  }
+  return TAMM_OK;
+}
+
+extern "C" void tamm_space_destroy(tamm_space* s) { delete s; }
+
+// ---------------------------------------------------------------- tensors
+
+namespace tamm {
+
+static bool block_rule(const tamm_tensor& T, const int64_t* tt) {
+  if (T.sym == TAMM_SYM_DENSE) return true;
+  int up = 0, lo = 0, x = 0;
+  for (int m = 0; m < T.nm; ++m) {
+    const int s = T.sp[m]->spin[(size_t)tt[m]];
+    (m < T.n_upper ? up : lo) += s;
+    x ^= T.sp[m]->irrep[(size_t)tt[m]];
+  }
+  if (up != lo) return false;
+  if (T.sym == TAMM_SYM_SPIN_IRREP && x != 0) return false;
+  return true;
+}
+
+// Fill lookup/tiles/off from a predicate on tile tuples (lexicographic order).
+template <class Pred>
+static void build_blocks(tamm_tensor& T, Pred keep) {
+  int64_t n_tuples = 1;
+  for (int m = 0; m < T.nm; ++m) {
+    n_tuples *= T.sp[m]->n_tiles;
+    if (n_tuples > (int64_t(1) << 31)) throw Error(TAMM_EINVAL, "tensor: too many tile tuples");
+  }
+  T.lookup.assign((size_t)n_tuples, -1);
+  T.tiles.clear();
+  T.off.assign(1, 0);
+  int64_t tt[kMaxModes];
+  int64_t pos = 0, nb = 0;
+  for (int64_t lin = 0; lin < n_tuples; ++lin) {
+    int64_t r = lin;
+    for (int m = T.nm - 1; m >= 0; --m) {
+      tt[m] = r % T.sp[m]->n_tiles;
+      r /= T.sp[m]->n_tiles;
+    }
+    if (!keep(tt)) continue;
+    int64_t sz = 1;
+    for (int m = 0; m < T.nm; ++m) {
+      T.tiles.push_back(tt[m]);
+      sz *= T.sp[m]->size[(size_t)tt[m]];
+    }
+    T.lookup[(size_t)lin] = nb++;
+    pos += sz;
+    T.off.push_back(pos);
+  }
+  T.n_blocks = nb;
+  T.n_elems = pos;
+}
+
+std::unique_ptr<tamm_tensor> make_permuted_tensor(const tamm_tensor& S, const int* perm) {
+  // New tensor whose mode m is S's mode perm[m]; stores exactly the images of S's blocks.
+  std::unique_ptr<tamm_tensor> T(new tamm_tensor());
+  T->ctx = S.ctx;
+  T->id = S.ctx->next_id++;
+  T->nm = S.nm;
+  T->n_upper = -1;
+  T->sym = -1;
+  for (int m = 0; m < S.nm; ++m) T->sp[m] = S.sp[perm[m]];
+  build_blocks(*T, [&](const int64_t* tt) {
+    int64_t st[kMaxModes];
+    for (int m = 0; m < S.nm; ++m) st[perm[m]] = tt[m];
+    return S.find(st) >= 0;
+  });
+  return T;
+}
+
+}  // namespace tamm
+
+extern "C" tamm_status tamm_tensor_create(tamm_ctx* ctx, int n_modes, tamm_space* const* modes, int n_upper,
+                                          int symmetry, tamm_tensor** out) {
+  if (!ctx || !out) return TAMM_EINVAL;
+  *out = nullptr;
+  return guarded(ctx, [&] {
+    if (n_modes <= 0 || n_modes > kMaxModes || !modes) throw Error(TAMM_EINVAL, "tensor: 1..8 modes");
+    if (n_upper < 0 || n_upper > n_modes) throw Error(TAMM_EINVAL, "tensor: n_upper out of range");
+    if (symmetry < TAMM_SYM_DENSE || symmetry > TAMM_SYM_SPIN_IRREP) throw Error(TAMM_EINVAL, "tensor: symmetry");
+    std::unique_ptr<tamm_tensor> T(new tamm_tensor());
+    T->ctx = ctx;
+    T->id = ctx->next_id++;
+    T->nm = n_modes;
+    T->n_upper = n_upper;
+    T->sym = symmetry;
+    for (int m = 0; m < n_modes; ++m) {
+      if (!modes[m]) throw Error(TAMM_EINVAL, "tensor: null space");
+      T->sp[m] = modes[m];
+    }
+    build_blocks(*T, [&](const int64_t* tt) { return block_rule(*T, tt); });
+    *out = T.release();
+  });
+}
+
+extern "C" tamm_status tamm_tensor_create_permuted(tamm_ctx* ctx, const tamm_tensor* like, const int* perm,
+                                                   tamm_tensor** out) {
+  if (!ctx || !out) return TAMM_EINVAL;
+  *out = nullptr;
+  return guarded(ctx, [&] {
+    if (!like || !perm) throw Error(TAMM_EINVAL, "permuted tensor: null argument");
+    bool seen[kMaxModes] = {};
+    for (int m = 0; m < like->nm; ++m) {
+      if (perm[m] < 0 || perm[m] >= like->nm || seen[perm[m]]) throw Error(TAMM_EINVAL, "permuted tensor: bad perm");
+      seen[perm[m]] = true;
+    }
+    *out = make_permuted_tensor(*like, perm).release();
+  });
+}
+
+extern "C" tamm_status tamm_tensor_info(const tamm_tensor* t, int64_t* n_blocks, int64_t* n_elems) {
+  if (!t) return TAMM_EINVAL;
+  if (n_blocks) *n_blocks = t->n_blocks;
+  if (n_elems) *n_elems = t->n_elems;
+  return TAMM_OK;
+}
+
+extern "C" tamm_status tamm_tensor_blocks(const tamm_tensor* t, int64_t* block_tiles, int64_t* block_offsets) {
+  if (!t) return TAMM_EINVAL;
+  if (block_tiles && !t->tiles.empty()) memcpy(block_tiles, t->tiles.data(), t->tiles.size() * sizeof(int64_t));
+  if (block_offsets && t->n_blocks) memcpy(block_offsets, t->off.data(), (size_t)t->n_blocks * sizeof(int64_t));
+  return TAMM_OK;
+}
+
+extern "C" tamm_status tamm_tensor_bind(tamm_tensor* t, double* device_data) {
+  if (!t) return TAMM_EINVAL;
+  return guarded(t->ctx, [&] {
+    require_device(t->ctx);
+    if (!device_data && t->n_elems) throw Error(TAMM_EINVAL, "bind: null device pointer");
+    if (((uintptr_t)device_data) % 8) throw Error(TAMM_EINVAL, "bind: pointer not 8-byte aligned");
+    if (t->owned) ctx_free(t->ctx, t->data, t->owned_bytes);
+    t->owned = false;
+    t->owned_bytes = 0;
+    t->data = device_data;
+  });
+}
+
+extern "C" tamm_status tamm_tensor_allocate(tamm_tensor* t) {
+  if (!t) return TAMM_EINVAL;
+  return guarded(t->ctx, [&] {
+    if (t->owned) ctx_free(t->ctx, t->data, t->owned_bytes);
+    t->owned = false;
+    const size_t bytes = (size_t)std::max<int64_t>(t->n_elems, 1) * sizeof(double);
+    t->data = (double*)ctx_alloc(t->ctx, bytes);
+    t->owned = true;
+    t->owned_bytes = bytes;
+  });
+}
+
+extern "C" double* tamm_tensor_data(const tamm_tensor* t) { return t ? t->data : nullptr; }
+
+extern "C" void tamm_tensor_destroy(tamm_tensor* t) {
+  if (!t) return;
+  if (t->owned) ctx_free(t->ctx, t->data, t->owned_bytes);
+  delete t;
+}
+
+// ------------------------------------------------------------- operations
+
+extern "C" tamm_status tamm_contract(tamm_ctx* ctx, double alpha, tamm_tensor* C, const char* lc, double beta,
+                                     const tamm_tensor* A, const char* la, const tamm_tensor* B, const char* lb,
+                                     int precision, int slices) {
+  if (!ctx) return TAMM_EINVAL;
+  return guarded(ctx, [&] {
+    require_device(ctx);
+    run_contract(ctx, alpha, C, lc, beta, A, la, B, lb, precision, slices);
+  });
+}
+
+extern "C" tamm_status tamm_contract_flops(tamm_ctx* ctx, const tamm_tensor* C, const char* lc,
+                                           const tamm_tensor* A, const char* la, const tamm_tensor* B,
+                                           const char* lb, double* flops) {
+  if (!ctx || !flops) return TAMM_EINVAL;
+  return guarded(ctx, [&] { *flops = contract_flops(ctx, C, lc, A, la, B, lb); });
+}
+
+extern "C" tamm_status tamm_add(tamm_ctx* ctx, tamm_tensor* C, const char* lc, double beta, const tamm_tensor* A,
+                                int n_terms, const char* const* la, const double* alpha) {
+  if (!ctx) return TAMM_EINVAL;
+  return guarded(ctx, [&] {
+    require_device(ctx);
+    run_add(ctx, C, lc, beta, A, n_terms, la, alpha);
+  });
+}
+
+extern "C" tamm_status tamm_energy_async(tamm_ctx* ctx, double alpha, const tamm_tensor* A, const char* la,
+                                         const tamm_tensor* B, const char* lb, double* result_device) {
+  if (!ctx) return TAMM_EINVAL;
+  return guarded(ctx, [&] {
+    require_device(ctx);
+    if (!result_device) throw Error(TAMM_EINVAL, "energy: null result pointer");
+    run_energy(ctx, alpha, A, la, B, lb, result_device);
+  });
+}
+
+extern "C" tamm_status tamm_energy(tamm_ctx* ctx, double alpha, const tamm_tensor* A, const char* la,
+                                   const tamm_tensor* B, const char* lb, double* result_host) {
+  if (!ctx) return TAMM_EINVAL;
+  return guarded(ctx, [&] {
+    require_device(ctx);
+    if (!result_host) throw Error(TAMM_EINVAL, "energy: null result pointer");
+    double* out = result_slot(ctx, 0);
+    run_energy(ctx, alpha, A, la, B, lb, out);
+    cuda_check(cudaMemcpyAsync(ctx->h_result, out, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream), "D2H");
+    sync_and_check(ctx);
+    *result_host = ctx->h_result[0];
+  });
+}
+
+extern "C" tamm_status tamm_norm_async(tamm_ctx* ctx, const tamm_tensor* t, double* result_device) {
+  if (!ctx) return TAMM_EINVAL;
+  return guarded(ctx, [&] {
+    require_device(ctx);
+    if (!result_device) throw Error(TAMM_EINVAL, "norm: null result pointer");
+    run_norm(ctx, t, result_device);
+  });
+}
+
+extern "C" tamm_status tamm_norm(tamm_ctx* ctx, const tamm_tensor* t, double* result_host) {
+  if (!ctx) return TAMM_EINVAL;
+  return guarded(ctx, [&] {
+    require_device(ctx);
+    if (!result_host) throw Error(TAMM_EINVAL, "norm: null result pointer");
+    double* out = result_slot(ctx, 1);
+    run_norm(ctx, t, out);
+    cuda_check(cudaMemcpyAsync(ctx->h_result, out, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream), "D2H");
+    sync_and_check(ctx);
+    *result_host = ctx->h_result[0];
+  });
+}

@@ -1,0 +1,151 @@
+// Internal structures of the GB300 block-sparse contraction library.
+// Host side: index spaces, block-sparse tensors, contraction plans.
+// Device side: plain-old-data task records consumed by the kernels.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <map>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/tamm_gb300.h"
+
+namespace tamm {
+
+constexpr int kMaxModes = 8;
+constexpr int kMaxKernelModes = 4;  // add/energy kernels handle tensors of up to 4 modes
+constexpr int kMaxAddTerms = 4;
+
+// ------------------------------------------------------------ device records
+
+// One output block of a permuted add (and of the energy's pairing).
+// Element e of the destination block (row-major over dim[0..nm)) reads term t's
+// source at src_off[t] + sum_m idx_m * sstride[t][m]  (src_off < 0: no source block).
+struct AddBlock {
+  int64_t dst_off;
+  int64_t n;
+  int32_t nm;
+  int32_t dim[kMaxKernelModes];
+  int64_t src_off[kMaxAddTerms];
+  int32_t sstride[kMaxAddTerms][kMaxKernelModes];
+};
+
+// A chunk of one AddBlock processed by one CTA.
+struct ChunkItem {
+  int32_t block;
+  int32_t pad;
+  int64_t start;
+};
+
+// FP64 block GEMM records.  One group per output block (in GEMM layout);
+// tasks of a group are the block pairs summed into it, in fixed order.
+struct GemmGroup {
+  int64_t c_off;
+  int32_t M, N;
+  int32_t task_begin, task_end;
+};
+struct GemmTask {
+  int64_t a_off;  // A block, row-major M x K
+  int64_t b_off;  // B block, row-major K x N
+  int32_t K;
+  int32_t pad;
+};
+struct GemmItem {
+  int32_t group;
+  int32_t m0, n0;
+  int32_t pad;
+};
+
+// ------------------------------------------------------------- host objects
+
+struct Allocator {
+  tamm_alloc_fn alloc = nullptr;
+  tamm_free_fn release = nullptr;
+  void* user = nullptr;
+};
+
+// Device buffer obtained from the context allocator, released stream-ordered.
+struct DevBuf {
+  void* ptr = nullptr;
+  size_t bytes = 0;
+};
+
+struct Plan;  // contraction / add / energy plans, cached per context
+
+}  // namespace tamm
+
+struct tamm_space {
+  tamm_ctx* ctx = nullptr;
+  uint64_t id = 0;
+  int n_tiles = 0;
+  int64_t n = 0;
+  std::vector<int64_t> off, size;
+  std::vector<int> spin, irrep;
+};
+
+struct tamm_tensor {
+  tamm_ctx* ctx = nullptr;
+  uint64_t id = 0;
+  int nm = 0, n_upper = 0, sym = 0;
+  const tamm_space* sp[tamm::kMaxModes] = {};
+  int64_t n_blocks = 0, n_elems = 0;
+  std::vector<int64_t> tiles;   // n_blocks * nm
+  std::vector<int64_t> off;     // n_blocks + 1
+  std::vector<int64_t> lookup;  // dense tile tuple -> block index, -1 if not stored
+  double* data = nullptr;
+  bool owned = false;
+  size_t owned_bytes = 0;
+
+  int64_t find(const int64_t* tt) const {
+    int64_t lin = 0;
+    for (int m = 0; m < nm; ++m) lin = lin * sp[m]->n_tiles + tt[m];
+    return lookup[(size_t)lin];
+  }
+  int64_t block_size(int64_t b) const { return off[(size_t)b + 1] - off[(size_t)b]; }
+};
+
+struct tamm_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  tamm::Allocator allocator;
+  std::string last_error;
+  uint64_t next_id = 1;
+  int* d_status = nullptr;    // device status word (TAMM_ETIMEOUT / TAMM_ECHECK)
+  double* d_reduce = nullptr; // partial sums of reductions
+  size_t reduce_cap = 0;
+  double* h_result = nullptr; // pinned host double for synchronous results
+  tamm::DevBuf scratch;       // grows on demand, stream-ordered reuse
+  std::map<std::string, std::unique_ptr<tamm::Plan>> plans;
+  int sm_count = 0;
+  bool host_only = false;  // device -1: metadata and planning only
+};
+
+namespace tamm {
+
+// allocation through the context allocator (stream-ordered)
+void* ctx_alloc(tamm_ctx* ctx, size_t bytes);
+void ctx_free(tamm_ctx* ctx, void* p, size_t bytes);
+void* ctx_scratch(tamm_ctx* ctx, size_t bytes);  // valid until the next ctx_scratch call
+
+// ------------------------------------------------------------ kernel launch
+// Implemented in kernels_f64.cu.  All launch on ctx->stream; return cudaError_t.
+cudaError_t launch_add(tamm_ctx* ctx, double* dst, const double* src, const AddBlock* blocks,
+                       const ChunkItem* items, int64_t n_items, int n_terms, double beta, const double* alpha_host);
+cudaError_t launch_energy_partials(tamm_ctx* ctx, const double* a, const double* b, const AddBlock* blocks,
+                                   const ChunkItem* items, int64_t n_items, double* partials);
+cudaError_t launch_sumsq_partials(tamm_ctx* ctx, const double* x, int64_t n, double* partials, int64_t n_parts);
+cudaError_t launch_reduce_final(tamm_ctx* ctx, const double* partials, int64_t n, double alpha, int take_sqrt,
+                                double* out_device);
+cudaError_t launch_gemm_f64(tamm_ctx* ctx, const double* a, const double* b, double* c, const GemmGroup* groups,
+                            const GemmTask* tasks, const GemmItem* items, int64_t n_items, double alpha,
+                            double beta);
+
+constexpr int kChunk = 4096;         // elements per add/energy chunk
+constexpr int kGemmTileM = 64;       // FP64 GEMM CTA tile
+constexpr int kGemmTileN = 64;
+
+}  // namespace tamm

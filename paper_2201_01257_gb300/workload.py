@@ -1,0 +1,106 @@
+"""Run a synthetic workload recipe (``tamm_synth.workloads``) through the GPU library.
+
+Builds the index spaces and block-sparse tensors of a recipe, fills them with
+the shared seeded generator on the host (per stored block) and uploads them,
+then executes the recipe's steps with ``tamm_contract`` / ``tamm_add`` /
+``tamm_energy``.  A contraction with an output antisymmetriser P(ab)P(ij)
+writes its product into a scratch tensor laid out in GEMM order and applies
+the four signed permutations in one ``tamm_add`` pass.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+import tamm_synth
+from tamm_synth import workloads as wl
+
+from . import Context, Tensor
+
+
+def build(ctx: Context, w: wl.Workload, fill: bool = True, only=None):
+    spaces = {k: ctx.space(s.groups, s.tile, s.tile_sizes) for k, s in w.spaces.items()}
+    tensors = {}
+    for name, t in w.tensors.items():
+        if only is not None and name not in only:
+            continue
+        T = ctx.tensor([spaces[m] for m in t.modes], t.n_upper, t.sym)
+        if fill and t.sigma != 0.0:
+            fill_tensor(T, w.seed, t)
+        tensors[name] = T
+    return spaces, tensors
+
+
+def fill_tensor(T: Tensor, seed: int, spec: wl.TensorSpec) -> None:
+    host = np.zeros(T.n_elems, dtype=np.float64)
+    lo, ext = T.block_lo_ext()
+    dims = [m.n for m in T.modes]
+    tamm_synth.fill_boxes(seed, spec.stream, spec.sigma, dims, spec.anti01, spec.anti23, lo, ext,
+                          T.block_offsets, host)
+    T.upload(host)
+
+
+def gemm_order(step: wl.ContractSpec) -> str:
+    """Output label order of the block GEMMs: C labels of the operand holding C's first label, then the rest."""
+    left = step.la if step.lc[0] in step.la else step.lb
+    fl = "".join(c for c in step.lc if c in left)
+    fr = "".join(c for c in step.lc if c not in left)
+    return fl + fr
+
+
+def antisym_terms(lc: str, lx: str):
+    """tamm_add terms for C(lc) += P(ab)P(ij) X, X stored with labels lx (a permutation of lc = 'abij')."""
+    a, b, i, j = lc
+    swaps = [({}, 1.0), ({a: b, b: a}, -1.0), ({i: j, j: i}, -1.0), ({a: b, b: a, i: j, j: i}, 1.0)]
+    return [(s, "".join(m.get(c, c) for c in lx)) for m, s in swaps]
+
+
+class Runner:
+    """Executes a recipe's steps; scratch tensors for antisymmetrised products are cached."""
+
+    def __init__(self, ctx: Context, w: wl.Workload, spaces, tensors):
+        self.ctx, self.w, self.spaces, self.tensors = ctx, w, spaces, tensors
+        self._scratch = {}
+
+    def scratch_for(self, step: wl.ContractSpec) -> tuple:
+        lx = gemm_order(step)
+        if step.name not in self._scratch:
+            C = self.tensors[step.c]
+            perm = [step.lc.index(c) for c in lx]
+            self._scratch[step.name] = (self.ctx.tensor_permuted(C, perm), lx)
+        return self._scratch[step.name]
+
+    def flops(self, step) -> float:
+        if not isinstance(step, wl.ContractSpec):
+            return 0.0
+        T = self.tensors
+        if step.antisym:
+            X, lx = self.scratch_for(step)
+            return self.ctx.flops(X, lx, T[step.a], step.la, T[step.b], step.lb)
+        return self.ctx.flops(T[step.c], step.lc, T[step.a], step.la, T[step.b], step.lb)
+
+    def run_step(self, step, precision="f64", slices: int = 0, energy_out=None):
+        T, ctx = self.tensors, self.ctx
+        if isinstance(step, wl.EnergySpec):
+            if energy_out is not None:
+                ctx.energy_async(step.alpha, T[step.a], step.la, T[step.b], step.lb, energy_out)
+                return None
+            return ctx.energy(step.alpha, T[step.a], step.la, T[step.b], step.lb)
+        if isinstance(step, wl.AddSpec):
+            ctx.add(T[step.c], step.lc, step.beta, T[step.a], [(step.alpha, step.la)])
+            return None
+        if step.antisym:
+            X, lx = self.scratch_for(step)
+            ctx.contract(step.alpha, X, lx, 0.0, T[step.a], step.la, T[step.b], step.lb, precision, slices)
+            ctx.add(T[step.c], step.lc, step.beta, X, antisym_terms(step.lc, lx))
+            return None
+        ctx.contract(step.alpha, T[step.c], step.lc, step.beta, T[step.a], step.la, T[step.b], step.lb,
+                     precision, slices)
+        return None
+
+    def run(self, precision="f64", slices: int = 0, steps=None, energy_out=None) -> dict:
+        out = {}
+        for s in steps if steps is not None else self.w.steps:
+            r = self.run_step(s, precision, slices, energy_out)
+            if r is not None:
+                out[s.name] = r
+        return out

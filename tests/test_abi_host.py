@@ -1,0 +1,145 @@
+"""C-ABI library: loads, exports every declared symbol, and its host-side
+planning (tiling, block tables, nonzero block pairs) agrees with the oracle's
+independent implementation and with closed forms.  No device work."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle as O
+import paper_2201_01257_gb300 as tg
+from tamm_synth import workloads as wl
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    names = set()
+    for f in os.listdir(os.path.join(ROOT, "include")):
+        if f.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", f)).read()
+            names |= set(re.findall(r"TAMM_API\s+[\w\s\*]+?\b(tamm_\w+)\s*\(", src))
+    return names
+
+
+def test_library_builds_and_exports_every_declared_symbol():
+    lib = tg.load()
+    names = declared_symbols()
+    assert len(names) >= 20
+    for n in sorted(names):
+        assert hasattr(lib, n), n
+    assert {n for n, _, _ in tg.PROTOTYPES} == names
+
+
+@pytest.fixture(scope="module")
+def hctx():
+    return tg.Context(-1)
+
+
+def spaces_for(ctx, w):
+    return ({k: ctx.space(s.groups, s.tile, s.tile_sizes) for k, s in w.spaces.items()},
+            {k: O.Space.from_spec(s) for k, s in w.spaces.items()})
+
+
+@pytest.mark.parametrize("cfg", [1, 2, 4, 5])
+def test_block_tables_match_oracle(hctx, cfg):
+    w = wl.CONFIGS[cfg]()
+    gs, os_ = spaces_for(hctx, w)
+    for k in gs:
+        assert gs[k].n == os_[k].n
+        assert list(gs[k].tile_size) == [t[1] for t in os_[k].tiles]
+        assert list(gs[k].tile_spin) == [t[2] for t in os_[k].tiles]
+    for name, t in w.tensors.items():
+        G = hctx.tensor([gs[m] for m in t.modes], t.n_upper, t.sym)
+        R = O.Tensor([os_[m] for m in t.modes], t.n_upper, t.sym, alloc=False)
+        assert (G.n_blocks, G.n_elems) == (R.n_blocks, R.n_elems), name
+        assert np.array_equal(G.block_tiles, R.block_tiles), name
+        assert np.array_equal(G.block_offsets, R.block_off), name
+
+
+def test_irrep_rule_and_explicit_tiles_match_oracle(hctx):
+    groups = [(5, 1, 0), (3, 1, 3), (4, 1, 5), (5, -1, 0), (3, -1, 3), (4, -1, 5)]
+    tiles = (2, 3, 3, 4, 3, 2, 3, 4)
+    g = hctx.space(groups, tile_sizes=tiles)
+    o = O.Space(groups, tile_sizes=tiles)
+    for sym in ("dense", "spin", "spin_irrep"):
+        G = hctx.tensor([g] * 4, 2, sym)
+        R = O.Tensor([o] * 4, 2, sym, alloc=False)
+        assert np.array_equal(G.block_tiles, R.block_tiles) and np.array_equal(G.block_offsets, R.block_off)
+
+
+def test_fig_tensor_const_eight_blocks(hctx):
+    tM = hctx.space([(30, 1, 0)], tile_sizes=(10, 20))
+    tK = hctx.space([(20, 1, 0)], tile=5)
+    A = hctx.tensor([tM, tK], 1, "dense")
+    assert (A.n_blocks, A.n_elems) == (8, 600)
+
+
+def test_flop_counts_closed_forms(hctx):
+    o = hctx.space([(4, 1, 0), (4, -1, 0)], tile=2)
+    v = hctx.space([(8, 1, 0), (8, -1, 0)], tile=4)
+    V = hctx.tensor([v] * 4, 2)
+    T = hctx.tensor([v, v, o, o], 2)
+    R = hctx.tensor([v, v, o, o], 2)
+    assert hctx.flops(R, "abij", V, "abef", T, "efij") * 32 == 5 * 2 * 16 ** 4 * 8 ** 2
+    t1 = hctx.tensor([v, o], 1)
+    V3 = hctx.tensor([v, v, v, o], 2)
+    assert hctx.flops(R, "abij", V3, "abej", t1, "ei") * 16 == 3 * 2 * 16 ** 3 * 8 ** 2
+    # operand order does not change the count
+    assert hctx.flops(R, "abij", T, "efij", V, "abef") == hctx.flops(R, "abij", V, "abef", T, "efij")
+
+
+def test_config2_flops(hctx):
+    w = wl.config2()
+    gs, _ = spaces_for(hctx, w)
+    T = {n: hctx.tensor([gs[m] for m in t.modes], t.n_upper, t.sym) for n, t in w.tensors.items()}
+    f = {s.name: hctx.flops(T[s.c], s.lc, T[s.a], s.la, T[s.b], s.lb) for s in w.steps
+         if isinstance(s, wl.ContractSpec)}
+    assert f["ladder"] == 5 / 32 * 2 * 240 ** 4 * 40 ** 2
+    assert f["intermediate"] == 5 / 32 * 2 * 240 ** 2 * 40 ** 4
+    assert f["oooo"] == 5 / 32 * 2 * 240 ** 2 * 40 ** 4
+    assert abs(f["ring"] - 2.765e11) / 2.765e11 < 1e-3
+    assert abs(f["t1"] - 8.294e9) / 8.294e9 < 1e-3
+
+
+@pytest.mark.parametrize("lc,la,lb", [
+    ("abij", "abef", "efkj"), ("abij", "abij", "efij"), ("abii", "abef", "efij"), ("abij", "abe", "efij")])
+def test_invalid_labels_rejected(hctx, lc, la, lb):
+    o = hctx.space([(4, 1, 0), (4, -1, 0)], tile=2)
+    v = hctx.space([(8, 1, 0), (8, -1, 0)], tile=4)
+    V, T, R = hctx.tensor([v] * 4, 2), hctx.tensor([v, v, o, o], 2), hctx.tensor([v, v, o, o], 2)
+    with pytest.raises(tg.TammError) as e:
+        hctx.flops(R, lc, V, la, T, lb)
+    assert e.value.status == tg.TAMM_EINVAL
+
+
+def test_space_errors(hctx):
+    with pytest.raises(tg.TammError):
+        hctx.space([(10, 1, 0), (10, -1, 0)], tile_sizes=(5, 10, 5))
+    with pytest.raises(tg.TammError):
+        hctx.space([(10, 2, 0)], tile=4)
+    with pytest.raises(tg.TammError):
+        hctx.space([(10, 1, 9)], tile=4)
+
+
+def test_host_only_context_refuses_device_work(hctx):
+    o = hctx.space([(4, 1, 0), (4, -1, 0)], tile=2)
+    T = hctx.tensor([o, o], 1)
+    r = ctypes.c_double()
+    assert hctx.lib.tamm_norm(hctx.handle, T.handle, ctypes.byref(r)) == tg.TAMM_ECUDA
+    assert b"host-only" in hctx.lib.tamm_last_error(hctx.handle)
+    assert hctx.lib.tamm_tensor_allocate(T.handle) == tg.TAMM_ECUDA
+
+
+def test_permuted_tensor_stores_images_of_blocks(hctx):
+    o = hctx.space([(4, 1, 0), (4, -1, 0)], tile=2)
+    v = hctx.space([(6, 1, 0), (6, -1, 0)], tile=3)
+    R = hctx.tensor([v, v, o, o], 2)
+    X = hctx.tensor_permuted(R, [0, 2, 1, 3])  # (a, i, b, j)
+    assert X.n_elems == R.n_elems and X.n_blocks == R.n_blocks
+    imgs = {tuple(t[[0, 2, 1, 3]]) for t in R.block_tiles}
+    assert {tuple(t) for t in X.block_tiles} == imgs
+    with pytest.raises(tg.TammError):
+        hctx.tensor_permuted(R, [0, 0, 1, 3])
