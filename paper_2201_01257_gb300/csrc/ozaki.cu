@@ -1,10 +1,737 @@
-// Split-precision (Ozaki-style) block-sparse contraction: placeholder until the
-// tcgen05 kernels land.
-#include "tamm_contract.h"
+// Split-precision block-sparse contraction: slicing kernel, tcgen05 GEMM
+// kernel and the host plan that drives them.  The arithmetic scheme is
+// described in ozaki.h.
+#include <algorithm>
+#include <cstring>
+
+#include "ozaki.h"
+#include "sm100.cuh"
 
 namespace tamm {
-void run_contract_ozaki(tamm_ctx*, double, tamm_tensor*, const char*, double, const tamm_tensor*, const char*,
-                        const tamm_tensor*, const char*, int) {
-  throw Error(TAMM_EUNSUPPORTED, "split-precision path not built");
+
+// ======================================================================
+// Device: slicing
+// ======================================================================
+namespace {
+
+// bf16 bits of d * 2^(-7k), |d| <= 64 (exact).
+__device__ __forceinline__ uint32_t bf16_digit(int d, int k) {
+  if (d == 0) return 0u;
+  const uint32_t s = d < 0 ? 0x8000u : 0u;
+  const uint32_t a = (uint32_t)(d < 0 ? -d : d);
+  const int p = 31 - __clz(a);  // 0..6
+  const uint32_t e = (uint32_t)(127 + p - 7 * k);
+  const uint32_t m = (a << (7 - p)) & 0x7Fu;
+  return s | (e << 7) | m;
 }
+
+// Balanced base-2^7 digits of x / 2^(e-6) (first digit 6 bits), S digits,
+// from the FP64 bit pattern with integer arithmetic only.
+__device__ __forceinline__ void digits_of(double x, int e, int S, int (&d)[kOzMaxSlices]) {
+#pragma unroll
+  for (int k = 0; k < kOzMaxSlices; ++k) d[k] = 0;
+  const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
+  const bool neg = (bits >> 63) != 0;
+  int E = (int)((bits >> 52) & 0x7FF);
+  unsigned long long M = bits & ((1ull << 52) - 1);
+  if (E == 0) E = 1; else M |= 1ull << 52;
+  if (M == 0 || e == kOzExpZero) return;
+  // |x| = M 2^(E-1075);  F = round(|x| 2^(7S-1-e))
+  const int shift = E - 1075 + 7 * S - 1 - e;
+  long long F;
+  if (shift >= 0) {
+    F = (long long)(M << shift);
+  } else if (shift > -63) {
+    const int rs = -shift;
+    F = (long long)((M >> rs) + ((M >> (rs - 1)) & 1ull));
+  } else {
+    return;
+  }
+#pragma unroll
+  for (int k = kOzMaxSlices - 1; k >= 1; --k) {
+    if (k < S) {
+      const int dk = (int)((F + 64) & 127) - 64;
+      d[k] = dk;
+      F = (F - dk) >> 7;
+    }
+  }
+  d[0] = (int)F;
+  if (neg) {
+#pragma unroll
+    for (int k = 0; k < kOzMaxSlices; ++k) d[k] = -d[k];
+  }
+}
+
+__device__ __forceinline__ int64_t mixed_offset(int32_t idx, int n, const int32_t* dim, const int32_t* stride) {
+  int64_t off = 0;
+  for (int m = n - 1; m >= 0; --m) {
+    const int32_t x = idx % dim[m];
+    idx /= dim[m];
+    off += (int64_t)x * stride[m];
+  }
+  return off;
+}
+
+// Offsets of the 8 consecutive summed indices k0..k0+7 (entries past K are unused).
+__device__ __forceinline__ void k_offsets8(const SliceBlock& B, int32_t k0, int64_t (&off)[8]) {
+  int32_t kk[4] = {0, 0, 0, 0};
+  int32_t r = k0;
+  int64_t o = 0;
+  for (int m = B.nk - 1; m >= 0; --m) {
+    kk[m] = r % B.kdim[m];
+    r /= B.kdim[m];
+    o += (int64_t)kk[m] * B.kstride[m];
+  }
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    off[j] = o;
+    int m = B.nk - 1;
+    if (m < 0) continue;
+    ++kk[m];
+    o += B.kstride[m];
+    while (m > 0 && kk[m] == B.kdim[m]) {
+      o -= (int64_t)kk[m] * B.kstride[m];
+      kk[m] = 0;
+      --m;
+      ++kk[m];
+      o += B.kstride[m];
+    }
+  }
+}
+
+__global__ void __launch_bounds__(256) ozaki_slice_kernel(const double* __restrict__ src,
+                                                          const SliceBlock* __restrict__ blocks,
+                                                          const SliceItem* __restrict__ items, int S,
+                                                          uint8_t* __restrict__ tiles, int32_t* __restrict__ exps) {
+  const SliceItem it = items[blockIdx.x];
+  const SliceBlock& B = blocks[it.block];
+  __shared__ unsigned long long rmax[32];
+  __shared__ int rexp[32];
+  __shared__ int64_t roff[32];
+  const int tid = threadIdx.x;
+  if (tid < it.nr) {
+    const int32_t grow = it.r0 + tid;
+    rmax[tid] = 0ull;
+    roff[tid] = grow < B.rows ? B.src_off + mixed_offset(grow, B.nr, B.rdim, B.rstride) : -1;
+  }
+  __syncthreads();
+  const int nch = B.k_tiles * 2;  // 8-wide chunks of the padded K range
+  const int units = it.nr * nch;
+  // pass 1: per-row max |x| (as ordered bit patterns)
+  for (int u = tid; u < units; u += blockDim.x) {
+    const int r = B.k_contig ? u / nch : u % it.nr;
+    const int ch = B.k_contig ? u % nch : u / it.nr;
+    if (roff[r] < 0) continue;
+    int64_t off[8];
+    k_offsets8(B, ch * 8, off);
+    unsigned long long m = 0ull;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      if (ch * 8 + j < B.K) {
+        const unsigned long long b = (unsigned long long)__double_as_longlong(__ldg(src + roff[r] + off[j]));
+        m = max(m, b & 0x7FFFFFFFFFFFFFFFull);
+      }
+    }
+    if (m) atomicMax(&rmax[r], m);
+  }
+  __syncthreads();
+  if (tid < it.nr) {
+    int e = kOzExpZero;
+    if (rmax[tid] != 0ull) (void)frexp(__longlong_as_double((long long)rmax[tid]), &e);
+    rexp[tid] = e;
+    exps[B.exp_off + it.r0 + tid] = e;
+  }
+  __syncthreads();
+  // pass 2: digits, written into the 32-byte-swizzled tile images
+  const size_t tile_bytes = (size_t)S * kOzTileBytesPerSlice;
+  for (int u = tid; u < units; u += blockDim.x) {
+    const int r = B.k_contig ? u / nch : u % it.nr;
+    const int ch = B.k_contig ? u % nch : u / it.nr;
+    uint32_t packed[kOzMaxSlices][4];
+#pragma unroll
+    for (int s = 0; s < kOzMaxSlices; ++s)
+#pragma unroll
+      for (int w = 0; w < 4; ++w) packed[s][w] = 0u;
+    if (roff[r] >= 0 && rexp[r] != kOzExpZero) {
+      int64_t off[8];
+      k_offsets8(B, ch * 8, off);
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const double x = ch * 8 + j < B.K ? __ldg(src + roff[r] + off[j]) : 0.0;
+        int d[kOzMaxSlices];
+        digits_of(x, rexp[r], S, d);
+#pragma unroll
+        for (int s = 0; s < kOzMaxSlices; ++s) packed[s][j >> 1] |= bf16_digit(d[s], s) << ((j & 1) * 16);
+      }
+    }
+    const int32_t grow = it.r0 + r;
+    const int32_t rr = grow % kOzTileM;
+    const int64_t tile = B.tile_off + (int64_t)(grow / kOzTileM) * B.k_tiles + ch / 2;
+    const int swz = (ch & 1) ^ ((rr >> 2) & 1);
+    uint8_t* base = tiles + (size_t)tile * tile_bytes + rr * 32 + swz * 16;
+    for (int s = 0; s < S; ++s)
+      *reinterpret_cast<uint4*>(base + (size_t)s * kOzTileBytesPerSlice) =
+          make_uint4(packed[s][0], packed[s][1], packed[s][2], packed[s][3]);
+  }
+}
+
+// ======================================================================
+// Device: tcgen05 GEMM
+// ======================================================================
+
+struct OzParams {
+  const uint8_t* a_tiles;
+  const uint8_t* b_tiles;
+  const int32_t* a_exp;
+  const int32_t* b_exp;
+  const OzGroup* groups;
+  const OzTask* tasks;
+  const OzItem* items;
+  double* c;
+  int* status;
+  double alpha, beta;
+  int S, stages;
+  OzOps full, ragged;
+};
+
+// Warp roles: warpgroup 0 = producer (warp 0), MMA issuer + TMEM owner (warp 1),
+// two idle warps; warpgroups 1 and 2 = eight epilogue warps, two per TMEM lane
+// quadrant.  Registers move from warpgroup 0 to the epilogue with setmaxnreg:
+// 128 * kRegsLow + 256 * kRegsHigh must not exceed 384 * (registers at launch).
+constexpr int kEpiWarps = 8;
+constexpr int kThreads = 128 + 32 * kEpiWarps;
+constexpr int kRegsLow = 40;
+constexpr int kRegsHigh = 232;
+constexpr int kRegsLaunchNeeded = (128 * kRegsLow + 256 * kRegsHigh + kThreads - 1) / kThreads;
+constexpr long long kWaitCycles = 4000000000ll;  // ~2 s at 2 GHz: a bounded wait gives up after this
+
+__device__ __forceinline__ bool wait_bounded(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
+                                             int* status) {
+  const long long t0 = clock64();
+  uint32_t ns = 16;
+  while (!sm100::mbar_try_wait(bar, parity)) {
+    if (*abort_flag) return false;
+    if (clock64() - t0 > kWaitCycles) {
+      *abort_flag = 1;
+      atomicExch(status, TAMM_ETIMEOUT);
+      return false;
+    }
+    __nanosleep(ns);
+    if (ns < 512) ns <<= 1;
+  }
+  return true;
+}
+
+__device__ __forceinline__ float pow2f(int d) {
+  return d < -126 ? 0.0f : __int_as_float((127 + d) << 23);
+}
+
+__device__ __forceinline__ double pow2d(int d) {
+  if (d < -1022) return 0.0;
+  if (d > 1023) return __longlong_as_double(0x7FF0000000000000ll);
+  return __longlong_as_double((long long)(1023 + d) << 52);
+}
+
+__device__ __forceinline__ void two_sum(float& hi, float x, float& err) {
+  const float s = __fadd_rn(hi, x);
+  const float bb = __fsub_rn(s, hi);
+  err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(x, bb));
+  hi = s;
+}
+
+// (hi, lo) += (s0 + s1 + s2 + s3) * sc.  The exact groups s0..s2 enter through
+// error-free TwoSum steps; only the weighted tail s3 is rounded.
+__device__ __forceinline__ void fold(float& hi, float& lo, float s0, float s1, float s2, float s3, float sc) {
+  float e0, e1, e2;
+  two_sum(hi, __fmul_rn(s0, sc), e0);
+  two_sum(hi, __fmul_rn(s1, sc), e1);
+  two_sum(hi, __fmul_rn(s2, sc), e2);
+  lo = __fadd_rn(lo, __fadd_rn(__fadd_rn(e0, e1), __fadd_rn(e2, __fmul_rn(s3, sc))));
+}
+
+__device__ __forceinline__ void epi_barrier() { asm volatile("bar.sync 1, %0;" ::"n"(32 * kEpiWarps) : "memory"); }
+
+__global__ void __launch_bounds__(kThreads, 1) ozaki_gemm_kernel(const __grid_constant__ OzParams p) {
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  const int S = p.S, stages = p.stages;
+  const uint32_t slice_bytes = kOzTileBytesPerSlice;
+  const uint32_t half_bytes = (uint32_t)S * slice_bytes;  // A (or B) part of a stage
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + (size_t)stages * 2 * half_bytes);
+  uint64_t* full = bars;
+  uint64_t* empty = bars + stages;
+  uint64_t* acc_full = bars + 2 * stages;
+  uint64_t* acc_empty = acc_full + 1;
+  uint64_t* drain = acc_full + 2;
+  uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(drain + 1);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_holder + 1);
+  float* sB = reinterpret_cast<float*>(tmem_holder + 4);  // [2][128] per-task column scales
+  int* fref = reinterpret_cast<int*>(sB + 256);            // [128] reference column exponents
+
+  const OzItem it = p.items[blockIdx.x];
+  const OzGroup g = p.groups[it.group];
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const int n_valid = min(kOzTileN, g.N - it.nt * kOzTileN);
+  const bool full_tile = n_valid == kOzTileN;
+  const int n16 = (n_valid + 15) & ~15;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < stages; ++s) {
+      sm100::mbar_init(&full[s], 1);
+      sm100::mbar_init(&empty[s], 1);
+    }
+    sm100::mbar_init(acc_full, 1);
+    sm100::mbar_init(acc_empty, kEpiWarps);
+    sm100::mbar_init(drain, 1);
+    *abort_flag = 0;
+    sm100::fence_mbar_init();
+  }
+  if (warp == 1) {
+    sm100::tmem_alloc(tmem_holder, 512);
+    sm100::tmem_relinquish();
+  }
+  sm100::tc_fence_before();
+  __syncthreads();
+  sm100::tc_fence_after();
+  const uint32_t tmem = *tmem_holder;
+
+  if (warp < 4) {
+    asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(kRegsLow));
+  }
+  if (warp == 0) {
+    // ------------------------------------------------------------ producer
+    if (lane == 0) {
+      int stage = 0;
+      uint32_t phase = 0, issued_mask = 0, issued_parity = 0;
+      for (int t = g.task_begin; t < g.task_end && !*abort_flag; ++t) {
+        const OzTask tk = p.tasks[t];
+        const uint8_t* a = p.a_tiles + (size_t)(tk.a_tile + (int64_t)it.mt * tk.k_tiles) * half_bytes;
+        const uint8_t* b = p.b_tiles + (size_t)(tk.b_tile + (int64_t)it.nt * tk.k_tiles) * half_bytes;
+        for (int kt = 0; kt < tk.k_tiles; ++kt) {
+          if (!wait_bounded(&empty[stage], phase ^ 1u, abort_flag, p.status)) break;
+          uint8_t* sa = smem + (size_t)stage * 2 * half_bytes;
+          sm100::mbar_arrive_expect_tx(&full[stage], 2 * half_bytes);
+          sm100::bulk_g2s(sa, a + (size_t)kt * half_bytes, half_bytes, &full[stage]);
+          sm100::bulk_g2s(sa + half_bytes, b + (size_t)kt * half_bytes, half_bytes, &full[stage]);
+          issued_mask |= 1u << stage;
+          issued_parity = (issued_parity & ~(1u << stage)) | (phase << stage);
+          if (++stage == stages) {
+            stage = 0;
+            phase ^= 1u;
+          }
+        }
+      }
+      // every issued copy must land before the CTA may exit
+      for (int s = 0; s < stages; ++s) {
+        if (!(issued_mask >> s & 1u)) continue;
+        const long long t0 = clock64();
+        while (!sm100::mbar_try_wait(&full[s], (issued_parity >> s) & 1u) && clock64() - t0 < kWaitCycles) {
+        }
+      }
+    }
+  } else if (warp == 1) {
+    // --------------------------------------------------------- MMA issuer
+    if (lane == 0) {
+      const OzOps& ops = full_tile ? p.full : p.ragged;
+      int stage = 0;
+      uint32_t phase = 0, acc_phase = 0;
+      bool ok = true;
+      for (int t = g.task_begin; t < g.task_end && ok; ++t) {
+        const int k_tiles = p.tasks[t].k_tiles;
+        for (int kt = 0; kt < k_tiles; ++kt) {
+          const bool first = kt % kOzChunkTiles == 0;
+          const bool last = (kt + 1) % kOzChunkTiles == 0 || kt + 1 == k_tiles;
+          if (first) {
+            if (!wait_bounded(acc_empty, acc_phase ^ 1u, abort_flag, p.status)) { ok = false; break; }
+            sm100::tc_fence_after();
+          }
+          if (!wait_bounded(&full[stage], phase, abort_flag, p.status)) { ok = false; break; }
+          sm100::tc_fence_after();
+          const uint32_t sa = sm100::smem_u32(smem + (size_t)stage * 2 * half_bytes);
+          const uint32_t sb = sa + half_bytes;
+          for (int i = 0; i < ops.n; ++i) {
+            const OzOp op = ops.op[i];
+            const uint32_t N = full_tile ? 128u * op.nb : (uint32_t)n16;
+            sm100::mma_bf16(tmem + 128u * op.region, sm100::desc_kmajor_sw32(sa + op.a * slice_bytes),
+                            sm100::desc_kmajor_sw32(sb + op.b * slice_bytes), sm100::idesc_bf16_f32(128, N),
+                            (first && op.first) ? 0u : 1u);
+          }
+          sm100::mma_commit(&empty[stage]);
+          if (last) {
+            sm100::mma_commit(acc_full);
+            acc_phase ^= 1u;
+          }
+          if (++stage == stages) {
+            stage = 0;
+            phase ^= 1u;
+          }
+        }
+      }
+      // all issued MMAs must finish before TMEM is released
+      sm100::mma_commit(drain);
+      const long long t0 = clock64();
+      while (!sm100::mbar_try_wait(drain, 0) && clock64() - t0 < kWaitCycles) {
+      }
+    }
+    __syncwarp();
+  } else if (warp >= 4) {
+    // ----------------------------------------------------------- epilogue
+    asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(kRegsHigh));
+    const int q = warp & 3;                 // TMEM lane quadrant of this warp
+    const int h = (warp - 4) >> 2;          // column half: [64h, 64h+64)
+    const int etid = threadIdx.x - 128;     // 0..255
+    const int row = q * 32 + lane;
+    const int c0 = 64 * h;
+    const uint32_t trow = tmem + ((uint32_t)(q * 32) << 16);
+    int Eref = kOzExpZero;
+    for (int t = g.task_begin; t < g.task_end; ++t)
+      Eref = max(Eref, p.a_exp[p.tasks[t].a_exp + (int64_t)it.mt * kOzTileM + row]);
+    if (etid < kOzTileN) {
+      int F = kOzExpZero;
+      for (int t = g.task_begin; t < g.task_end; ++t)
+        F = max(F, p.b_exp[p.tasks[t].b_exp + (int64_t)it.nt * kOzTileN + etid]);
+      fref[etid] = F;
+    }
+    epi_barrier();
+    float hi[64], lo[64];
+#pragma unroll
+    for (int j = 0; j < 64; ++j) hi[j] = lo[j] = 0.0f;
+    uint32_t chunk = 0;
+    bool ok = true;
+    // every epilogue warp passes the per-task named barrier on every path (also after a timeout)
+    for (int t = g.task_begin; t < g.task_end; ++t) {
+      const OzTask tk = p.tasks[t];
+      float* sbuf = sB + ((t - g.task_begin) & 1) * 128;
+      if (etid < kOzTileN) {
+        const int eb = p.b_exp[tk.b_exp + (int64_t)it.nt * kOzTileN + etid];
+        sbuf[etid] = (eb == kOzExpZero) ? 0.0f : pow2f(eb - fref[etid]);
+      }
+      epi_barrier();
+      const int ea = p.a_exp[tk.a_exp + (int64_t)it.mt * kOzTileM + row];
+      const float sA = (ea == kOzExpZero) ? 0.0f : pow2f(ea - Eref);
+      const int n_chunks = ok ? (tk.k_tiles + kOzChunkTiles - 1) / kOzChunkTiles : 0;
+      for (int ck = 0; ck < n_chunks; ++ck, ++chunk) {
+        if (!wait_bounded(acc_full, chunk & 1u, abort_flag, p.status)) { ok = false; break; }
+        sm100::tc_fence_after();
+#pragma unroll
+        for (int g8 = 0; g8 < 8; ++g8) {
+          const int col = c0 + 8 * g8;
+          float r0[8], r1[8], r2[8], r3[8];
+          sm100::tmem_ld8(trow + 0 * 128 + col, r0);
+          sm100::tmem_ld8(trow + 1 * 128 + col, r1);
+          sm100::tmem_ld8(trow + 2 * 128 + col, r2);
+          sm100::tmem_ld8(trow + 3 * 128 + col, r3);
+          sm100::tmem_wait_ld();
+#pragma unroll
+          for (int j = 0; j < 8; ++j)
+            fold(hi[8 * g8 + j], lo[8 * g8 + j], r0[j], r1[j], r2[j], r3[j], sA * sbuf[col + j]);
+        }
+        sm100::tc_fence_before();
+        __syncwarp();
+        if (lane == 0) sm100::mbar_arrive(acc_empty);
+      }
+    }
+    if (ok) {
+      const int grow = it.mt * kOzTileM + row;
+      if (grow < g.M) {
+        double* crow = p.c + g.c_off + (int64_t)grow * g.N + (int64_t)it.nt * kOzTileN;
+#pragma unroll
+        for (int j = 0; j < 64; ++j) {
+          const int col = c0 + j;
+          if (col < n_valid) {
+            double v = 0.0;
+            if (Eref != kOzExpZero && fref[col] != kOzExpZero)
+              v = ((double)hi[j] + (double)lo[j]) * pow2d(Eref + fref[col] - 12);
+            double* cp = crow + col;
+            *cp = p.beta != 0.0 ? fma(p.beta, *cp, p.alpha * v) : p.alpha * v;
+          }
+        }
+      }
+    }
+  }
+  __syncthreads();
+  if (warp == 1) {
+    sm100::tc_fence_after();
+    sm100::tmem_dealloc(tmem, 512);
+  }
+}
+
+}  // namespace
+
+// ======================================================================
+// Launchers
+// ======================================================================
+
+cudaError_t launch_ozaki_slice(tamm_ctx* ctx, const double* src, const SliceBlock* blocks, const SliceItem* items,
+                               int64_t n_items, int S, uint8_t* tiles, int32_t* exps) {
+  if (n_items == 0) return cudaSuccess;
+  ozaki_slice_kernel<<<(unsigned)n_items, 256, 0, ctx->stream>>>(src, blocks, items, S, tiles, exps);
+  return cudaGetLastError();
+}
+
+static int oz_stages(int S) { return std::min(6, (192 * 1024) / (2 * S * kOzTileBytesPerSlice)); }
+
+static size_t oz_smem_bytes(int S) {
+  return (size_t)oz_stages(S) * 2 * S * kOzTileBytesPerSlice + 1024 + 4096;
+}
+
+cudaError_t launch_ozaki_gemm(tamm_ctx* ctx, const uint8_t* a_tiles, const uint8_t* b_tiles, const int32_t* a_exp,
+                              const int32_t* b_exp, const OzGroup* groups, const OzTask* tasks, const OzItem* items,
+                              int64_t n_items, int S, const OzOps& full, const OzOps& ragged, double* c,
+                              double alpha, double beta) {
+  if (n_items == 0) return cudaSuccess;
+  OzParams p;
+  p.a_tiles = a_tiles;
+  p.b_tiles = b_tiles;
+  p.a_exp = a_exp;
+  p.b_exp = b_exp;
+  p.groups = groups;
+  p.tasks = tasks;
+  p.items = items;
+  p.c = c;
+  p.status = ctx->d_status;
+  p.alpha = alpha;
+  p.beta = beta;
+  p.S = S;
+  p.stages = oz_stages(S);
+  p.full = full;
+  p.ragged = ragged;
+  const size_t smem = oz_smem_bytes(S);
+  static int checked_regs = 0;
+  if (!checked_regs) {
+    cudaFuncAttributes fa;
+    cudaError_t e0 = cudaFuncGetAttributes(&fa, ozaki_gemm_kernel);
+    if (e0 != cudaSuccess) return e0;
+    // setmaxnreg.inc would wait forever if the launch pool were too small
+    if (fa.numRegs < kRegsLaunchNeeded) return cudaErrorLaunchOutOfResources;
+    checked_regs = fa.numRegs;
+  }
+  cudaError_t e = cudaFuncSetAttribute(ozaki_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  ozaki_gemm_kernel<<<(unsigned)n_items, kThreads, smem, ctx->stream>>>(p);
+  return cudaGetLastError();
+}
+
+// ======================================================================
+// Host plan
+// ======================================================================
+
+// MMA schedules: products (k, l) with k + l <= S + 1 (1-based), region min(k+l-2, 3).
+static OzOps make_ops(int S, bool fuse) {
+  OzOps ops;
+  memset(&ops, 0, sizeof(ops));
+  bool written[4] = {false, false, false, false};
+  auto push = [&](int a, int b, int nb, int region) {
+    if (ops.n >= kOzMaxOps) throw Error(TAMM_EINVAL, "ozaki: too many MMA ops");
+    OzOp& o = ops.op[ops.n++];
+    o.a = (uint8_t)a;
+    o.b = (uint8_t)b;
+    o.nb = (uint8_t)nb;
+    o.region = (uint8_t)region;
+    bool f0 = !written[region], f1 = nb == 2 ? !written[region + 1] : f0;
+    if (f0 != f1) throw Error(TAMM_EINVAL, "ozaki: inconsistent accumulator schedule");
+    o.first = f0 ? 1 : 0;
+    written[region] = true;
+    if (nb == 2) written[region + 1] = true;
+  };
+  for (int k = 1; k <= S; ++k) {
+    // exact groups (k + l <= 4), fused in pairs of adjacent B slices when allowed
+    int l = 1;
+    while (l <= S + 1 - k && k + l <= 4) {
+      const int region = k + l - 2;
+      if (fuse && l + 1 <= S + 1 - k && k + l + 1 <= 4) {
+        push(k - 1, l - 1, 2, region);
+        l += 2;
+      } else {
+        push(k - 1, l - 1, 1, region);
+        l += 1;
+      }
+    }
+    for (; l <= S + 1 - k; ++l) push(k - 1, l - 1, 1, 3);
+  }
+  return ops;
+}
+
+struct OzakiPlan : Plan {
+  ContractLayout lay;
+  int S;
+  OzOps ops_full, ops_ragged;
+  SliceBlock* d_sa = nullptr;
+  SliceItem* d_ia = nullptr;
+  int64_t n_ia = 0;
+  SliceBlock* d_sb = nullptr;
+  SliceItem* d_ib = nullptr;
+  int64_t n_ib = 0;
+  OzGroup* d_groups = nullptr;
+  OzTask* d_tasks = nullptr;
+  OzItem* d_items = nullptr;
+  int64_t n_items = 0;
+  std::unique_ptr<AddPlan> perm_out;
+  size_t off_ta = 0, off_tb = 0, off_ea = 0, off_eb = 0, off_x = 0, scratch_bytes = 0;
+
+  // Slice records for the GEMM-order operand `gemm` (blocks of `native`
+  // permuted by perm); row modes are [r0, r0+nr), summed modes [k0, k0+nk).
+  static void slice_blocks(const tamm_tensor& native, const tamm_tensor& gemm, const std::vector<int>& perm,
+                           int r0, int nr, int k0, int nk, std::vector<SliceBlock>& out,
+                           std::vector<SliceItem>& items, int64_t& tiles, int64_t& exps) {
+    out.resize((size_t)gemm.n_blocks);
+    for (int64_t b = 0; b < gemm.n_blocks; ++b) {
+      const int64_t* gt = &gemm.tiles[(size_t)(b * gemm.nm)];
+      int64_t nt[kMaxModes];
+      for (int m = 0; m < gemm.nm; ++m) nt[perm[m]] = gt[m];
+      const int64_t nb = native.find(nt);
+      if (nb < 0) throw Error(TAMM_EINVAL, "ozaki: operand block lookup failed");
+      int64_t stride[kMaxModes], s = 1;
+      for (int q = native.nm - 1; q >= 0; --q) {
+        stride[q] = s;
+        s *= native.sp[q]->size[(size_t)nt[q]];
+      }
+      SliceBlock& B = out[(size_t)b];
+      memset(&B, 0, sizeof(B));
+      B.src_off = native.off[(size_t)nb];
+      if (nr > 4 || nk > 4) throw Error(TAMM_EUNSUPPORTED, "ozaki: at most 4 free and 4 summed modes per operand");
+      B.nr = nr;
+      B.nk = nk;
+      int64_t rows = 1, K = 1;
+      for (int m = 0; m < nr; ++m) {
+        B.rdim[m] = (int32_t)gemm.sp[r0 + m]->size[(size_t)gt[r0 + m]];
+        B.rstride[m] = (int32_t)stride[perm[r0 + m]];
+        rows *= B.rdim[m];
+      }
+      for (int m = 0; m < nk; ++m) {
+        B.kdim[m] = (int32_t)gemm.sp[k0 + m]->size[(size_t)gt[k0 + m]];
+        B.kstride[m] = (int32_t)stride[perm[k0 + m]];
+        K *= B.kdim[m];
+      }
+      if (rows > (1 << 30) || K > (1 << 30)) throw Error(TAMM_EUNSUPPORTED, "ozaki: block too large");
+      B.rows = (int32_t)rows;
+      B.K = (int32_t)K;
+      B.row_tiles = (int32_t)((rows + kOzTileM - 1) / kOzTileM);
+      B.k_tiles = (int32_t)((K + kOzTileK - 1) / kOzTileK);
+      B.k_contig = (nk > 0 && B.kstride[nk - 1] == 1) ? 1 : 0;
+      if (nk == 0) B.k_contig = 1;
+      B.tile_off = tiles;
+      B.exp_off = exps;
+      tiles += (int64_t)B.row_tiles * B.k_tiles;
+      exps += (int64_t)B.row_tiles * kOzTileM;
+      // rows per slicing CTA: a power of two <= 32 keeping a strip near 64 KB (k-contiguous),
+      // 32 rows when consecutive rows are the contiguous direction
+      int R = 32;
+      if (B.k_contig) {
+        R = 1;
+        while (R < 32 && (int64_t)(2 * R) * K * 8 <= 65536) R *= 2;
+      }
+      for (int32_t r = 0; r < B.row_tiles * kOzTileM; r += R) items.push_back({(int32_t)b, r, R, 0});
+    }
+  }
+
+  OzakiPlan(tamm_ctx* c, const tamm_tensor* C, const char* lc, const tamm_tensor* A, const char* la,
+            const tamm_tensor* B, const char* lb, int slices)
+      : Plan(c), lay(c, C, lc, A, la, B, lb), S(slices) {
+    ops_full = make_ops(S, true);
+    ops_ragged = make_ops(S, false);
+    const int nfl = (int)lay.free_left.size(), nfr = (int)lay.free_right.size(), nk = (int)lay.summed.size();
+    auto perm_of = [](const std::string& need, const std::string& have) {
+      std::vector<int> p(need.size());
+      for (size_t m = 0; m < need.size(); ++m) p[m] = (int)have.find(need[m]);
+      return p;
+    };
+    std::vector<SliceBlock> sa, sb;
+    std::vector<SliceItem> ia, ib;
+    int64_t ta = 0, tb = 0, ea = 0, eb = 0;
+    slice_blocks(*lay.left, lay.left_gemm(), perm_of(lay.need_left, lay.label_left), 0, nfl, nfl, nk, sa, ia, ta,
+                 ea);
+    slice_blocks(*lay.right, lay.right_gemm(), perm_of(lay.need_right, lay.label_right), nk, nfr, 0, nk, sb, ib,
+                 tb, eb);
+    auto align = [](size_t x) { return (x + 1023) & ~size_t(1023); };
+    const size_t tile_bytes = (size_t)S * kOzTileBytesPerSlice;
+    off_ta = 0;
+    scratch_bytes = align((size_t)ta * tile_bytes);
+    off_tb = scratch_bytes;
+    scratch_bytes += align((size_t)tb * tile_bytes);
+    off_ea = scratch_bytes;
+    scratch_bytes += align((size_t)ea * 4);
+    off_eb = scratch_bytes;
+    scratch_bytes += align((size_t)eb * 4);
+    if (lay.out_perm) {
+      const char* ls[1] = {lay.out_gemm.c_str()};
+      perm_out.reset(new AddPlan(c, *C, lay.label_c.c_str(), *lay.out_perm, 1, ls));
+      off_x = scratch_bytes;
+      scratch_bytes += align((size_t)lay.out_perm->n_elems * 8);
+    }
+    const tamm_tensor& O = lay.out_gemm_tensor();
+    std::vector<OzGroup> groups;
+    std::vector<OzTask> tasks;
+    std::vector<OzItem> items;
+    for (const auto& g : lay.groups) {
+      OzGroup gg;
+      gg.c_off = O.off[(size_t)g.out_block];
+      gg.M = (int32_t)g.M;
+      gg.N = (int32_t)g.N;
+      gg.task_begin = (int32_t)tasks.size();
+      int64_t Ksum = 0;
+      for (int64_t t = g.task_begin; t < g.task_end; ++t) {
+        const auto& tk = lay.tasks[(size_t)t];
+        const SliceBlock& A_ = sa[(size_t)tk.left_block];
+        const SliceBlock& B_ = sb[(size_t)tk.right_block];
+        if (A_.k_tiles != B_.k_tiles) throw Error(TAMM_EINVAL, "ozaki: K mismatch");
+        tasks.push_back({A_.tile_off, B_.tile_off, A_.exp_off, B_.exp_off, A_.k_tiles, 0});
+        Ksum += (int64_t)A_.k_tiles * kOzTileK;
+      }
+      // the double-float accumulator holds sums of |G0| <= Ksum * 64 * 64 far below 2^40
+      if (Ksum > (int64_t(1) << 26)) throw Error(TAMM_EUNSUPPORTED, "ozaki: summed extent too large");
+      gg.task_end = (int32_t)tasks.size();
+      const int32_t gi = (int32_t)groups.size();
+      groups.push_back(gg);
+      const int32_t mts = (gg.M + kOzTileM - 1) / kOzTileM, nts = (gg.N + kOzTileN - 1) / kOzTileN;
+      for (int32_t mt = 0; mt < mts; ++mt)
+        for (int32_t nt = 0; nt < nts; ++nt) items.push_back({gi, mt, nt, 0});
+    }
+    n_ia = (int64_t)ia.size();
+    n_ib = (int64_t)ib.size();
+    n_items = (int64_t)items.size();
+    d_sa = upload(sa);
+    d_ia = upload(ia);
+    d_sb = upload(sb);
+    d_ib = upload(ib);
+    d_groups = upload(groups);
+    d_tasks = upload(tasks);
+    d_items = upload(items);
+  }
+};
+
+void run_contract_ozaki(tamm_ctx* ctx, double alpha, tamm_tensor* C, const char* lc, double beta,
+                        const tamm_tensor* A, const char* la, const tamm_tensor* B, const char* lb, int slices) {
+  if (slices == 0) slices = kOzDefaultSlices;
+  if (slices < kOzMinSlices || slices > kOzMaxSlices)
+    throw Error(TAMM_EINVAL, "ozaki: slices must be %d..%d (0 = %d)", kOzMinSlices, kOzMaxSlices, kOzDefaultSlices);
+  const std::string key = "oz" + std::to_string(slices) + "|" + std::to_string(C->id) + "|" + lc + "|" +
+                          std::to_string(A->id) + "|" + la + "|" + std::to_string(B->id) + "|" + lb;
+  OzakiPlan* p;
+  auto itp = ctx->plans.find(key);
+  if (itp != ctx->plans.end()) {
+    p = static_cast<OzakiPlan*>(itp->second.get());
+  } else {
+    p = new OzakiPlan(ctx, C, lc, A, la, B, lb, slices);
+    ctx->plans[key].reset(p);
+  }
+  char* scratch = (char*)ctx_scratch(ctx, p->scratch_bytes);
+  uint8_t* ta = (uint8_t*)(scratch + p->off_ta);
+  uint8_t* tb = (uint8_t*)(scratch + p->off_tb);
+  int32_t* ea = (int32_t*)(scratch + p->off_ea);
+  int32_t* eb = (int32_t*)(scratch + p->off_eb);
+  const double* lp = p->lay.swap ? B->data : A->data;
+  const double* rp = p->lay.swap ? A->data : B->data;
+  cuda_check(launch_ozaki_slice(ctx, lp, p->d_sa, p->d_ia, p->n_ia, slices, ta, ea), "ozaki slice (left)");
+  cuda_check(launch_ozaki_slice(ctx, rp, p->d_sb, p->d_ib, p->n_ib, slices, tb, eb), "ozaki slice (right)");
+  double* out = p->perm_out ? (double*)(scratch + p->off_x) : C->data;
+  cuda_check(launch_ozaki_gemm(ctx, ta, tb, ea, eb, p->d_groups, p->d_tasks, p->d_items, p->n_items, slices,
+                               p->ops_full, p->ops_ragged, out, alpha, p->perm_out ? 0.0 : beta),
+             "ozaki gemm");
+  if (p->perm_out) {
+    const double one = 1.0;
+    p->perm_out->run(C->data, out, beta, &one);
+  }
+}
+
 }  // namespace tamm

@@ -1,0 +1,95 @@
+// Split-precision (Ozaki-style) block GEMMs on the tcgen05 tensor cores.
+//
+// Every FP64 operand row (A) / column (B) of a block is scaled by a power of
+// two 2^e with |x| < 2^e and cut into S balanced base-2^7 integer digits
+//     x = 2^(e-6) * sum_k d_k 2^(-7(k-1)),   |d_k| <= 64,
+// stored as BF16 values v_k = d_k 2^(-7(k-1)) (exact: at most 7 significant
+// bits).  Products of slices k,l (k+l <= S+1) run as BF16 MMAs with FP32
+// accumulation in TMEM, in four accumulator regions:
+//     G0: k+l=2, G1: k+l=3, G2: k+l=4 (each sums integer multiples of 2^-7G),
+//     G3: every k+l >= 5 (weighted tail, rounding allowed there).
+// A chunk of at most kOzChunkK summed indices keeps |G0|, |G1| 2^7, |G2| 2^14
+// below 3 * 1280 * 64 * 64 < 2^24, so G0..G2 are exact in FP32.  After each
+// chunk the epilogue scales the four partial sums by the chunk's power-of-two
+// row/column factors and folds them into a (hi, lo) FP32 pair, G0..G2 through
+// error-free TwoSum steps and G3 by a rounded add into lo; FP64 is used only
+// for the final reconstruction
+//     C = beta*C + alpha * 2^(Eref+Fref-12) * (hi + lo).
+#pragma once
+
+#include "tamm_contract.h"
+
+namespace tamm {
+
+constexpr int kOzTileM = 128;     // A-tile rows (MMA M)
+constexpr int kOzTileN = 128;     // B-tile rows = output columns per CTA
+constexpr int kOzTileK = 16;      // summed indices per tile (32 bytes of bf16)
+constexpr int kOzChunkK = 1280;   // summed indices per exact FP32 chunk
+constexpr int kOzChunkTiles = kOzChunkK / kOzTileK;
+constexpr int kOzMinSlices = 3;
+constexpr int kOzMaxSlices = 8;
+constexpr int kOzDefaultSlices = 6;
+constexpr int kOzTileBytesPerSlice = 128 * 32;  // 128 rows x 16 bf16
+constexpr int kOzExpZero = -30000;              // exponent of an all-zero (or padding) row
+constexpr int kOzMaxOps = 40;
+
+// One GEMM-order operand block to slice.  Rows are the output-side index
+// (M for A, N for B), K the summed index; native element (r, k) sits at
+//   src_off + sum_m r_m*rstride[m] + sum_m k_m*kstride[m]
+// with r, k decomposed row-major over rdim / kdim.
+struct SliceBlock {
+  int64_t src_off;
+  int64_t tile_off;  // first tile of this block in the sliced buffer (tiles ordered [row tile][k tile])
+  int64_t exp_off;   // exponent of row 0
+  int32_t rows, K;
+  int32_t row_tiles, k_tiles;
+  int32_t nr, nk;
+  int32_t rdim[4], rstride[4];
+  int32_t kdim[4], kstride[4];
+  int32_t k_contig;  // consecutive k are adjacent in memory (else consecutive rows are)
+  int32_t pad;
+};
+
+struct SliceItem {
+  int32_t block;
+  int32_t r0;  // first row (padding rows up to row_tiles*128 are written as zeros)
+  int32_t nr;
+  int32_t pad;
+};
+
+struct OzGroup {
+  int64_t c_off;
+  int32_t M, N;
+  int32_t task_begin, task_end;
+};
+
+struct OzTask {
+  int64_t a_tile, b_tile;  // first tile of the A / B block
+  int64_t a_exp, b_exp;    // exponent offsets of the A / B block
+  int32_t k_tiles;
+  int32_t pad;
+};
+
+struct OzItem {
+  int32_t group, mt, nt, pad;
+};
+
+// MMA schedule for one K step: A slice, first B slice, number of adjacent B
+// slices fused along N (1 or 2), accumulator region, and whether it is the
+// first write of its region(s) in a chunk.
+struct OzOp {
+  uint8_t a, b, nb, region, first;
+};
+struct OzOps {
+  int32_t n;
+  OzOp op[kOzMaxOps];
+};
+
+cudaError_t launch_ozaki_slice(tamm_ctx* ctx, const double* src, const SliceBlock* blocks, const SliceItem* items,
+                               int64_t n_items, int S, uint8_t* tiles, int32_t* exps);
+cudaError_t launch_ozaki_gemm(tamm_ctx* ctx, const uint8_t* a_tiles, const uint8_t* b_tiles, const int32_t* a_exp,
+                              const int32_t* b_exp, const OzGroup* groups, const OzTask* tasks, const OzItem* items,
+                              int64_t n_items, int S, const OzOps& full, const OzOps& ragged, double* c,
+                              double alpha, double beta);
+
+}  // namespace tamm
