@@ -1,0 +1,481 @@
+"""Benchmark: block-sparse contraction TFLOP/s, split precision vs FP64, on one GB300.
+
+One step = one pass of the whole hot path on the 40/240 spin-orbital
+coupled-cluster-doubles workload (tiles 20/40, spin block sparsity): vvvv
+ladder, W = W0 copy, intermediate W += V_oovv T, oooo ladder, ring term with
+the P(ab)P(ij) antisymmetriser, T1 term, and the energy.  The headline runs
+every contraction in split precision (six BF16 slices per FP64 operand on the
+tcgen05 tensor cores); an FP64 pass of the same step gives the FP64 rate and
+the split-precision error.  Throughput counts nonzero-block flops (2*M*N*K
+over every stored block pair), the same count for every precision.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Multi-GPU (torchrun, one rank per GPU): independent replicas of the step, one
+per GPU, no collective on the data path (weak scaling).  ``--impl reference``
+times the FP64 CPU oracle on bounded samples of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "block-sparse contraction TFLOP/s: split-precision vs FP64, rel err ≤1e-10"
+UNIT = "TFLOP/s"
+SLICES = 6
+# DRAM bytes per launch of the split-precision GEMM kernel from an ncu capture,
+# keyed by the hash of the kernel source it was taken on (null when it changed).
+MEASURED_TRAFFIC = {}
+
+
+def kernel_source_hash() -> str:
+    p = os.path.join(ROOT, "paper_2201_01257_gb300", "csrc", "ozaki.cu")
+    return hashlib.sha256(open(p, "rb").read()).hexdigest()[:16]
+
+
+def measured_peaks() -> dict:
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        d["_source"] = "measured"
+        return d
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "_source": "fallback"}
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self._t = threading.Thread(target=self._read, daemon=True)
+            self._t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        return False
+
+    def summary(self) -> dict:
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ ours
+
+def run_ours(args, rank: int, world: int) -> dict | None:
+    import torch
+
+    import paper_2201_01257_gb300 as tg
+    from paper_2201_01257_gb300 import workload as gw
+    from tamm_synth import workloads as wl
+    import tamm_synth
+
+    dev = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(dev)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device(f"cuda:{dev}"))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    w = wl.config2()
+    ctx = tg.Context(dev)
+    spaces, T = gw.build(ctx, w, fill=False)
+    host = {}
+    for name, spec in w.tensors.items():
+        if spec.sigma == 0.0:
+            continue
+        t = T[name]
+        h = torch.empty(t.n_elems, dtype=torch.float64, pin_memory=True)
+        lo, ext = t.block_lo_ext()
+        tamm_synth.fill_boxes(w.seed, spec.stream, spec.sigma, [m.n for m in t.modes], spec.anti01, spec.anti23,
+                              lo, ext, t.block_offsets, h.numpy())
+        host[name] = h
+        ctx.copy_from_host(t, h.numpy())
+    ctx.sync()
+    run = gw.Runner(ctx, w, spaces, T)
+    flops = sum(run.flops(s) for s in w.steps)
+    n_products = SLICES * (SLICES + 1) // 2
+    energy_dev = torch.zeros(1, dtype=torch.float64, device=f"cuda:{dev}")
+    stream = torch.cuda.current_stream()
+
+    def step(prec):
+        run.run("ozaki_bf16" if prec == "oz" else "f64", SLICES if prec == "oz" else 0,
+                energy_out=energy_dev.data_ptr())
+
+    # --- device-resident timed region (split precision) ---
+    for _ in range(args.warmup):
+        step("oz")
+    barrier()
+    ctx.profile_read()
+    ctx.profile(True)
+    l0 = ctx.launch_count()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(dev) as clocks:
+        barrier()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            step("oz")
+        ev1.record(stream)
+        barrier()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    launches = ctx.launch_count() - l0
+    ctx.profile(False)
+    prof = ctx.profile_read()
+    r_oz = T["R"].download()
+    w_oz = T["W"].download()
+    e_oz = float(energy_dev.item())
+
+    # --- FP64 pass of the same step: its rate and the split-precision error ---
+    step("f64")
+    ctx.sync()
+    f64_steps = max(1, min(2, args.steps))
+    ev2, ev3 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev2.record(stream)
+    for _ in range(f64_steps):
+        step("f64")
+    ev3.record(stream)
+    torch.cuda.synchronize()
+    ms_f64 = ev2.elapsed_time(ev3) / f64_steps
+    r_64, w_64, e_64 = T["R"].download(), T["W"].download(), float(energy_dev.item())
+    rel = lambda a, b: float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+    # --- end to end through the C ABI: pinned host inputs in, result out, every step ---
+    out_host = torch.empty(T["R"].n_elems, dtype=torch.float64, pin_memory=True)
+    e_host = torch.empty(1, dtype=torch.float64, pin_memory=True)
+    h2d = sum(T[k].n_elems * 8 for k in host)
+    d2h = T["R"].n_elems * 8 + 8
+
+    def e2e_step():
+        for k, h in host.items():
+            ctx.copy_from_host(T[k], h.numpy())
+        step("oz")
+        ctx.copy_to_host(T["R"], out_host.numpy())
+        e_host.copy_(energy_dev, non_blocking=True)
+
+    e2e_k = max(1, min(args.steps, 5))
+    e2e_step()
+    barrier()
+    ev4, ev5 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev4.record(stream)
+    for _ in range(e2e_k):
+        e2e_step()
+    ev5.record(stream)
+    barrier()
+    ms_e2e = ev4.elapsed_time(ev5) / e2e_k
+
+    # max over ranks
+    def max_all(x):
+        if dist is None:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device=f"cuda:{dev}")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    ms, ms_e2e, ms_f64 = max_all(ms), max_all(ms_e2e), max_all(ms_f64)
+    if dist is not None:
+        dist.destroy_process_group()
+    if rank != 0:
+        return None
+
+    peaks = measured_peaks()
+    gemm_ms, gemm_n = prof["gemm_ozaki"]
+    dominant = max(prof, key=lambda k: prof[k][0])
+    tensor_flops_per_step = flops * n_products  # BF16 slice products issued per step (algorithmic)
+    achieved = tensor_flops_per_step * args.steps / (gemm_ms * 1e-3) / 1e12 if gemm_ms else None
+    peak = peaks.get("bf16_tflops_sustained", 1700.0)
+    traffic = MEASURED_TRAFFIC.get(kernel_source_hash())
+    value = world * flops / (ms * 1e-3) / 1e12
+    return {
+        "metric": METRIC,
+        "value": round(value, 3),
+        "unit": UNIT,
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(ms, 3),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "bf16 slices (6 per f64 operand, f32 accumulate, f64 reconstruct)",
+        "data": "synthetic (seeded Philox normals, antisymmetrised; V~N(0,0.1), T~N(0,0.01))",
+        "config": {
+            "workload": "ccsd_doubles_O40_V240: vvvv ladder + W copy + intermediate + oooo ladder + ring with "
+                        "P(ab)P(ij) + T1 term + energy",
+            "O": 40, "V": 240, "tiles": [20, 40], "symmetry": "spin",
+            "precision": "ozaki_bf16", "slices": SLICES,
+            "nonzero_block_flops_per_step": flops,
+            "l2": "inputs larger than L2 (V_vvvv 9.95 GB per step)",
+            "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+        },
+        "f64": {"value": round(world * flops / (ms_f64 * 1e-3) / 1e12, 4), "unit": UNIT,
+                "ms_per_step": round(ms_f64, 2), "steps": f64_steps},
+        "speedup_vs_f64": round(ms_f64 / ms, 2),
+        "rel_err_vs_f64": {"R": rel(r_oz, r_64), "W": rel(w_oz, w_64), "energy": abs(e_oz - e_64) / abs(e_64)},
+        "e2e": {"value": round(world * flops / (ms_e2e * 1e-3) / 1e12, 3), "unit": UNIT,
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": round(ms_e2e, 3),
+                "steps": e2e_k},
+        "gpu_launches": launches,
+        "kernel_ms_per_step": {k: round(v[0] / args.steps, 3) for k, v in prof.items()},
+        "roofline": {
+            "kernel": "ozaki_gemm_kernel (tcgen05 BF16 slice products)",
+            "dominant_by_time": dominant,
+            "bound": "tensor",
+            "achieved": round(achieved, 2) if achieved else None,
+            "peak": peak,
+            "unit": "TFLOP/s",
+            "frac": round(achieved / peak, 4) if achieved else None,
+            "peak_source": f"{peaks['_source']} bf16_tflops_sustained",
+            "algorithmic_flops_per_launch": tensor_flops_per_step / max(1, gemm_n // max(1, args.steps)),
+            "avg_launch_ms": round(gemm_ms / gemm_n, 4) if gemm_n else None,
+            "traffic": traffic,
+        },
+        "clocks": clocks.summary(),
+        "cpu_baseline": cpu_baseline(seconds=args.cpu_seconds) if world == 1 or rank == 0 else None,
+    }
+
+
+# ---------------------------------------------------------- CPU (oracle)
+
+def oracle_sample(w, target_flops: float, seed: int = 0, box: int = 4):
+    """Oracle tensors with only the blocks a seeded sample needs filled, and the sample:
+    for every contraction, box^4 sub-boxes of randomly chosen output blocks.
+
+    Returns (tensors, [(step, cblocks, lo, ext)], total nonzero-block flops of the sample)."""
+    import itertools
+
+    import oracle as O
+    import tamm_synth
+    from tamm_synth import workloads as wl
+
+    spaces = {k: O.Space.from_spec(s) for k, s in w.spaces.items()}
+    T = {n: O.Tensor([spaces[m] for m in t.modes], t.n_upper, t.sym) for n, t in w.tensors.items()}
+    rng = np.random.default_rng(seed)
+    steps = [s for s in w.steps if isinstance(s, wl.ContractSpec)]
+    plan, need, total = [], {n: set() for n in T}, 0.0
+    per_step = target_flops / len(steps)
+    for s in steps:
+        C, A, B = T[s.c], T[s.a], T[s.b]
+        lab = {}
+        for X, l in ((C, s.lc), (A, s.la), (B, s.lb)):
+            for m, ch in enumerate(l):
+                lab[ch] = X.modes[m]
+        summed = [ch for ch in s.la if ch not in s.lc]
+        _, ext_all = C.block_lo_ext()
+        kcache = {}
+
+        def k_eff(cb):
+            if cb not in kcache:
+                tile = {ch: int(C.block_tiles[cb, m]) for m, ch in enumerate(s.lc)}
+                k, blocks = 0, []
+                for kt in itertools.product(*[range(lab[ch].n_tiles) for ch in summed]):
+                    tile.update(dict(zip(summed, kt)))
+                    ab = A.find_block([tile[ch] for ch in s.la])
+                    bb = B.find_block([tile[ch] for ch in s.lb])
+                    if ab < 0 or bb < 0:
+                        continue
+                    blocks.append((ab, bb))
+                    kk = 1
+                    for ch in summed:
+                        kk *= lab[ch].tiles[tile[ch]][1]
+                    k += kk
+                kcache[cb] = (k, blocks)
+            return kcache[cb]
+
+        cbs, los, exts, fl = [], [], [], 0.0
+        guard = 0
+        # boxes come from two output blocks per contraction, so few input blocks need filling
+        pool = [int(x) for x in rng.permutation(C.n_blocks)[:2]]
+        while fl < per_step and guard < 100000:
+            guard += 1
+            cb = pool[guard % len(pool)]
+            k, blocks = k_eff(cb)
+            if k == 0:
+                continue
+            ext = [min(box, int(e)) for e in ext_all[cb]]
+            lo = [int(rng.integers(0, int(e) - x + 1)) for e, x in zip(ext_all[cb], ext)]
+            cbs.append(cb)
+            los.append(lo)
+            exts.append(ext)
+            fl += 2.0 * float(np.prod(ext)) * k
+            for ab, bb in blocks:
+                need[s.a].add(ab)
+                need[s.b].add(bb)
+        plan.append((s, cbs, los, exts))
+        total += fl
+    for n, blocks in need.items():
+        if not blocks:
+            continue
+        spec = w.tensors[n]
+        if spec.sigma == 0.0:
+            continue
+        X = T[n]
+        lo, ext = X.block_lo_ext()
+        idx = np.array(sorted(blocks))
+        tamm_synth.fill_boxes(w.seed, spec.stream, spec.sigma, X.dense_shape(), spec.anti01, spec.anti23,
+                              lo[idx], ext[idx], X.block_off[idx], X.data)
+    return T, plan, total
+
+
+def time_oracle_sample(T, plan) -> float:
+    import oracle as O
+
+    t0 = time.perf_counter()
+    for s, cbs, los, exts in plan:
+        O.contract_boxes(s.alpha, T[s.c], s.lc, T[s.a], s.la, T[s.b], s.lb, cbs, los, exts)
+    return time.perf_counter() - t0
+
+
+def cpu_baseline(seconds: float = 15.0) -> dict:
+    """The FP64 oracle (as it stands) on a bounded sample of the same workload."""
+    from tamm_synth import workloads as wl
+
+    w = wl.config2()
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    # calibrate on a small sample, then size the timed sample to about `seconds`
+    T, plan, fl = oracle_sample(w, 1e9, seed=1)
+    dt = time_oracle_sample(T, plan)
+    T, plan, fl = oracle_sample(w, fl / max(dt, 1e-6) * seconds, seed=2)
+    dt = time_oracle_sample(T, plan)
+    return {"value": round(fl / dt / 1e12, 6), "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"FP64 oracle on seeded 4x4x4x4 sub-boxes of output blocks of each of the five "
+                      f"contractions of ccsd_doubles_O40_V240 ({fl:.3e} nonzero-block flops, {dt:.1f} s)",
+            "seconds": round(dt, 2)}
+
+
+def run_reference(args, rank: int) -> dict | None:
+    if rank != 0:
+        return None
+    from tamm_synth import workloads as wl
+
+    w = wl.config2()
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    T, plan, fl = oracle_sample(w, 1e9, seed=1)
+    dt = time_oracle_sample(T, plan)
+    per_step_flops = fl / dt * args.ref_seconds
+    T, plan, fl = oracle_sample(w, per_step_flops, seed=3)
+    for _ in range(args.warmup):
+        time_oracle_sample(T, plan)
+    times = [time_oracle_sample(T, plan) for _ in range(args.steps)]
+    ms = 1e3 * float(np.sum(times)) / args.steps
+    value = fl / (ms * 1e-3) / 1e12
+    sample = (f"FP64 oracle on seeded 4x4x4x4 sub-boxes of output blocks of the five contractions of "
+              f"ccsd_doubles_O40_V240 ({fl:.3e} nonzero-block flops per step)")
+    return {"impl": "reference", "metric": METRIC, "value": round(value, 6), "unit": UNIT, "n_gpus": 0,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 2), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "ccsd_doubles_O40_V240 (bounded sample per step)", "O": 40, "V": 240,
+                       "tiles": [20, 40], "precision": "f64 (CPU oracle)"},
+            "cpu_baseline": {"value": round(value, 6), "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": round(value, 6), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def run_ladder_case(args) -> dict:
+    """A single split-precision vvvv ladder at a chosen size (small cases for profiling)."""
+    import torch
+
+    import paper_2201_01257_gb300 as tg
+    from paper_2201_01257_gb300 import workload as gw
+    from tamm_synth import workloads as wl
+
+    O_, V_ = (int(x) for x in args.ladder.split(","))
+    w = wl._doubles(wl._vt(2, O_, V_, 20, 40, f"ladder_O{O_}_V{V_}"))
+    ctx = tg.Context(0)
+    _, T = gw.build(ctx, w, only={"V_vvvv", "T", "R"})
+    fl = ctx.flops(T["R"], "abij", T["V_vvvv"], "abef", T["T"], "efij")
+    go = lambda: ctx.contract(0.5, T["R"], "abij", 0.0, T["V_vvvv"], "abef", T["T"], "efij", "ozaki_bf16", SLICES)
+    for _ in range(args.warmup):
+        go()
+    ctx.sync()
+    s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s.record()
+    for _ in range(args.steps):
+        go()
+    e.record()
+    ctx.sync()
+    ms = s.elapsed_time(e) / args.steps
+    return {"case": f"vvvv ladder O={O_} V={V_} tiles 20/40, split precision", "ms": round(ms, 3),
+            "TFLOP/s": round(fl / ms / 1e9, 3), "nonzero_block_flops": fl}
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0, help="size of the CPU-baseline sample")
+    ap.add_argument("--ref-seconds", type=float, default=6.0, help="CPU work per reference-arm step")
+    ap.add_argument("--ladder", default="", help="O,V: time one split-precision ladder of that size instead")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if args.ladder:
+        out = run_ladder_case(args)
+    elif args.impl == "reference":
+        out = run_reference(args, rank)
+    else:
+        out = run_ours(args, rank, world)
+    if out is not None:
+        print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -95,6 +95,23 @@ TAMM_API tamm_status tamm_ctx_set_stream(tamm_ctx* ctx, void* stream);
 TAMM_API void tamm_ctx_destroy(tamm_ctx* ctx);
 /* Message of the last failed call on this context ("" if none); owned by ctx. */
 TAMM_API const char* tamm_last_error(const tamm_ctx* ctx);
+/* Kernel classes for launch counting and timing. */
+#define TAMM_KERNEL_ADD 0       /* permuted add / operand and output permutation */
+#define TAMM_KERNEL_REDUCE 1    /* energy and norm partial sums and final reduction */
+#define TAMM_KERNEL_GEMM_F64 2  /* FP64 block GEMM */
+#define TAMM_KERNEL_SLICE 3     /* split-precision operand slicing */
+#define TAMM_KERNEL_GEMM_OZ 4   /* split-precision tcgen05 block GEMM */
+#define TAMM_KERNEL_CLASSES 5
+/* Number of kernels this context has launched since creation. */
+TAMM_API tamm_status tamm_ctx_launch_count(const tamm_ctx* ctx, int64_t* launches);
+/* enable != 0: bracket every later kernel launch with CUDA events on the
+ * context's stream.  enable == 0 stops recording.  Recorded times are kept until
+ * read. */
+TAMM_API tamm_status tamm_ctx_profile(tamm_ctx* ctx, int enable);
+/* Synchronise, then return and clear, per kernel class (TAMM_KERNEL_*), the
+ * summed device time in milliseconds and the number of timed launches.
+ * `ms` and `launches` hold TAMM_KERNEL_CLASSES entries (either may be NULL). */
+TAMM_API tamm_status tamm_ctx_profile_read(tamm_ctx* ctx, double* ms, int64_t* launches);
 /* Synchronise the stream and report any device-side status (TAMM_ETIMEOUT,
  * TAMM_ECHECK) recorded since the last synchronising call, then clear it. */
 TAMM_API tamm_status tamm_sync(tamm_ctx* ctx);
@@ -148,6 +165,13 @@ TAMM_API tamm_status tamm_tensor_blocks(const tamm_tensor* t, int64_t* block_til
 TAMM_API tamm_status tamm_tensor_bind(tamm_tensor* t, double* device_data);
 /* Allocate n_elems doubles through the context allocator (freed by destroy). */
 TAMM_API tamm_status tamm_tensor_allocate(tamm_tensor* t);
+/* Copy the tensor's n_elems doubles from / to host memory, enqueued on the
+ * context's stream (asynchronous when the host buffer is page-locked, e.g.
+ * cudaMallocHost; pageable buffers make the copy synchronous).  The host buffer
+ * uses the same packed block layout as the device data.  Errors: TAMM_EINVAL,
+ * TAMM_ECUDA. */
+TAMM_API tamm_status tamm_tensor_copy_from_host(tamm_ctx* ctx, tamm_tensor* t, const double* host);
+TAMM_API tamm_status tamm_tensor_copy_to_host(tamm_ctx* ctx, const tamm_tensor* t, double* host);
 /* Device pointer of the tensor's packed data (NULL if unbound). */
 TAMM_API double* tamm_tensor_data(const tamm_tensor* t);
 /* NULL is ignored.  Storage obtained by tamm_tensor_allocate is released

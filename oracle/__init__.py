@@ -65,6 +65,8 @@ def _load(path: str | None = None):
             L.oracle_tensor_find_block.argtypes = [vp, i64p]
             L.oracle_tensor_find_block.restype = i64
             L.oracle_contract.argtypes = [d, vp, cp, d, vp, cp, vp, cp, dp, dp, dp]
+            L.oracle_contract_blocks.argtypes = [d, vp, cp, d, vp, cp, vp, cp, dp, dp, dp, i64p, i64]
+            L.oracle_contract_boxes.argtypes = [d, vp, cp, vp, cp, vp, cp, dp, dp, i64, i64p, i64p, i64p, i64p, dp]
             L.oracle_contract_box.argtypes = [d, vp, cp, d, vp, cp, vp, cp, dp, dp, i64, i64p, i64p, dp, dp]
             L.oracle_add.argtypes = [d, vp, cp, d, vp, cp, dp, dp]
             L.oracle_energy.argtypes = [d, vp, cp, vp, cp, dp, dp, dp]
@@ -231,6 +233,14 @@ def contract(alpha: float, C: Tensor, lc: str, beta: float, A: Tensor, la: str, 
                                  _pd(C.data), _pd(A.data), _pd(B.data)), "contract")
 
 
+def contract_blocks(alpha: float, C: Tensor, lc: str, beta: float, A: Tensor, la: str, B: Tensor, lb: str,
+                    blocks) -> None:
+    """The contraction restricted to the listed stored blocks of C (in place)."""
+    bl = _i64(blocks)
+    _chk(_load().oracle_contract_blocks(alpha, C._h, lc.encode(), beta, A._h, la.encode(), B._h, lb.encode(),
+                                        _pd(C.data), _pd(A.data), _pd(B.data), _p(bl), len(bl)), "contract_blocks")
+
+
 def contract_box(alpha: float, C: Tensor, lc: str, beta: float, A: Tensor, la: str, B: Tensor, lb: str,
                  cblock: int, lo, ext, c_in: np.ndarray | None = None) -> np.ndarray:
     """Values of the box [lo, lo+ext) of stored C block ``cblock`` after the contraction."""
@@ -241,6 +251,21 @@ def contract_box(alpha: float, C: Tensor, lc: str, beta: float, A: Tensor, la: s
                                      _pd(A.data), _pd(B.data), int(cblock), _p(lo), _p(ext), _pd(cin), _pd(out)),
          "contract_box")
     return out.reshape(tuple(ext))
+
+
+def contract_boxes(alpha: float, C: Tensor, lc: str, A: Tensor, la: str, B: Tensor, lb: str, cblocks, lo,
+                   ext) -> list:
+    """Several boxes of stored C blocks (beta = 0), evaluated in parallel; returns one array per box."""
+    cb = _i64(cblocks)
+    lo = _i64(lo).reshape(len(cb), C.nm)
+    ext = _i64(ext).reshape(len(cb), C.nm)
+    sizes = ext.prod(axis=1)
+    off = _i64(np.concatenate([[0], np.cumsum(sizes)[:-1]]) if len(cb) else [])
+    out = np.zeros(int(sizes.sum()) if len(cb) else 1)
+    _chk(_load().oracle_contract_boxes(alpha, C._h, lc.encode(), A._h, la.encode(), B._h, lb.encode(), _pd(A.data),
+                                       _pd(B.data), len(cb), _p(cb), _p(lo), _p(ext), _p(off), _pd(out)),
+         "contract_boxes")
+    return [out[o:o + n].reshape(tuple(e)) for o, n, e in zip(off, sizes, ext)]
 
 
 def add(alpha: float, C: Tensor, lc: str, beta: float, A: Tensor, la: str) -> None:

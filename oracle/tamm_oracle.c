@@ -414,6 +414,34 @@ int oracle_contract(double alpha, const otensor* C, const char* lc, double beta,
   return err;
 }
 
+/* Like oracle_contract, restricted to the listed stored C blocks (others untouched). */
+int oracle_contract_blocks(double alpha, const otensor* C, const char* lc, double beta, const otensor* A,
+                           const char* la, const otensor* B, const char* lb, double* c, const double* a,
+                           const double* b, const int64_t* blocks, int64_t n_blocks) {
+  cplan P;
+  if (contract_plan(&P, C, lc, A, la, B, lb)) return OR_EINVAL;
+  for (int64_t i = 0; i < n_blocks; ++i)
+    if (blocks[i] < 0 || blocks[i] >= C->n_blocks) return OR_EINVAL;
+  int err = OR_OK;
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int64_t i = 0; i < n_blocks; ++i) {
+    const int64_t cb = blocks[i];
+    int64_t lo[OR_MAX_MODES], ext[OR_MAX_MODES];
+    const int64_t* ct = C->tiles + cb * C->nm;
+    for (int m = 0; m < C->nm; ++m) {
+      lo[m] = 0;
+      ext[m] = C->sp[m]->size[ct[m]];
+    }
+    double* cblk = c + C->off[cb];
+    int e = contract_box(&P, alpha, C, beta, A, B, a, b, cb, lo, ext, cblk, cblk);
+    if (e) {
+#pragma omp atomic write
+      err = e;
+    }
+  }
+  return err;
+}
+
 /* One box of one C block; c_box_in holds the box's current C values (ignored when beta == 0). */
 int oracle_contract_box(double alpha, const otensor* C, const char* lc, double beta, const otensor* A,
                         const char* la, const otensor* B, const char* lb, const double* a, const double* b,
@@ -423,6 +451,29 @@ int oracle_contract_box(double alpha, const otensor* C, const char* lc, double b
   if (contract_plan(&P, C, lc, A, la, B, lb)) return OR_EINVAL;
   if (cb < 0 || cb >= C->n_blocks) return OR_EINVAL;
   return contract_box(&P, alpha, C, beta, A, B, a, b, cb, lo, ext, c_box_in, out);
+}
+
+/* Many boxes at once (OpenMP over boxes): box i is [lo[i], lo[i]+ext[i]) of C
+ * block cblocks[i], written row-major at out + out_off[i] (beta taken as 0). */
+int oracle_contract_boxes(double alpha, const otensor* C, const char* lc, const otensor* A, const char* la,
+                          const otensor* B, const char* lb, const double* a, const double* b, int64_t n_boxes,
+                          const int64_t* cblocks, const int64_t* lo, const int64_t* ext, const int64_t* out_off,
+                          double* out) {
+  cplan P;
+  if (contract_plan(&P, C, lc, A, la, B, lb)) return OR_EINVAL;
+  int err = OR_OK;
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int64_t i = 0; i < n_boxes; ++i) {
+    int e = OR_EINVAL;
+    if (cblocks[i] >= 0 && cblocks[i] < C->n_blocks)
+      e = contract_box(&P, alpha, C, 0.0, A, B, a, b, cblocks[i], lo + i * C->nm, ext + i * C->nm, NULL,
+                       out + out_off[i]);
+    if (e) {
+#pragma omp atomic write
+      err = e;
+    }
+  }
+  return err;
 }
 
 /* --------------------------------------------------------------------- add */

@@ -26,6 +26,7 @@ _lib = None
 TAMM_OK, TAMM_EINVAL, TAMM_ENOMEM, TAMM_ECUDA, TAMM_EUNSUPPORTED, TAMM_ETIMEOUT, TAMM_ECHECK = range(7)
 TAMM_SYM_DENSE, TAMM_SYM_SPIN, TAMM_SYM_SPIN_IRREP = 0, 1, 2
 TAMM_PREC_F64, TAMM_PREC_OZAKI_BF16, TAMM_PREC_OZAKI_I8 = 0, 1, 2
+KERNEL_CLASSES = ("add", "reduce", "gemm_f64", "slice", "gemm_ozaki")
 SYM = {"dense": TAMM_SYM_DENSE, "spin": TAMM_SYM_SPIN, "spin_irrep": TAMM_SYM_SPIN_IRREP}
 PREC = {"f64": TAMM_PREC_F64, "ozaki_bf16": TAMM_PREC_OZAKI_BF16, "ozaki_i8": TAMM_PREC_OZAKI_I8}
 STATUS_NAMES = {0: "TAMM_OK", 1: "TAMM_EINVAL", 2: "TAMM_ENOMEM", 3: "TAMM_ECUDA", 4: "TAMM_EUNSUPPORTED",
@@ -44,6 +45,9 @@ PROTOTYPES = [
     ("tamm_ctx_destroy", None, [_vp]),
     ("tamm_last_error", _cp, [_vp]),
     ("tamm_sync", _i, [_vp]),
+    ("tamm_ctx_launch_count", _i, [_vp, _i64p]),
+    ("tamm_ctx_profile", _i, [_vp, _i]),
+    ("tamm_ctx_profile_read", _i, [_vp, _dp, _i64p]),
     ("tamm_space_create", _i, [_vp, _i, _i64p, _ip, _ip, _i, _i64p, _i64, ctypes.POINTER(_vp)]),
     ("tamm_space_info", _i, [_vp, _ip, _i64p]),
     ("tamm_space_tiles", _i, [_vp, _i64p, _i64p, _ip, _ip]),
@@ -54,6 +58,8 @@ PROTOTYPES = [
     ("tamm_tensor_blocks", _i, [_vp, _i64p, _i64p]),
     ("tamm_tensor_bind", _i, [_vp, _vp]),
     ("tamm_tensor_allocate", _i, [_vp]),
+    ("tamm_tensor_copy_from_host", _i, [_vp, _vp, _vp]),
+    ("tamm_tensor_copy_to_host", _i, [_vp, _vp, _vp]),
     ("tamm_tensor_data", _vp, [_vp]),
     ("tamm_tensor_destroy", None, [_vp]),
     ("tamm_contract", _i, [_vp, _d, _vp, _cp, _d, _vp, _cp, _vp, _cp, _i, _i]),
@@ -220,6 +226,31 @@ class Context:
 
     def sync(self) -> None:
         self.check(self.lib.tamm_sync(self.handle), "tamm_sync")
+
+    def launch_count(self) -> int:
+        n = ctypes.c_int64()
+        self.check(self.lib.tamm_ctx_launch_count(self.handle, ctypes.byref(n)), "tamm_ctx_launch_count")
+        return n.value
+
+    def profile(self, enable: bool) -> None:
+        self.check(self.lib.tamm_ctx_profile(self.handle, int(enable)), "tamm_ctx_profile")
+
+    def profile_read(self) -> dict:
+        """{kernel class: (total ms, launches)} recorded since the last read."""
+        n = len(KERNEL_CLASSES)
+        ms, cnt = (ctypes.c_double * n)(), (ctypes.c_int64 * n)()
+        self.check(self.lib.tamm_ctx_profile_read(self.handle, ms, cnt), "tamm_ctx_profile_read")
+        return {k: (ms[i], cnt[i]) for i, k in enumerate(KERNEL_CLASSES)}
+
+    def copy_from_host(self, T, host: np.ndarray) -> None:
+        assert host.dtype == np.float64 and host.flags.c_contiguous and host.size >= T.n_elems
+        self.check(self.lib.tamm_tensor_copy_from_host(self.handle, T.handle, ctypes.c_void_p(host.ctypes.data)),
+                   "tamm_tensor_copy_from_host")
+
+    def copy_to_host(self, T, host: np.ndarray) -> None:
+        assert host.dtype == np.float64 and host.flags.c_contiguous and host.size >= T.n_elems
+        self.check(self.lib.tamm_tensor_copy_to_host(self.handle, T.handle, ctypes.c_void_p(host.ctypes.data)),
+                   "tamm_tensor_copy_to_host")
 
 
 class Space:

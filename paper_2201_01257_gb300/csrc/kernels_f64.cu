@@ -191,27 +191,35 @@ cudaError_t launch_add(tamm_ctx* ctx, double* dst, const double* src, const AddB
   if (n_items == 0) return cudaSuccess;
   Alpha4 al{};
   for (int t = 0; t < n_terms; ++t) al.v[t] = alpha_host[t];
+  kernel_begin(ctx, TAMM_KERNEL_ADD);
   add_kernel<<<(unsigned)n_items, 256, 0, ctx->stream>>>(dst, src, blocks, items, n_terms, beta, al);
+  kernel_end(ctx, TAMM_KERNEL_ADD);
   return cudaGetLastError();
 }
 
 cudaError_t launch_energy_partials(tamm_ctx* ctx, const double* a, const double* b, const AddBlock* blocks,
                                    const ChunkItem* items, int64_t n_items, double* partials) {
   if (n_items == 0) return cudaSuccess;
+  kernel_begin(ctx, TAMM_KERNEL_REDUCE);
   energy_partials_kernel<<<(unsigned)n_items, 256, 0, ctx->stream>>>(a, b, blocks, items, partials);
+  kernel_end(ctx, TAMM_KERNEL_REDUCE);
   return cudaGetLastError();
 }
 
 cudaError_t launch_sumsq_partials(tamm_ctx* ctx, const double* x, int64_t n, double* partials, int64_t n_parts) {
   if (n_parts == 0) return cudaSuccess;
   const int64_t per = (n + n_parts - 1) / n_parts;
+  kernel_begin(ctx, TAMM_KERNEL_REDUCE);
   sumsq_partials_kernel<<<(unsigned)n_parts, 256, 0, ctx->stream>>>(x, n, per, partials);
+  kernel_end(ctx, TAMM_KERNEL_REDUCE);
   return cudaGetLastError();
 }
 
 cudaError_t launch_reduce_final(tamm_ctx* ctx, const double* partials, int64_t n, double alpha, int take_sqrt,
                                 double* out_device) {
+  kernel_begin(ctx, TAMM_KERNEL_REDUCE);
   reduce_final_kernel<<<1, 1024, 0, ctx->stream>>>(partials, n, alpha, take_sqrt, out_device);
+  kernel_end(ctx, TAMM_KERNEL_REDUCE);
   return cudaGetLastError();
 }
 
@@ -219,7 +227,9 @@ cudaError_t launch_gemm_f64(tamm_ctx* ctx, const double* a, const double* b, dou
                             const GemmTask* tasks, const GemmItem* items, int64_t n_items, double alpha,
                             double beta) {
   if (n_items == 0) return cudaSuccess;
+  kernel_begin(ctx, TAMM_KERNEL_GEMM_F64);
   gemm_f64_kernel<<<(unsigned)n_items, 256, 0, ctx->stream>>>(a, b, c, groups, tasks, items, alpha, beta);
+  kernel_end(ctx, TAMM_KERNEL_GEMM_F64);
   return cudaGetLastError();
 }
 

@@ -465,7 +465,9 @@ __global__ void __launch_bounds__(kThreads, 1) ozaki_gemm_kernel(const __grid_co
 cudaError_t launch_ozaki_slice(tamm_ctx* ctx, const double* src, const SliceBlock* blocks, const SliceItem* items,
                                int64_t n_items, int S, uint8_t* tiles, int32_t* exps) {
   if (n_items == 0) return cudaSuccess;
+  kernel_begin(ctx, TAMM_KERNEL_SLICE);
   ozaki_slice_kernel<<<(unsigned)n_items, 256, 0, ctx->stream>>>(src, blocks, items, S, tiles, exps);
+  kernel_end(ctx, TAMM_KERNEL_SLICE);
   return cudaGetLastError();
 }
 
@@ -508,7 +510,9 @@ cudaError_t launch_ozaki_gemm(tamm_ctx* ctx, const uint8_t* a_tiles, const uint8
   }
   cudaError_t e = cudaFuncSetAttribute(ozaki_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
+  kernel_begin(ctx, TAMM_KERNEL_GEMM_OZ);
   ozaki_gemm_kernel<<<(unsigned)n_items, kThreads, smem, ctx->stream>>>(p);
+  kernel_end(ctx, TAMM_KERNEL_GEMM_OZ);
   return cudaGetLastError();
 }
 

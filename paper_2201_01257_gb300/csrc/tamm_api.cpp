@@ -175,6 +175,11 @@ extern "C" void tamm_ctx_destroy(tamm_ctx* ctx) {
   ctx_free(ctx, ctx->d_status, 256);
   cudaStreamSynchronize(ctx->stream);
   if (ctx->h_result) cudaFreeHost(ctx->h_result);
+  for (auto& t : ctx->timed) {
+    cudaEventDestroy(t.start);
+    cudaEventDestroy(t.stop);
+  }
+  for (auto e : ctx->event_pool) cudaEventDestroy(e);
   (void)cudaGetLastError();
   delete ctx;
 }
@@ -415,6 +420,28 @@ extern "C" tamm_status tamm_tensor_allocate(tamm_tensor* t) {
     t->data = (double*)ctx_alloc(t->ctx, bytes);
     t->owned = true;
     t->owned_bytes = bytes;
+  });
+}
+
+extern "C" tamm_status tamm_tensor_copy_from_host(tamm_ctx* ctx, tamm_tensor* t, const double* host) {
+  if (!ctx || !t) return TAMM_EINVAL;
+  return guarded(ctx, [&] {
+    require_device(ctx);
+    if (!host || (t->n_elems && !t->data)) throw Error(TAMM_EINVAL, "copy: null buffer or unbound tensor");
+    cuda_check(cudaMemcpyAsync(t->data, host, (size_t)t->n_elems * sizeof(double), cudaMemcpyHostToDevice,
+                               ctx->stream),
+               "host to device copy");
+  });
+}
+
+extern "C" tamm_status tamm_tensor_copy_to_host(tamm_ctx* ctx, const tamm_tensor* t, double* host) {
+  if (!ctx || !t) return TAMM_EINVAL;
+  return guarded(ctx, [&] {
+    require_device(ctx);
+    if (!host || (t->n_elems && !t->data)) throw Error(TAMM_EINVAL, "copy: null buffer or unbound tensor");
+    cuda_check(cudaMemcpyAsync(host, t->data, (size_t)t->n_elems * sizeof(double), cudaMemcpyDeviceToHost,
+                               ctx->stream),
+               "device to host copy");
   });
 }
 

@@ -122,9 +122,21 @@ struct tamm_ctx {
   std::map<std::string, std::unique_ptr<tamm::Plan>> plans;
   int sm_count = 0;
   bool host_only = false;  // device -1: metadata and planning only
+  int64_t launches = 0;    // kernels launched by this context
+  bool profiling = false;  // bracket launches with CUDA events
+  struct TimedLaunch {
+    int kind;
+    cudaEvent_t start, stop;
+  };
+  std::vector<TimedLaunch> timed;
+  std::vector<cudaEvent_t> event_pool;
 };
 
 namespace tamm {
+
+// Launch bookkeeping: call around every kernel launch (counts, optional event timing).
+void kernel_begin(tamm_ctx* ctx, int kind);
+void kernel_end(tamm_ctx* ctx, int kind);
 
 // allocation through the context allocator (stream-ordered)
 void* ctx_alloc(tamm_ctx* ctx, size_t bytes);

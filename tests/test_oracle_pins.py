@@ -342,3 +342,28 @@ def test_pins_catch_planted_oracle_mistakes(mutant, tmp_path):
     with O.using_library(str(lib)):
         caught = not _pins_hold()
     assert caught, f"planted mistake {mutant!r} was not caught"
+
+
+def test_contract_blocks_matches_full(small):
+    _, T = small
+    R1 = O.Tensor(T["R"].modes, 2)
+    R2 = O.Tensor(T["R"].modes, 2)
+    O.contract(0.5, R1, "abij", 0.0, T["V_vvvv"], "abef", T["T"], "efij")
+    pick = [1, 5, R1.n_blocks - 1]
+    O.contract_blocks(0.5, R2, "abij", 0.0, T["V_vvvv"], "abef", T["T"], "efij", pick)
+    for b in range(R1.n_blocks):
+        if b in pick:
+            assert np.array_equal(R2.block_view(b), R1.block_view(b))
+        else:
+            assert not R2.block_view(b).any()
+
+
+def test_contract_boxes_match_single_box(small):
+    _, T = small
+    R = O.Tensor(T["R"].modes, 2)
+    boxes = [(0, [0, 0, 0, 0], [2, 3, 1, 2]), (R.n_blocks - 1, [1, 1, 0, 0], [2, 2, 2, 2])]
+    outs = O.contract_boxes(0.5, R, "abij", T["V_vvvv"], "abef", T["T"], "efij", [b[0] for b in boxes],
+                            [b[1] for b in boxes], [b[2] for b in boxes])
+    for (b, lo, ext), got in zip(boxes, outs):
+        ref = O.contract_box(0.5, R, "abij", 0.0, T["V_vvvv"], "abef", T["T"], "efij", b, lo, ext)
+        assert np.array_equal(got, ref)
