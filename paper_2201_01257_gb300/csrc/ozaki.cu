@@ -14,51 +14,66 @@ namespace tamm {
 // ======================================================================
 namespace {
 
-// bf16 bits of d * 2^(-7k), |d| <= 64 (exact).
-__device__ __forceinline__ uint32_t bf16_digit(int d, int k) {
+// bf16 bits of d (|d| <= 64), exact; the slice-k value d * 2^(-7k) subtracts 7k from the exponent.
+__host__ __device__ constexpr uint32_t bf16_of_small_int(int d) {
   if (d == 0) return 0u;
   const uint32_t s = d < 0 ? 0x8000u : 0u;
   const uint32_t a = (uint32_t)(d < 0 ? -d : d);
-  const int p = 31 - __clz(a);  // 0..6
-  const uint32_t e = (uint32_t)(127 + p - 7 * k);
-  const uint32_t m = (a << (7 - p)) & 0x7Fu;
-  return s | (e << 7) | m;
+  int p = 0;
+  while ((a >> (p + 1)) != 0u) ++p;  // floor(log2 a), 0..6
+  return s | ((uint32_t)(127 + p) << 7) | ((a << (7 - p)) & 0x7Fu);
 }
 
-// Balanced base-2^7 digits of x / 2^(e-6) (first digit 6 bits), S digits,
-// from the FP64 bit pattern with integer arithmetic only.
-__device__ __forceinline__ void digits_of(double x, int e, int S, int (&d)[kOzMaxSlices]) {
+__host__ __device__ constexpr unsigned long long digit_bias(int S) {
+  unsigned long long b = 0;
+  for (int j = 0; j + 1 < S; ++j) b |= 64ull << (7 * j);
+  return b;
+}
+
+// Balanced base-2^7 digits of x / 2^(e-6), S of them (first digit 6 bits):
+// F = round(|x| 2^(7S-1-e)) from the FP64 bit pattern.  Adding 64 to every
+// lower digit position, G = F + 64 (1 + 2^7 + ... + 2^(7(S-2))), makes the
+// balanced digits plain fields: d_k = field_k(G) - 64 (k >= 2), d_1 = G >> 7(S-1).
+template <int S>
+__device__ __forceinline__ void digits_of(double x, int e, int (&d)[S]) {
 #pragma unroll
-  for (int k = 0; k < kOzMaxSlices; ++k) d[k] = 0;
+  for (int k = 0; k < S; ++k) d[k] = 0;
   const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
-  const bool neg = (bits >> 63) != 0;
   int E = (int)((bits >> 52) & 0x7FF);
   unsigned long long M = bits & ((1ull << 52) - 1);
   if (E == 0) E = 1; else M |= 1ull << 52;
-  if (M == 0 || e == kOzExpZero) return;
-  // |x| = M 2^(E-1075);  F = round(|x| 2^(7S-1-e))
   const int shift = E - 1075 + 7 * S - 1 - e;
-  long long F;
+  if (M == 0 || shift <= -63) return;
+  unsigned long long F;
   if (shift >= 0) {
-    F = (long long)(M << shift);
-  } else if (shift > -63) {
-    const int rs = -shift;
-    F = (long long)((M >> rs) + ((M >> (rs - 1)) & 1ull));
+    F = M << shift;
   } else {
-    return;
+    const int rs = -shift;
+    F = (M >> rs) + ((M >> (rs - 1)) & 1ull);
   }
+  constexpr unsigned long long kBias = digit_bias(S);
+  const unsigned long long G = F + kBias;
+  const uint32_t lo = (uint32_t)G, hi = (uint32_t)(G >> 32);
 #pragma unroll
-  for (int k = kOzMaxSlices - 1; k >= 1; --k) {
-    if (k < S) {
-      const int dk = (int)((F + 64) & 127) - 64;
-      d[k] = dk;
-      F = (F - dk) >> 7;
-    }
+  for (int k = 1; k < S; ++k) {
+    const int sh = 7 * (S - 1 - k);
+    uint32_t u;
+    if (sh + 7 <= 32) u = (lo >> sh) & 127u;
+    else if (sh >= 32) u = (hi >> (sh - 32)) & 127u;
+    else u = ((lo >> sh) | (hi << (32 - sh))) & 127u;
+    d[k] = (int)u - 64;
   }
-  d[0] = (int)F;
-  if (neg) {
+  {
+    constexpr int sh = 7 * (S - 1);
+    uint32_t u;
+    if constexpr (sh >= 32) u = hi >> (sh - 32);
+    else if constexpr (sh == 0) u = lo;
+    else u = (lo >> sh) | (hi << (32 - sh));
+    d[0] = (int)u;
+  }
+  if (bits >> 63) {
 #pragma unroll
-    for (int k = 0; k < kOzMaxSlices; ++k) d[k] = -d[k];
+    for (int k = 0; k < S; ++k) d[k] = -d[k];
   }
 }
 
@@ -99,35 +114,153 @@ __device__ __forceinline__ void k_offsets8(const SliceBlock& B, int32_t k0, int6
   }
 }
 
+template <int S>
+__device__ __forceinline__ void pack_digits(const double x0, const double x1, int e, uint32_t (&w)[S],
+                                            const uint32_t* lut) {
+  int d0[S], d1[S];
+  digits_of<S>(x0, e, d0);
+  digits_of<S>(x1, e, d1);
+#pragma unroll
+  for (int s = 0; s < S; ++s) {
+    const uint32_t v0 = lut[d0[s] + 64], v1 = lut[d1[s] + 64];
+    const uint32_t sub = (uint32_t)(7 * s << 7);
+    w[s] = (v0 ? v0 - sub : 0u) | ((v1 ? v1 - sub : 0u) << 16);
+  }
+}
+
+// One CTA slices rows [r0, r0+nr) of one block.
+// Dense summed range: the strip is brought into shared memory by 1-D bulk
+// copies (one per row), row maxima come from warp reductions, and each lane
+// turns two consecutive elements into one 32-bit word per slice, so shared
+// reads are conflict-free and every warp store fills whole 32-byte sectors.
+// Other layouts: 8-wide units read straight from global memory twice, lanes
+// walking rows fastest so that the contiguous direction is coalesced.
+template <int S>
 __global__ void __launch_bounds__(256) ozaki_slice_kernel(const double* __restrict__ src,
                                                           const SliceBlock* __restrict__ blocks,
-                                                          const SliceItem* __restrict__ items, int S,
-                                                          uint8_t* __restrict__ tiles, int32_t* __restrict__ exps) {
-  const SliceItem it = items[blockIdx.x];
-  const SliceBlock& B = blocks[it.block];
+                                                          const SliceItem* __restrict__ items,
+                                                          uint8_t* __restrict__ tiles, int32_t* __restrict__ exps,
+                                                          int* __restrict__ status) {
+  extern __shared__ __align__(16) double strip[];
   __shared__ unsigned long long rmax[32];
   __shared__ int rexp[32];
   __shared__ int64_t roff[32];
-  const int tid = threadIdx.x;
-  if (tid < it.nr) {
+  __shared__ uint32_t lut[129];
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ int bulk_ok;
+  const SliceItem it = items[blockIdx.x];
+  const SliceBlock& B = blocks[it.block];
+  const int tid = threadIdx.x, lane = tid % 32, warp = tid / 32;
+  const int nr = it.nr;
+  if (tid < nr) {
     const int32_t grow = it.r0 + tid;
     rmax[tid] = 0ull;
     roff[tid] = grow < B.rows ? B.src_off + mixed_offset(grow, B.nr, B.rdim, B.rstride) : -1;
   }
+  if (tid < 129) lut[tid] = bf16_of_small_int(tid - 64);
   __syncthreads();
-  const int nch = B.k_tiles * 2;  // 8-wide chunks of the padded K range
-  const int units = it.nr * nch;
-  // pass 1: per-row max |x| (as ordered bit patterns)
-  for (int u = tid; u < units; u += blockDim.x) {
-    const int r = B.k_contig ? u / nch : u % it.nr;
-    const int ch = B.k_contig ? u % nch : u / it.nr;
+  const int K = B.K;
+  constexpr size_t tile_bytes = (size_t)S * kOzTileBytesPerSlice;
+  const bool staged = B.k_dense && (int64_t)nr * K * 8 <= kOzStageBytes;
+
+  if (staged) {
+    if (tid == 0) {
+      bool ok = (K % 2) == 0 && (reinterpret_cast<uintptr_t>(src) & 15) == 0;
+      for (int r = 0; r < nr; ++r)
+        if (roff[r] >= 0 && (roff[r] & 1)) ok = false;
+      bulk_ok = ok;
+      if (ok) {
+        sm100::mbar_init(&bar, 1);
+        sm100::fence_mbar_init();
+      }
+    }
+    __syncthreads();
+    if (bulk_ok) {
+      if (tid == 0) {
+        uint32_t bytes = 0;
+        for (int r = 0; r < nr; ++r)
+          if (roff[r] >= 0) bytes += (uint32_t)K * 8u;
+        sm100::mbar_arrive_expect_tx(&bar, bytes);
+        for (int r = 0; r < nr; ++r)
+          if (roff[r] >= 0) sm100::bulk_g2s(strip + (size_t)r * K, src + roff[r], (uint32_t)K * 8u, &bar);
+      }
+      // every thread waits (bounded) for the strip; a timeout is reported, then the copies are drained
+      const long long t0 = clock64();
+      bool ok = true;
+      while (!sm100::mbar_try_wait(&bar, 0)) {
+        if (clock64() - t0 > 4000000000ll) {
+          ok = false;
+          break;
+        }
+      }
+      if (!ok) {
+        if (tid == 0) atomicExch(status, TAMM_ETIMEOUT);
+        const long long t1 = clock64();
+        while (!sm100::mbar_try_wait(&bar, 0) && clock64() - t1 < 4000000000ll) {
+        }
+        return;
+      }
+    } else {
+      for (int i = tid; i < nr * K; i += blockDim.x) {
+        const int r = i / K;
+        strip[i] = roff[r] >= 0 ? __ldg(src + roff[r] + (i - r * K)) : 0.0;
+      }
+      __syncthreads();
+    }
+    // row maxima: one warp per row
+    for (int r = warp; r < nr; r += blockDim.x / 32) {
+      unsigned long long m = 0ull;
+      if (roff[r] >= 0)
+        for (int k = lane; k < K; k += 32)
+          m = max(m, (unsigned long long)__double_as_longlong(strip[(size_t)r * K + k]) & 0x7FFFFFFFFFFFFFFFull);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+      if (lane == 0) {
+        int e = kOzExpZero;
+        if (m != 0ull) (void)frexp(__longlong_as_double((long long)m), &e);
+        rexp[r] = e;
+        exps[B.exp_off + it.r0 + r] = e;
+      }
+    }
+    __syncthreads();
+    // digits: unit u = (row r, 32-bit word w of the padded K range), two elements per word
+    const int nw = B.k_tiles * 8;
+    for (int u = tid; u < nr * nw; u += blockDim.x) {
+      const int r = u / nw, w = u - r * nw;
+      uint32_t wd[S];
+#pragma unroll
+      for (int q = 0; q < S; ++q) wd[q] = 0u;
+      const int e = rexp[r];
+      const int k = 2 * w;
+      if (roff[r] >= 0 && e != kOzExpZero && k < K) {
+        const double x0 = strip[(size_t)r * K + k];
+        const double x1 = k + 1 < K ? strip[(size_t)r * K + k + 1] : 0.0;
+        pack_digits<S>(x0, x1, e, wd, lut);
+      }
+      const int32_t grow = it.r0 + r;
+      const int32_t rr = grow % kOzTileM;
+      const int wt = w & 7;
+      const int swz = (wt >> 2) ^ ((rr >> 2) & 1);
+      const int64_t tile = B.tile_off + (int64_t)(grow / kOzTileM) * B.k_tiles + (w >> 3);
+      uint8_t* base = tiles + (size_t)tile * tile_bytes + rr * 32 + swz * 16 + (wt & 3) * 4;
+#pragma unroll
+      for (int q = 0; q < S; ++q) *reinterpret_cast<uint32_t*>(base + (size_t)q * kOzTileBytesPerSlice) = wd[q];
+    }
+    return;
+  }
+
+  // ---- general layouts: two passes over global memory
+  const int nch = (K + 7) / 8;
+  for (int u = tid; u < nr * nch; u += blockDim.x) {
+    const int r = B.k_contig ? u / nch : u % nr;
+    const int ch = B.k_contig ? u % nch : u / nr;
     if (roff[r] < 0) continue;
     int64_t off[8];
     k_offsets8(B, ch * 8, off);
     unsigned long long m = 0ull;
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
-      if (ch * 8 + j < B.K) {
+      if (ch * 8 + j < K) {
         const unsigned long long b = (unsigned long long)__double_as_longlong(__ldg(src + roff[r] + off[j]));
         m = max(m, b & 0x7FFFFFFFFFFFFFFFull);
       }
@@ -135,33 +268,34 @@ __global__ void __launch_bounds__(256) ozaki_slice_kernel(const double* __restri
     if (m) atomicMax(&rmax[r], m);
   }
   __syncthreads();
-  if (tid < it.nr) {
+  if (tid < nr) {
     int e = kOzExpZero;
     if (rmax[tid] != 0ull) (void)frexp(__longlong_as_double((long long)rmax[tid]), &e);
     rexp[tid] = e;
     exps[B.exp_off + it.r0 + tid] = e;
   }
   __syncthreads();
-  // pass 2: digits, written into the 32-byte-swizzled tile images
-  const size_t tile_bytes = (size_t)S * kOzTileBytesPerSlice;
-  for (int u = tid; u < units; u += blockDim.x) {
-    const int r = B.k_contig ? u / nch : u % it.nr;
-    const int ch = B.k_contig ? u % nch : u / it.nr;
-    uint32_t packed[kOzMaxSlices][4];
+  const int nch2 = B.k_tiles * 2;
+  for (int u = tid; u < nr * nch2; u += blockDim.x) {
+    const int r = u % nr, ch = u / nr;
+    uint32_t packed[S][4];
 #pragma unroll
-    for (int s = 0; s < kOzMaxSlices; ++s)
+    for (int q = 0; q < S; ++q)
 #pragma unroll
-      for (int w = 0; w < 4; ++w) packed[s][w] = 0u;
-    if (roff[r] >= 0 && rexp[r] != kOzExpZero) {
+      for (int w = 0; w < 4; ++w) packed[q][w] = 0u;
+    const int e = rexp[r];
+    if (roff[r] >= 0 && e != kOzExpZero) {
       int64_t off[8];
       k_offsets8(B, ch * 8, off);
+      double xs[8];
 #pragma unroll
-      for (int j = 0; j < 8; ++j) {
-        const double x = ch * 8 + j < B.K ? __ldg(src + roff[r] + off[j]) : 0.0;
-        int d[kOzMaxSlices];
-        digits_of(x, rexp[r], S, d);
+      for (int j = 0; j < 8; ++j) xs[j] = ch * 8 + j < K ? __ldg(src + roff[r] + off[j]) : 0.0;
 #pragma unroll
-        for (int s = 0; s < kOzMaxSlices; ++s) packed[s][j >> 1] |= bf16_digit(d[s], s) << ((j & 1) * 16);
+      for (int j = 0; j < 8; j += 2) {
+        uint32_t wd[S];
+        pack_digits<S>(xs[j], xs[j + 1], e, wd, lut);
+#pragma unroll
+        for (int q = 0; q < S; ++q) packed[q][j >> 1] = wd[q];
       }
     }
     const int32_t grow = it.r0 + r;
@@ -169,9 +303,10 @@ __global__ void __launch_bounds__(256) ozaki_slice_kernel(const double* __restri
     const int64_t tile = B.tile_off + (int64_t)(grow / kOzTileM) * B.k_tiles + ch / 2;
     const int swz = (ch & 1) ^ ((rr >> 2) & 1);
     uint8_t* base = tiles + (size_t)tile * tile_bytes + rr * 32 + swz * 16;
-    for (int s = 0; s < S; ++s)
-      *reinterpret_cast<uint4*>(base + (size_t)s * kOzTileBytesPerSlice) =
-          make_uint4(packed[s][0], packed[s][1], packed[s][2], packed[s][3]);
+#pragma unroll
+    for (int q = 0; q < S; ++q)
+      *reinterpret_cast<uint4*>(base + (size_t)q * kOzTileBytesPerSlice) =
+          make_uint4(packed[q][0], packed[q][1], packed[q][2], packed[q][3]);
   }
 }
 
@@ -190,8 +325,7 @@ struct OzParams {
   double* c;
   int* status;
   double alpha, beta;
-  int S, stages;
-  OzOps full, ragged;
+  int stages;
 };
 
 // Warp roles: warpgroup 0 = producer (warp 0), MMA issuer + TMEM owner (warp 1),
@@ -251,12 +385,28 @@ __device__ __forceinline__ void fold(float& hi, float& lo, float s0, float s1, f
 
 __device__ __forceinline__ void epi_barrier() { asm volatile("bar.sync 1, %0;" ::"n"(32 * kEpiWarps) : "memory"); }
 
+// Issue the MMAs of one K step for schedule (S, fuse), op I onwards; every
+// operand offset, shape and flag is a compile-time constant.
+template <int S, bool kFuse, int I>
+__device__ __forceinline__ void issue_ops(uint32_t tmem, uint64_t a0, uint64_t b0, uint32_t idesc_ragged,
+                                          bool first) {
+  constexpr OzSched sch = oz_schedule(S, kFuse);
+  if constexpr (I < sch.n) {
+    constexpr OzOp op = sch.op[I];
+    constexpr uint32_t idesc_full = sm100::idesc_bf16_f32(128, 128 * op.nb);
+    // descriptor start address counts 16-byte units: one 4096-byte slice is +256
+    sm100::mma_bf16(tmem + 128u * op.region, a0 + (uint64_t)(256 * op.a), b0 + (uint64_t)(256 * op.b),
+                    kFuse ? idesc_full : idesc_ragged, (op.first && first) ? 0u : 1u);
+    issue_ops<S, kFuse, I + 1>(tmem, a0, b0, idesc_ragged, first);
+  }
+}
+
+template <int S>
 __global__ void __launch_bounds__(kThreads, 1) ozaki_gemm_kernel(const __grid_constant__ OzParams p) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  const int S = p.S, stages = p.stages;
-  const uint32_t slice_bytes = kOzTileBytesPerSlice;
-  const uint32_t half_bytes = (uint32_t)S * slice_bytes;  // A (or B) part of a stage
+  const int stages = p.stages;
+  constexpr uint32_t half_bytes = (uint32_t)S * kOzTileBytesPerSlice;  // A (or B) part of a stage
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + (size_t)stages * 2 * half_bytes);
   uint64_t* full = bars;
   uint64_t* empty = bars + stages;
@@ -332,7 +482,7 @@ __global__ void __launch_bounds__(kThreads, 1) ozaki_gemm_kernel(const __grid_co
   } else if (warp == 1) {
     // --------------------------------------------------------- MMA issuer
     if (lane == 0) {
-      const OzOps& ops = full_tile ? p.full : p.ragged;
+      const uint32_t idesc_ragged = sm100::idesc_bf16_f32(128, (uint32_t)n16);
       int stage = 0;
       uint32_t phase = 0, acc_phase = 0;
       bool ok = true;
@@ -348,14 +498,10 @@ __global__ void __launch_bounds__(kThreads, 1) ozaki_gemm_kernel(const __grid_co
           if (!wait_bounded(&full[stage], phase, abort_flag, p.status)) { ok = false; break; }
           sm100::tc_fence_after();
           const uint32_t sa = sm100::smem_u32(smem + (size_t)stage * 2 * half_bytes);
-          const uint32_t sb = sa + half_bytes;
-          for (int i = 0; i < ops.n; ++i) {
-            const OzOp op = ops.op[i];
-            const uint32_t N = full_tile ? 128u * op.nb : (uint32_t)n16;
-            sm100::mma_bf16(tmem + 128u * op.region, sm100::desc_kmajor_sw32(sa + op.a * slice_bytes),
-                            sm100::desc_kmajor_sw32(sb + op.b * slice_bytes), sm100::idesc_bf16_f32(128, N),
-                            (first && op.first) ? 0u : 1u);
-          }
+          const uint64_t a0 = sm100::desc_kmajor_sw32(sa);
+          const uint64_t b0 = sm100::desc_kmajor_sw32(sa + half_bytes);
+          if (full_tile) issue_ops<S, true, 0>(tmem, a0, b0, idesc_ragged, first);
+          else issue_ops<S, false, 0>(tmem, a0, b0, idesc_ragged, first);
           sm100::mma_commit(&empty[stage]);
           if (last) {
             sm100::mma_commit(acc_full);
@@ -462,13 +608,36 @@ __global__ void __launch_bounds__(kThreads, 1) ozaki_gemm_kernel(const __grid_co
 // Launchers
 // ======================================================================
 
+template <int S>
+static cudaError_t slice_dispatch(tamm_ctx* ctx, const double* src, const SliceBlock* blocks, const SliceItem* items,
+                                  int64_t n_items, uint8_t* tiles, int32_t* exps) {
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(ozaki_slice_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         kOzStageBytes);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  ozaki_slice_kernel<S><<<(unsigned)n_items, 256, kOzStageBytes, ctx->stream>>>(src, blocks, items, tiles, exps,
+                                                                                ctx->d_status);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_ozaki_slice(tamm_ctx* ctx, const double* src, const SliceBlock* blocks, const SliceItem* items,
                                int64_t n_items, int S, uint8_t* tiles, int32_t* exps) {
   if (n_items == 0) return cudaSuccess;
   kernel_begin(ctx, TAMM_KERNEL_SLICE);
-  ozaki_slice_kernel<<<(unsigned)n_items, 256, 0, ctx->stream>>>(src, blocks, items, S, tiles, exps);
+  cudaError_t e = cudaErrorInvalidValue;
+  switch (S) {
+    case 3: e = slice_dispatch<3>(ctx, src, blocks, items, n_items, tiles, exps); break;
+    case 4: e = slice_dispatch<4>(ctx, src, blocks, items, n_items, tiles, exps); break;
+    case 5: e = slice_dispatch<5>(ctx, src, blocks, items, n_items, tiles, exps); break;
+    case 6: e = slice_dispatch<6>(ctx, src, blocks, items, n_items, tiles, exps); break;
+    case 7: e = slice_dispatch<7>(ctx, src, blocks, items, n_items, tiles, exps); break;
+    case 8: e = slice_dispatch<8>(ctx, src, blocks, items, n_items, tiles, exps); break;
+  }
   kernel_end(ctx, TAMM_KERNEL_SLICE);
-  return cudaGetLastError();
+  return e;
 }
 
 static int oz_stages(int S) { return std::min(6, (192 * 1024) / (2 * S * kOzTileBytesPerSlice)); }
@@ -477,10 +646,27 @@ static size_t oz_smem_bytes(int S) {
   return (size_t)oz_stages(S) * 2 * S * kOzTileBytesPerSlice + 1024 + 4096;
 }
 
+template <int S>
+static cudaError_t gemm_dispatch(tamm_ctx* ctx, const OzParams& p, int64_t n_items) {
+  static int ready = 0;
+  const size_t smem = oz_smem_bytes(S);
+  if (!ready) {
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaFuncGetAttributes(&fa, ozaki_gemm_kernel<S>);
+    if (e != cudaSuccess) return e;
+    // setmaxnreg.inc would wait forever if the launch pool were too small
+    if (fa.numRegs < kRegsLaunchNeeded) return cudaErrorLaunchOutOfResources;
+    e = cudaFuncSetAttribute(ozaki_gemm_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    ready = 1;
+  }
+  ozaki_gemm_kernel<S><<<(unsigned)n_items, kThreads, smem, ctx->stream>>>(p);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_ozaki_gemm(tamm_ctx* ctx, const uint8_t* a_tiles, const uint8_t* b_tiles, const int32_t* a_exp,
                               const int32_t* b_exp, const OzGroup* groups, const OzTask* tasks, const OzItem* items,
-                              int64_t n_items, int S, const OzOps& full, const OzOps& ragged, double* c,
-                              double alpha, double beta) {
+                              int64_t n_items, int S, double* c, double alpha, double beta) {
   if (n_items == 0) return cudaSuccess;
   OzParams p;
   p.a_tiles = a_tiles;
@@ -494,72 +680,28 @@ cudaError_t launch_ozaki_gemm(tamm_ctx* ctx, const uint8_t* a_tiles, const uint8
   p.status = ctx->d_status;
   p.alpha = alpha;
   p.beta = beta;
-  p.S = S;
   p.stages = oz_stages(S);
-  p.full = full;
-  p.ragged = ragged;
-  const size_t smem = oz_smem_bytes(S);
-  static int checked_regs = 0;
-  if (!checked_regs) {
-    cudaFuncAttributes fa;
-    cudaError_t e0 = cudaFuncGetAttributes(&fa, ozaki_gemm_kernel);
-    if (e0 != cudaSuccess) return e0;
-    // setmaxnreg.inc would wait forever if the launch pool were too small
-    if (fa.numRegs < kRegsLaunchNeeded) return cudaErrorLaunchOutOfResources;
-    checked_regs = fa.numRegs;
-  }
-  cudaError_t e = cudaFuncSetAttribute(ozaki_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
   kernel_begin(ctx, TAMM_KERNEL_GEMM_OZ);
-  ozaki_gemm_kernel<<<(unsigned)n_items, kThreads, smem, ctx->stream>>>(p);
+  cudaError_t e = cudaErrorInvalidValue;
+  switch (S) {
+    case 3: e = gemm_dispatch<3>(ctx, p, n_items); break;
+    case 4: e = gemm_dispatch<4>(ctx, p, n_items); break;
+    case 5: e = gemm_dispatch<5>(ctx, p, n_items); break;
+    case 6: e = gemm_dispatch<6>(ctx, p, n_items); break;
+    case 7: e = gemm_dispatch<7>(ctx, p, n_items); break;
+    case 8: e = gemm_dispatch<8>(ctx, p, n_items); break;
+  }
   kernel_end(ctx, TAMM_KERNEL_GEMM_OZ);
-  return cudaGetLastError();
+  return e;
 }
 
 // ======================================================================
 // Host plan
 // ======================================================================
 
-// MMA schedules: products (k, l) with k + l <= S + 1 (1-based), region min(k+l-2, 3).
-static OzOps make_ops(int S, bool fuse) {
-  OzOps ops;
-  memset(&ops, 0, sizeof(ops));
-  bool written[4] = {false, false, false, false};
-  auto push = [&](int a, int b, int nb, int region) {
-    if (ops.n >= kOzMaxOps) throw Error(TAMM_EINVAL, "ozaki: too many MMA ops");
-    OzOp& o = ops.op[ops.n++];
-    o.a = (uint8_t)a;
-    o.b = (uint8_t)b;
-    o.nb = (uint8_t)nb;
-    o.region = (uint8_t)region;
-    bool f0 = !written[region], f1 = nb == 2 ? !written[region + 1] : f0;
-    if (f0 != f1) throw Error(TAMM_EINVAL, "ozaki: inconsistent accumulator schedule");
-    o.first = f0 ? 1 : 0;
-    written[region] = true;
-    if (nb == 2) written[region + 1] = true;
-  };
-  for (int k = 1; k <= S; ++k) {
-    // exact groups (k + l <= 4), fused in pairs of adjacent B slices when allowed
-    int l = 1;
-    while (l <= S + 1 - k && k + l <= 4) {
-      const int region = k + l - 2;
-      if (fuse && l + 1 <= S + 1 - k && k + l + 1 <= 4) {
-        push(k - 1, l - 1, 2, region);
-        l += 2;
-      } else {
-        push(k - 1, l - 1, 1, region);
-        l += 1;
-      }
-    }
-    for (; l <= S + 1 - k; ++l) push(k - 1, l - 1, 1, 3);
-  }
-  return ops;
-}
-
 struct OzakiPlan : Plan {
   ContractLayout lay;
   int S;
-  OzOps ops_full, ops_ragged;
   SliceBlock* d_sa = nullptr;
   SliceItem* d_ia = nullptr;
   int64_t n_ia = 0;
@@ -614,16 +756,24 @@ struct OzakiPlan : Plan {
       B.k_tiles = (int32_t)((K + kOzTileK - 1) / kOzTileK);
       B.k_contig = (nk > 0 && B.kstride[nk - 1] == 1) ? 1 : 0;
       if (nk == 0) B.k_contig = 1;
+      {
+        int64_t st = 1;
+        B.k_dense = 1;
+        for (int m = nk - 1; m >= 0; --m) {
+          if (B.kstride[m] != st) B.k_dense = 0;
+          st *= B.kdim[m];
+        }
+      }
       B.tile_off = tiles;
       B.exp_off = exps;
       tiles += (int64_t)B.row_tiles * B.k_tiles;
       exps += (int64_t)B.row_tiles * kOzTileM;
-      // rows per slicing CTA: a power of two <= 32 keeping a strip near 64 KB (k-contiguous),
-      // 32 rows when consecutive rows are the contiguous direction
+      // rows per slicing CTA: a power of two <= 32; for a dense summed range the
+      // largest strip that fits the shared-memory stage, else 32 rows
       int R = 32;
-      if (B.k_contig) {
+      if (B.k_dense) {
         R = 1;
-        while (R < 32 && (int64_t)(2 * R) * K * 8 <= 65536) R *= 2;
+        while (R < 32 && (int64_t)(2 * R) * K * 8 <= kOzStageBytes) R *= 2;
       }
       for (int32_t r = 0; r < B.row_tiles * kOzTileM; r += R) items.push_back({(int32_t)b, r, R, 0});
     }
@@ -632,8 +782,6 @@ struct OzakiPlan : Plan {
   OzakiPlan(tamm_ctx* c, const tamm_tensor* C, const char* lc, const tamm_tensor* A, const char* la,
             const tamm_tensor* B, const char* lb, int slices)
       : Plan(c), lay(c, C, lc, A, la, B, lb), S(slices) {
-    ops_full = make_ops(S, true);
-    ops_ragged = make_ops(S, false);
     const int nfl = (int)lay.free_left.size(), nfr = (int)lay.free_right.size(), nk = (int)lay.summed.size();
     auto perm_of = [](const std::string& need, const std::string& have) {
       std::vector<int> p(need.size());
@@ -729,8 +877,8 @@ void run_contract_ozaki(tamm_ctx* ctx, double alpha, tamm_tensor* C, const char*
   cuda_check(launch_ozaki_slice(ctx, lp, p->d_sa, p->d_ia, p->n_ia, slices, ta, ea), "ozaki slice (left)");
   cuda_check(launch_ozaki_slice(ctx, rp, p->d_sb, p->d_ib, p->n_ib, slices, tb, eb), "ozaki slice (right)");
   double* out = p->perm_out ? (double*)(scratch + p->off_x) : C->data;
-  cuda_check(launch_ozaki_gemm(ctx, ta, tb, ea, eb, p->d_groups, p->d_tasks, p->d_items, p->n_items, slices,
-                               p->ops_full, p->ops_ragged, out, alpha, p->perm_out ? 0.0 : beta),
+  cuda_check(launch_ozaki_gemm(ctx, ta, tb, ea, eb, p->d_groups, p->d_tasks, p->d_items, p->n_items, slices, out,
+                               alpha, p->perm_out ? 0.0 : beta),
              "ozaki gemm");
   if (p->perm_out) {
     const double one = 1.0;

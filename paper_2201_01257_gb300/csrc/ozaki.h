@@ -47,7 +47,7 @@ struct SliceBlock {
   int32_t rdim[4], rstride[4];
   int32_t kdim[4], kstride[4];
   int32_t k_contig;  // consecutive k are adjacent in memory (else consecutive rows are)
-  int32_t pad;
+  int32_t k_dense;   // the whole summed range is one contiguous run: offset of k is k
 };
 
 struct SliceItem {
@@ -76,20 +76,45 @@ struct OzItem {
 
 // MMA schedule for one K step: A slice, first B slice, number of adjacent B
 // slices fused along N (1 or 2), accumulator region, and whether it is the
-// first write of its region(s) in a chunk.
+// first write of its region(s) in a chunk.  Products (k, l) with k + l <= S + 1
+// (1-based) go to region min(k + l - 2, 3); exact-group products of adjacent B
+// slices are fused into one N = 256 MMA when `fuse` is set (full tiles).
 struct OzOp {
-  uint8_t a, b, nb, region, first;
+  int a, b, nb, region, first;
 };
-struct OzOps {
-  int32_t n;
+struct OzSched {
+  int n;
   OzOp op[kOzMaxOps];
 };
+
+__host__ __device__ constexpr OzSched oz_schedule(int S, bool fuse) {
+  OzSched s{};
+  bool written[4] = {false, false, false, false};
+  for (int k = 1; k <= S; ++k) {
+    int l = 1;
+    while (l <= S + 1 - k) {
+      const int region = k + l - 2 < 3 ? k + l - 2 : 3;
+      const bool pair = fuse && region < 2 && l + 1 <= S + 1 - k && k + l + 1 <= 4;
+      OzOp& o = s.op[s.n++];
+      o.a = k - 1;
+      o.b = l - 1;
+      o.nb = pair ? 2 : 1;
+      o.region = region;
+      o.first = written[region] ? 0 : 1;
+      written[region] = true;
+      if (pair) written[region + 1] = true;
+      l += pair ? 2 : 1;
+    }
+  }
+  return s;
+}
+
+constexpr int kOzStageBytes = 48 * 1024;  // shared-memory strip of one slicing CTA
 
 cudaError_t launch_ozaki_slice(tamm_ctx* ctx, const double* src, const SliceBlock* blocks, const SliceItem* items,
                                int64_t n_items, int S, uint8_t* tiles, int32_t* exps);
 cudaError_t launch_ozaki_gemm(tamm_ctx* ctx, const uint8_t* a_tiles, const uint8_t* b_tiles, const int32_t* a_exp,
                               const int32_t* b_exp, const OzGroup* groups, const OzTask* tasks, const OzItem* items,
-                              int64_t n_items, int S, const OzOps& full, const OzOps& ragged, double* c,
-                              double alpha, double beta);
+                              int64_t n_items, int S, double* c, double alpha, double beta);
 
 }  // namespace tamm
