@@ -95,6 +95,15 @@ TAMM_API tamm_status tamm_ctx_set_stream(tamm_ctx* ctx, void* stream);
 TAMM_API void tamm_ctx_destroy(tamm_ctx* ctx);
 /* Message of the last failed call on this context ("" if none); owned by ctx. */
 TAMM_API const char* tamm_last_error(const tamm_ctx* ctx);
+/* Tuning options of a context. */
+#define TAMM_OPT_OZAKI_CHUNK_K 0 /* split precision: summed indices per exact FP32 accumulation chunk,
+                                    a multiple of 16 in 16..1280 (default 640); shorter chunks read the
+                                    accumulators more often and shrink the rounding of the tail group */
+#define TAMM_OPT_OZAKI_PERSISTENT 1 /* split precision: 1 = one CTA per SM walks the work items, 0 = one CTA
+                                       per work item (default) */
+/* Set option `option` to `value`.  Errors: TAMM_EINVAL (unknown option or value out of range). */
+TAMM_API tamm_status tamm_ctx_set_option(tamm_ctx* ctx, int option, int64_t value);
+
 /* Kernel classes for launch counting and timing. */
 #define TAMM_KERNEL_ADD 0       /* permuted add / operand and output permutation */
 #define TAMM_KERNEL_REDUCE 1    /* energy and norm partial sums and final reduction */

@@ -27,6 +27,7 @@ TAMM_OK, TAMM_EINVAL, TAMM_ENOMEM, TAMM_ECUDA, TAMM_EUNSUPPORTED, TAMM_ETIMEOUT,
 TAMM_SYM_DENSE, TAMM_SYM_SPIN, TAMM_SYM_SPIN_IRREP = 0, 1, 2
 TAMM_PREC_F64, TAMM_PREC_OZAKI_BF16, TAMM_PREC_OZAKI_I8 = 0, 1, 2
 KERNEL_CLASSES = ("add", "reduce", "gemm_f64", "slice", "gemm_ozaki")
+TAMM_OPT_OZAKI_CHUNK_K = 0
 SYM = {"dense": TAMM_SYM_DENSE, "spin": TAMM_SYM_SPIN, "spin_irrep": TAMM_SYM_SPIN_IRREP}
 PREC = {"f64": TAMM_PREC_F64, "ozaki_bf16": TAMM_PREC_OZAKI_BF16, "ozaki_i8": TAMM_PREC_OZAKI_I8}
 STATUS_NAMES = {0: "TAMM_OK", 1: "TAMM_EINVAL", 2: "TAMM_ENOMEM", 3: "TAMM_ECUDA", 4: "TAMM_EUNSUPPORTED",
@@ -45,6 +46,7 @@ PROTOTYPES = [
     ("tamm_ctx_destroy", None, [_vp]),
     ("tamm_last_error", _cp, [_vp]),
     ("tamm_sync", _i, [_vp]),
+    ("tamm_ctx_set_option", _i, [_vp, _i, _i64]),
     ("tamm_ctx_launch_count", _i, [_vp, _i64p]),
     ("tamm_ctx_profile", _i, [_vp, _i]),
     ("tamm_ctx_profile_read", _i, [_vp, _dp, _i64p]),
@@ -226,6 +228,9 @@ class Context:
 
     def sync(self) -> None:
         self.check(self.lib.tamm_sync(self.handle), "tamm_sync")
+
+    def set_option(self, option: int, value: int) -> None:
+        self.check(self.lib.tamm_ctx_set_option(self.handle, int(option), int(value)), "tamm_ctx_set_option")
 
     def launch_count(self) -> int:
         n = ctypes.c_int64()

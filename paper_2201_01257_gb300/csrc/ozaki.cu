@@ -142,9 +142,9 @@ __global__ void __launch_bounds__(256) ozaki_slice_kernel(const double* __restri
                                                           uint8_t* __restrict__ tiles, int32_t* __restrict__ exps,
                                                           int* __restrict__ status) {
   extern __shared__ __align__(16) double strip[];
-  __shared__ unsigned long long rmax[32];
-  __shared__ int rexp[32];
-  __shared__ int64_t roff[32];
+  __shared__ unsigned long long rmax[kOzSliceMaxRows];
+  __shared__ int rexp[kOzSliceMaxRows];
+  __shared__ int64_t roff[kOzSliceMaxRows];
   __shared__ uint32_t lut[129];
   __shared__ __align__(8) uint64_t bar;
   __shared__ int bulk_ok;
@@ -152,10 +152,10 @@ __global__ void __launch_bounds__(256) ozaki_slice_kernel(const double* __restri
   const SliceBlock& B = blocks[it.block];
   const int tid = threadIdx.x, lane = tid % 32, warp = tid / 32;
   const int nr = it.nr;
-  if (tid < nr) {
-    const int32_t grow = it.r0 + tid;
-    rmax[tid] = 0ull;
-    roff[tid] = grow < B.rows ? B.src_off + mixed_offset(grow, B.nr, B.rdim, B.rstride) : -1;
+  for (int r = tid; r < nr; r += blockDim.x) {
+    const int32_t grow = it.r0 + r;
+    rmax[r] = 0ull;
+    roff[r] = grow < B.rows ? B.src_off + mixed_offset(grow, B.nr, B.rdim, B.rstride) : -1;
   }
   if (tid < 129) lut[tid] = bf16_of_small_int(tid - 64);
   __syncthreads();
@@ -268,11 +268,11 @@ __global__ void __launch_bounds__(256) ozaki_slice_kernel(const double* __restri
     if (m) atomicMax(&rmax[r], m);
   }
   __syncthreads();
-  if (tid < nr) {
+  for (int r = tid; r < nr; r += blockDim.x) {
     int e = kOzExpZero;
-    if (rmax[tid] != 0ull) (void)frexp(__longlong_as_double((long long)rmax[tid]), &e);
-    rexp[tid] = e;
-    exps[B.exp_off + it.r0 + tid] = e;
+    if (rmax[r] != 0ull) (void)frexp(__longlong_as_double((long long)rmax[r]), &e);
+    rexp[r] = e;
+    exps[B.exp_off + it.r0 + r] = e;
   }
   __syncthreads();
   const int nch2 = B.k_tiles * 2;
@@ -315,17 +315,13 @@ __global__ void __launch_bounds__(256) ozaki_slice_kernel(const double* __restri
 // ======================================================================
 
 struct OzParams {
-  const uint8_t* a_tiles;
-  const uint8_t* b_tiles;
-  const int32_t* a_exp;
-  const int32_t* b_exp;
-  const OzGroup* groups;
-  const OzTask* tasks;
   const OzItem* items;
-  double* c;
+  int64_t n_items;
   int* status;
-  double alpha, beta;
   int stages;
+  int chunk_tiles;  // K tiles per exact accumulation chunk (<= kOzChunkTiles)
+  int n_problems;
+  OzProblem problems[kOzMaxProblems];
 };
 
 // Warp roles: warpgroup 0 = producer (warp 0), MMA issuer + TMEM owner (warp 1),
@@ -418,12 +414,7 @@ __global__ void __launch_bounds__(kThreads, 1) ozaki_gemm_kernel(const __grid_co
   float* sB = reinterpret_cast<float*>(tmem_holder + 4);  // [2][128] per-task column scales
   int* fref = reinterpret_cast<int*>(sB + 256);            // [128] reference column exponents
 
-  const OzItem it = p.items[blockIdx.x];
-  const OzGroup g = p.groups[it.group];
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-  const int n_valid = min(kOzTileN, g.N - it.nt * kOzTileN);
-  const bool full_tile = n_valid == kOzTileN;
-  const int n16 = (n_valid + 15) & ~15;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < stages; ++s) {
@@ -453,21 +444,28 @@ __global__ void __launch_bounds__(kThreads, 1) ozaki_gemm_kernel(const __grid_co
     if (lane == 0) {
       int stage = 0;
       uint32_t phase = 0, issued_mask = 0, issued_parity = 0;
-      for (int t = g.task_begin; t < g.task_end && !*abort_flag; ++t) {
-        const OzTask tk = p.tasks[t];
-        const uint8_t* a = p.a_tiles + (size_t)(tk.a_tile + (int64_t)it.mt * tk.k_tiles) * half_bytes;
-        const uint8_t* b = p.b_tiles + (size_t)(tk.b_tile + (int64_t)it.nt * tk.k_tiles) * half_bytes;
-        for (int kt = 0; kt < tk.k_tiles; ++kt) {
-          if (!wait_bounded(&empty[stage], phase ^ 1u, abort_flag, p.status)) break;
-          uint8_t* sa = smem + (size_t)stage * 2 * half_bytes;
-          sm100::mbar_arrive_expect_tx(&full[stage], 2 * half_bytes);
-          sm100::bulk_g2s(sa, a + (size_t)kt * half_bytes, half_bytes, &full[stage]);
-          sm100::bulk_g2s(sa + half_bytes, b + (size_t)kt * half_bytes, half_bytes, &full[stage]);
-          issued_mask |= 1u << stage;
-          issued_parity = (issued_parity & ~(1u << stage)) | (phase << stage);
-          if (++stage == stages) {
-            stage = 0;
-            phase ^= 1u;
+      for (int64_t i = blockIdx.x; i < p.n_items && !*abort_flag; i += gridDim.x) {
+        const OzItem it = p.items[i];
+        const OzTask* tasks = p.problems[it.problem].tasks;
+        const uint8_t* a_tiles = p.problems[it.problem].a_tiles;
+        const uint8_t* b_tiles = p.problems[it.problem].b_tiles;
+        const OzGroup g = p.problems[it.problem].groups[it.group];
+        for (int t = g.task_begin; t < g.task_end && !*abort_flag; ++t) {
+          const OzTask tk = tasks[t];
+          const uint8_t* a = a_tiles + (size_t)(tk.a_tile + (int64_t)it.mt * tk.k_tiles) * half_bytes;
+          const uint8_t* b = b_tiles + (size_t)(tk.b_tile + (int64_t)it.nt * tk.k_tiles) * half_bytes;
+          for (int kt = 0; kt < tk.k_tiles; ++kt) {
+            if (!wait_bounded(&empty[stage], phase ^ 1u, abort_flag, p.status)) break;
+            uint8_t* sa = smem + (size_t)stage * 2 * half_bytes;
+            sm100::mbar_arrive_expect_tx(&full[stage], 2 * half_bytes);
+            sm100::bulk_g2s(sa, a + (size_t)kt * half_bytes, half_bytes, &full[stage]);
+            sm100::bulk_g2s(sa + half_bytes, b + (size_t)kt * half_bytes, half_bytes, &full[stage]);
+            issued_mask |= 1u << stage;
+            issued_parity = (issued_parity & ~(1u << stage)) | (phase << stage);
+            if (++stage == stages) {
+              stage = 0;
+              phase ^= 1u;
+            }
           }
         }
       }
@@ -482,34 +480,45 @@ __global__ void __launch_bounds__(kThreads, 1) ozaki_gemm_kernel(const __grid_co
   } else if (warp == 1) {
     // --------------------------------------------------------- MMA issuer
     if (lane == 0) {
-      const uint32_t idesc_ragged = sm100::idesc_bf16_f32(128, (uint32_t)n16);
+      const uint64_t desc_stage0 = sm100::desc_kmajor_sw32(sm100::smem_u32(smem));
       int stage = 0;
       uint32_t phase = 0, acc_phase = 0;
       bool ok = true;
-      for (int t = g.task_begin; t < g.task_end && ok; ++t) {
-        const int k_tiles = p.tasks[t].k_tiles;
-        for (int kt = 0; kt < k_tiles; ++kt) {
-          const bool first = kt % kOzChunkTiles == 0;
-          const bool last = (kt + 1) % kOzChunkTiles == 0 || kt + 1 == k_tiles;
-          if (first) {
-            if (!wait_bounded(acc_empty, acc_phase ^ 1u, abort_flag, p.status)) { ok = false; break; }
+      for (int64_t i = blockIdx.x; i < p.n_items && ok; i += gridDim.x) {
+        const OzItem it = p.items[i];
+        const OzTask* tasks = p.problems[it.problem].tasks;
+        const OzGroup g = p.problems[it.problem].groups[it.group];
+        const int n_valid = min(kOzTileN, g.N - it.nt * kOzTileN);
+        const bool full_tile = n_valid == kOzTileN;
+        const uint32_t idesc_ragged = sm100::idesc_bf16_f32(128, (uint32_t)((n_valid + 15) & ~15));
+        for (int t = g.task_begin; t < g.task_end && ok; ++t) {
+          const int k_tiles = tasks[t].k_tiles;
+          int in_chunk = 0;  // position inside the current chunk (no division on the issue path)
+          for (int kt = 0; kt < k_tiles; ++kt) {
+            const bool first = in_chunk == 0;
+            const bool last = ++in_chunk == p.chunk_tiles || kt + 1 == k_tiles;
+            if (last) in_chunk = 0;
+            if (first) {
+              if (!wait_bounded(acc_empty, acc_phase ^ 1u, abort_flag, p.status)) { ok = false; break; }
+              sm100::tc_fence_after();
+            }
+            if (!wait_bounded(&full[stage], phase, abort_flag, p.status)) { ok = false; break; }
             sm100::tc_fence_after();
-          }
-          if (!wait_bounded(&full[stage], phase, abort_flag, p.status)) { ok = false; break; }
-          sm100::tc_fence_after();
-          const uint32_t sa = sm100::smem_u32(smem + (size_t)stage * 2 * half_bytes);
-          const uint64_t a0 = sm100::desc_kmajor_sw32(sa);
-          const uint64_t b0 = sm100::desc_kmajor_sw32(sa + half_bytes);
-          if (full_tile) issue_ops<S, true, 0>(tmem, a0, b0, idesc_ragged, first);
-          else issue_ops<S, false, 0>(tmem, a0, b0, idesc_ragged, first);
-          sm100::mma_commit(&empty[stage]);
-          if (last) {
-            sm100::mma_commit(acc_full);
-            acc_phase ^= 1u;
-          }
-          if (++stage == stages) {
-            stage = 0;
-            phase ^= 1u;
+            // descriptor start addresses count 16-byte units and stay below 2^14, so stage and
+            // operand offsets add straight onto the stage-0 descriptor
+            const uint64_t a0 = desc_stage0 + (uint64_t)((uint32_t)stage * (2u * half_bytes >> 4));
+            const uint64_t b0 = a0 + (half_bytes >> 4);
+            if (full_tile) issue_ops<S, true, 0>(tmem, a0, b0, idesc_ragged, first);
+            else issue_ops<S, false, 0>(tmem, a0, b0, idesc_ragged, first);
+            sm100::mma_commit(&empty[stage]);
+            if (last) {
+              sm100::mma_commit(acc_full);
+              acc_phase ^= 1u;
+            }
+            if (++stage == stages) {
+              stage = 0;
+              phase ^= 1u;
+            }
           }
         }
       }
@@ -529,67 +538,79 @@ __global__ void __launch_bounds__(kThreads, 1) ozaki_gemm_kernel(const __grid_co
     const int row = q * 32 + lane;
     const int c0 = 64 * h;
     const uint32_t trow = tmem + ((uint32_t)(q * 32) << 16);
-    int Eref = kOzExpZero;
-    for (int t = g.task_begin; t < g.task_end; ++t)
-      Eref = max(Eref, p.a_exp[p.tasks[t].a_exp + (int64_t)it.mt * kOzTileM + row]);
-    if (etid < kOzTileN) {
-      int F = kOzExpZero;
-      for (int t = g.task_begin; t < g.task_end; ++t)
-        F = max(F, p.b_exp[p.tasks[t].b_exp + (int64_t)it.nt * kOzTileN + etid]);
-      fref[etid] = F;
-    }
-    epi_barrier();
-    float hi[64], lo[64];
-#pragma unroll
-    for (int j = 0; j < 64; ++j) hi[j] = lo[j] = 0.0f;
-    uint32_t chunk = 0;
+    uint32_t chunk = 0, task_count = 0;
     bool ok = true;
-    // every epilogue warp passes the per-task named barrier on every path (also after a timeout)
-    for (int t = g.task_begin; t < g.task_end; ++t) {
-      const OzTask tk = p.tasks[t];
-      float* sbuf = sB + ((t - g.task_begin) & 1) * 128;
+    // Every epilogue warp passes the same named barriers on every path (also after a timeout).
+    for (int64_t i = blockIdx.x; i < p.n_items; i += gridDim.x) {
+      const OzItem it = p.items[i];
+      const OzTask* tasks = p.problems[it.problem].tasks;
+      const int32_t* a_exp = p.problems[it.problem].a_exp;
+      const int32_t* b_exp = p.problems[it.problem].b_exp;
+      const OzGroup g = p.problems[it.problem].groups[it.group];
+      const int n_valid = min(kOzTileN, g.N - it.nt * kOzTileN);
+      epi_barrier();  // the previous item's output writes (which read fref) are done
+      int Eref = kOzExpZero;
+      for (int t = g.task_begin; t < g.task_end; ++t)
+        Eref = max(Eref, a_exp[tasks[t].a_exp + (int64_t)it.mt * kOzTileM + row]);
       if (etid < kOzTileN) {
-        const int eb = p.b_exp[tk.b_exp + (int64_t)it.nt * kOzTileN + etid];
-        sbuf[etid] = (eb == kOzExpZero) ? 0.0f : pow2f(eb - fref[etid]);
+        int F = kOzExpZero;
+        for (int t = g.task_begin; t < g.task_end; ++t)
+          F = max(F, b_exp[tasks[t].b_exp + (int64_t)it.nt * kOzTileN + etid]);
+        fref[etid] = F;
       }
-      epi_barrier();
-      const int ea = p.a_exp[tk.a_exp + (int64_t)it.mt * kOzTileM + row];
-      const float sA = (ea == kOzExpZero) ? 0.0f : pow2f(ea - Eref);
-      const int n_chunks = ok ? (tk.k_tiles + kOzChunkTiles - 1) / kOzChunkTiles : 0;
-      for (int ck = 0; ck < n_chunks; ++ck, ++chunk) {
-        if (!wait_bounded(acc_full, chunk & 1u, abort_flag, p.status)) { ok = false; break; }
-        sm100::tc_fence_after();
+      float hi[64], lo[64];
 #pragma unroll
-        for (int g8 = 0; g8 < 8; ++g8) {
-          const int col = c0 + 8 * g8;
-          float r0[8], r1[8], r2[8], r3[8];
-          sm100::tmem_ld8(trow + 0 * 128 + col, r0);
-          sm100::tmem_ld8(trow + 1 * 128 + col, r1);
-          sm100::tmem_ld8(trow + 2 * 128 + col, r2);
-          sm100::tmem_ld8(trow + 3 * 128 + col, r3);
-          sm100::tmem_wait_ld();
-#pragma unroll
-          for (int j = 0; j < 8; ++j)
-            fold(hi[8 * g8 + j], lo[8 * g8 + j], r0[j], r1[j], r2[j], r3[j], sA * sbuf[col + j]);
+      for (int j = 0; j < 64; ++j) hi[j] = lo[j] = 0.0f;
+      for (int t = g.task_begin; t < g.task_end; ++t, ++task_count) {
+        const OzTask tk = tasks[t];
+        float* sbuf = sB + (task_count & 1u) * 128;
+        epi_barrier();  // fref is set, and sbuf's previous readers (two tasks ago) are done
+        if (etid < kOzTileN) {
+          const int eb = b_exp[tk.b_exp + (int64_t)it.nt * kOzTileN + etid];
+          sbuf[etid] = (eb == kOzExpZero) ? 0.0f : pow2f(eb - fref[etid]);
         }
-        sm100::tc_fence_before();
-        __syncwarp();
-        if (lane == 0) sm100::mbar_arrive(acc_empty);
-      }
-    }
-    if (ok) {
-      const int grow = it.mt * kOzTileM + row;
-      if (grow < g.M) {
-        double* crow = p.c + g.c_off + (int64_t)grow * g.N + (int64_t)it.nt * kOzTileN;
+        epi_barrier();
+        const int ea = a_exp[tk.a_exp + (int64_t)it.mt * kOzTileM + row];
+        const float sA = (ea == kOzExpZero) ? 0.0f : pow2f(ea - Eref);
+        const int n_chunks = ok ? (tk.k_tiles + p.chunk_tiles - 1) / p.chunk_tiles : 0;
+        for (int ck = 0; ck < n_chunks; ++ck, ++chunk) {
+          if (!wait_bounded(acc_full, chunk & 1u, abort_flag, p.status)) { ok = false; break; }
+          sm100::tc_fence_after();
 #pragma unroll
-        for (int j = 0; j < 64; ++j) {
-          const int col = c0 + j;
-          if (col < n_valid) {
-            double v = 0.0;
-            if (Eref != kOzExpZero && fref[col] != kOzExpZero)
-              v = ((double)hi[j] + (double)lo[j]) * pow2d(Eref + fref[col] - 12);
-            double* cp = crow + col;
-            *cp = p.beta != 0.0 ? fma(p.beta, *cp, p.alpha * v) : p.alpha * v;
+          for (int g8 = 0; g8 < 8; ++g8) {
+            const int col = c0 + 8 * g8;
+            if (col >= n_valid) break;  // columns past a ragged tile's width were not computed
+            float r0[8], r1[8], r2[8], r3[8];
+            sm100::tmem_ld8(trow + 0 * 128 + col, r0);
+            sm100::tmem_ld8(trow + 1 * 128 + col, r1);
+            sm100::tmem_ld8(trow + 2 * 128 + col, r2);
+            sm100::tmem_ld8(trow + 3 * 128 + col, r3);
+            sm100::tmem_wait_ld();
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+              fold(hi[8 * g8 + j], lo[8 * g8 + j], r0[j], r1[j], r2[j], r3[j], sA * sbuf[col + j]);
+          }
+          sm100::tc_fence_before();
+          __syncwarp();
+          if (lane == 0) sm100::mbar_arrive(acc_empty);
+        }
+      }
+      if (g.task_begin == g.task_end) epi_barrier();  // keep the fref barrier count uniform
+      if (ok) {
+        const int grow = it.mt * kOzTileM + row;
+        if (grow < g.M) {
+          double* crow = p.problems[it.problem].c + g.c_off + (int64_t)grow * g.N + (int64_t)it.nt * kOzTileN;
+          const double alpha = p.problems[it.problem].alpha, beta = p.problems[it.problem].beta;
+#pragma unroll
+          for (int j = 0; j < 64; ++j) {
+            const int col = c0 + j;
+            if (col < n_valid) {
+              double v = 0.0;
+              if (Eref != kOzExpZero && fref[col] != kOzExpZero)
+                v = ((double)hi[j] + (double)lo[j]) * pow2d(Eref + fref[col] - 12);
+              double* cp = crow + col;
+              *cp = beta != 0.0 ? fma(beta, *cp, alpha * v) : alpha * v;
+            }
           }
         }
       }
@@ -647,7 +668,7 @@ static size_t oz_smem_bytes(int S) {
 }
 
 template <int S>
-static cudaError_t gemm_dispatch(tamm_ctx* ctx, const OzParams& p, int64_t n_items) {
+static cudaError_t gemm_dispatch(tamm_ctx* ctx, const OzParams& p, int grid) {
   static int ready = 0;
   const size_t smem = oz_smem_bytes(S);
   if (!ready) {
@@ -660,36 +681,35 @@ static cudaError_t gemm_dispatch(tamm_ctx* ctx, const OzParams& p, int64_t n_ite
     if (e != cudaSuccess) return e;
     ready = 1;
   }
-  ozaki_gemm_kernel<S><<<(unsigned)n_items, kThreads, smem, ctx->stream>>>(p);
+  ozaki_gemm_kernel<S><<<(unsigned)grid, kThreads, smem, ctx->stream>>>(p);
   return cudaGetLastError();
 }
 
-cudaError_t launch_ozaki_gemm(tamm_ctx* ctx, const uint8_t* a_tiles, const uint8_t* b_tiles, const int32_t* a_exp,
-                              const int32_t* b_exp, const OzGroup* groups, const OzTask* tasks, const OzItem* items,
-                              int64_t n_items, int S, double* c, double alpha, double beta) {
+cudaError_t launch_ozaki_gemm(tamm_ctx* ctx, const OzProblem* problems, int n_problems, const OzItem* items,
+                              int64_t n_items, int S, int chunk_tiles) {
   if (n_items == 0) return cudaSuccess;
-  OzParams p;
-  p.a_tiles = a_tiles;
-  p.b_tiles = b_tiles;
-  p.a_exp = a_exp;
-  p.b_exp = b_exp;
-  p.groups = groups;
-  p.tasks = tasks;
+  if (chunk_tiles < 1 || chunk_tiles > kOzChunkTiles) return cudaErrorInvalidValue;
+  if (n_problems < 1 || n_problems > kOzMaxProblems) return cudaErrorInvalidValue;
+  static OzParams p;  // large parameter block; copied into the launch
   p.items = items;
-  p.c = c;
+  p.n_items = n_items;
   p.status = ctx->d_status;
-  p.alpha = alpha;
-  p.beta = beta;
   p.stages = oz_stages(S);
+  p.chunk_tiles = chunk_tiles;
+  p.n_problems = n_problems;
+  for (int i = 0; i < n_problems; ++i) p.problems[i] = problems[i];
+  // persistent: one CTA per SM walks items round-robin; otherwise one CTA per item
+  const int grid = ctx->oz_persistent ? (int)std::min<int64_t>(n_items, std::max(1, ctx->sm_count))
+                                      : (int)std::min<int64_t>(n_items, 0x7FFFFFFF);
   kernel_begin(ctx, TAMM_KERNEL_GEMM_OZ);
   cudaError_t e = cudaErrorInvalidValue;
   switch (S) {
-    case 3: e = gemm_dispatch<3>(ctx, p, n_items); break;
-    case 4: e = gemm_dispatch<4>(ctx, p, n_items); break;
-    case 5: e = gemm_dispatch<5>(ctx, p, n_items); break;
-    case 6: e = gemm_dispatch<6>(ctx, p, n_items); break;
-    case 7: e = gemm_dispatch<7>(ctx, p, n_items); break;
-    case 8: e = gemm_dispatch<8>(ctx, p, n_items); break;
+    case 3: e = gemm_dispatch<3>(ctx, p, grid); break;
+    case 4: e = gemm_dispatch<4>(ctx, p, grid); break;
+    case 5: e = gemm_dispatch<5>(ctx, p, grid); break;
+    case 6: e = gemm_dispatch<6>(ctx, p, grid); break;
+    case 7: e = gemm_dispatch<7>(ctx, p, grid); break;
+    case 8: e = gemm_dispatch<8>(ctx, p, grid); break;
   }
   kernel_end(ctx, TAMM_KERNEL_GEMM_OZ);
   return e;
@@ -770,10 +790,14 @@ struct OzakiPlan : Plan {
       exps += (int64_t)B.row_tiles * kOzTileM;
       // rows per slicing CTA: a power of two <= 32; for a dense summed range the
       // largest strip that fits the shared-memory stage, else 32 rows
-      int R = 32;
+      int R;
       if (B.k_dense) {
         R = 1;
-        while (R < 32 && (int64_t)(2 * R) * K * 8 <= kOzStageBytes) R *= 2;
+        while (R < kOzSliceMaxRows && (int64_t)(2 * R) * K * 8 <= kOzStageBytes) R *= 2;
+      } else {
+        // enough rows for every thread to have work, at least 32 for coalescing along rows
+        R = 32;
+        while (R < kOzSliceMaxRows && (int64_t)R * ((K + 7) / 8) < 1024) R *= 2;
       }
       for (int32_t r = 0; r < B.row_tiles * kOzTileM; r += R) items.push_back({(int32_t)b, r, R, 0});
     }
@@ -837,7 +861,7 @@ struct OzakiPlan : Plan {
       groups.push_back(gg);
       const int32_t mts = (gg.M + kOzTileM - 1) / kOzTileM, nts = (gg.N + kOzTileN - 1) / kOzTileN;
       for (int32_t mt = 0; mt < mts; ++mt)
-        for (int32_t nt = 0; nt < nts; ++nt) items.push_back({gi, mt, nt, 0});
+        for (int32_t nt = 0; nt < nts; ++nt) items.push_back({0, gi, mt, nt});
     }
     n_ia = (int64_t)ia.size();
     n_ib = (int64_t)ib.size();
@@ -877,8 +901,17 @@ void run_contract_ozaki(tamm_ctx* ctx, double alpha, tamm_tensor* C, const char*
   cuda_check(launch_ozaki_slice(ctx, lp, p->d_sa, p->d_ia, p->n_ia, slices, ta, ea), "ozaki slice (left)");
   cuda_check(launch_ozaki_slice(ctx, rp, p->d_sb, p->d_ib, p->n_ib, slices, tb, eb), "ozaki slice (right)");
   double* out = p->perm_out ? (double*)(scratch + p->off_x) : C->data;
-  cuda_check(launch_ozaki_gemm(ctx, ta, tb, ea, eb, p->d_groups, p->d_tasks, p->d_items, p->n_items, slices, out,
-                               alpha, p->perm_out ? 0.0 : beta),
+  OzProblem prob;
+  prob.a_tiles = ta;
+  prob.b_tiles = tb;
+  prob.a_exp = ea;
+  prob.b_exp = eb;
+  prob.groups = p->d_groups;
+  prob.tasks = p->d_tasks;
+  prob.c = out;
+  prob.alpha = alpha;
+  prob.beta = p->perm_out ? 0.0 : beta;
+  cuda_check(launch_ozaki_gemm(ctx, &prob, 1, p->d_items, p->n_items, slices, ctx->oz_chunk_k / kOzTileK),
              "ozaki gemm");
   if (p->perm_out) {
     const double one = 1.0;

@@ -9,7 +9,9 @@
 //     G0: k+l=2, G1: k+l=3, G2: k+l=4 (each sums integer multiples of 2^-7G),
 //     G3: every k+l >= 5 (weighted tail, rounding allowed there).
 // A chunk of at most kOzChunkK summed indices keeps |G0|, |G1| 2^7, |G2| 2^14
-// below 3 * 1280 * 64 * 64 < 2^24, so G0..G2 are exact in FP32.  After each
+// below 3 * 1280 * 64 * 64 < 2^24, so G0..G2 are exact in FP32.  The tail G3
+// is summed by the tensor core with FP32 rounding that is not unbiased, so its
+// error grows with the chunk length; the default chunk is 640.  After each
 // chunk the epilogue scales the four partial sums by the chunk's power-of-two
 // row/column factors and folds them into a (hi, lo) FP32 pair, G0..G2 through
 // error-free TwoSum steps and G3 by a rounded add into lo; FP64 is used only
@@ -50,6 +52,8 @@ struct SliceBlock {
   int32_t k_dense;   // the whole summed range is one contiguous run: offset of k is k
 };
 
+constexpr int kOzSliceMaxRows = 128;  // rows per slicing CTA
+
 struct SliceItem {
   int32_t block;
   int32_t r0;  // first row (padding rows up to row_tiles*128 are written as zeros)
@@ -70,8 +74,21 @@ struct OzTask {
   int32_t pad;
 };
 
+// One contraction inside a (possibly grouped) persistent GEMM launch.
+struct OzProblem {
+  const uint8_t* a_tiles;
+  const uint8_t* b_tiles;
+  const int32_t* a_exp;
+  const int32_t* b_exp;
+  const OzGroup* groups;
+  const OzTask* tasks;
+  double* c;
+  double alpha, beta;
+};
+constexpr int kOzMaxProblems = 64;  // problems per launch (kernel-parameter table)
+
 struct OzItem {
-  int32_t group, mt, nt, pad;
+  int32_t problem, group, mt, nt;
 };
 
 // MMA schedule for one K step: A slice, first B slice, number of adjacent B
@@ -113,8 +130,8 @@ constexpr int kOzStageBytes = 48 * 1024;  // shared-memory strip of one slicing 
 
 cudaError_t launch_ozaki_slice(tamm_ctx* ctx, const double* src, const SliceBlock* blocks, const SliceItem* items,
                                int64_t n_items, int S, uint8_t* tiles, int32_t* exps);
-cudaError_t launch_ozaki_gemm(tamm_ctx* ctx, const uint8_t* a_tiles, const uint8_t* b_tiles, const int32_t* a_exp,
-                              const int32_t* b_exp, const OzGroup* groups, const OzTask* tasks, const OzItem* items,
-                              int64_t n_items, int S, double* c, double alpha, double beta);
+// Persistent launch over `n_items` work items of up to kOzMaxProblems problems.
+cudaError_t launch_ozaki_gemm(tamm_ctx* ctx, const OzProblem* problems, int n_problems, const OzItem* items,
+                              int64_t n_items, int S, int chunk_tiles);
 
 }  // namespace tamm

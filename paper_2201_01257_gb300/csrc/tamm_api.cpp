@@ -184,6 +184,23 @@ extern "C" void tamm_ctx_destroy(tamm_ctx* ctx) {
   delete ctx;
 }
 
+extern "C" tamm_status tamm_ctx_set_option(tamm_ctx* ctx, int option, int64_t value) {
+  if (!ctx) return TAMM_EINVAL;
+  return guarded(ctx, [&] {
+    if (option == TAMM_OPT_OZAKI_CHUNK_K) {
+      if (value < 16 || value > 1280 || value % 16) throw Error(TAMM_EINVAL, "chunk must be a multiple of 16 in 16..1280");
+      ctx->oz_chunk_k = (int)value;
+      return;
+    }
+    if (option == TAMM_OPT_OZAKI_PERSISTENT) {
+      if (value != 0 && value != 1) throw Error(TAMM_EINVAL, "persistent must be 0 or 1");
+      ctx->oz_persistent = value != 0;
+      return;
+    }
+    throw Error(TAMM_EINVAL, "unknown option %d", option);
+  });
+}
+
 extern "C" const char* tamm_last_error(const tamm_ctx* ctx) { return ctx ? ctx->last_error.c_str() : ""; }
 
 namespace tamm {

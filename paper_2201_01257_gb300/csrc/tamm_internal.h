@@ -122,6 +122,8 @@ struct tamm_ctx {
   std::map<std::string, std::unique_ptr<tamm::Plan>> plans;
   int sm_count = 0;
   bool host_only = false;  // device -1: metadata and planning only
+  int oz_chunk_k = 640;    // split precision: summed indices per exact FP32 chunk
+  bool oz_persistent = false;  // split precision: persistent GEMM grid (one CTA per SM)
   int64_t launches = 0;    // kernels launched by this context
   bool profiling = false;  // bracket launches with CUDA events
   struct TimedLaunch {
