@@ -51,6 +51,7 @@ typedef int tamm_status;
 #define TAMM_EUNSUPPORTED 4 /* valid request this build/device cannot run */
 #define TAMM_ETIMEOUT 5     /* a bounded device-side wait ran out */
 #define TAMM_ECHECK 6       /* a device-side bounds check failed (checked build) */
+#define TAMM_ELIMIT 7       /* a size exceeds a fixed limit of the call */
 
 /* Block-sparsity rule of a tensor (Sec. III.A: spin attributes on tiles and a
  * user-definable non-zero check). */
@@ -233,6 +234,25 @@ TAMM_API tamm_status tamm_energy_async(tamm_ctx* ctx, double alpha, const tamm_t
  * FP64, deterministic.  Synchronises. */
 TAMM_API tamm_status tamm_norm(tamm_ctx* ctx, const tamm_tensor* t, double* result_host);
 TAMM_API tamm_status tamm_norm_async(tamm_ctx* ctx, const tamm_tensor* t, double* result_device);
+
+/* Allocation-free norm.  The paper has no counterpart to this call; it exists
+ * for callers that must not allocate device memory while they run: programs
+ * whose GPU memory is entirely owned by another allocator or pool, latency-
+ * critical loops where a cudaMalloc would synchronise the device, or processes
+ * that reserved all device memory up front.  It needs no context.
+ *   *result_device = sqrt(sum_{e < n} x_device[e]^2)
+ * for n doubles at x_device (device memory, any layout), enqueued on `stream`
+ * (a cudaStream_t, NULL = legacy default stream) of the current device; the
+ * result is one double of device memory written by the call.  Nothing is
+ * allocated: the partial sums live in a fixed 256 KB array inside the library
+ * that every device using the library holds until the process exits.  The
+ * first call on a device looks that array's device address up, so make it
+ * before any stream capture.  All calls on a device share the array, so calls
+ * whose kernels overlap on the GPU (e.g. on two streams) race and must be
+ * serialised by the caller.  Limit: n <= 2^29 (536,870,912 doubles).
+ * Errors: TAMM_EINVAL (n < 0 or a null pointer), TAMM_ELIMIT (n above the
+ * limit), TAMM_ECUDA (no usable current device or a failed launch). */
+TAMM_API tamm_status tamm_norm_noalloc(const double* x_device, int64_t n, double* result_device, void* stream);
 
 #ifdef __cplusplus
 }

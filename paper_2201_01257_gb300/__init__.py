@@ -23,7 +23,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _lock = threading.Lock()
 _lib = None
 
-TAMM_OK, TAMM_EINVAL, TAMM_ENOMEM, TAMM_ECUDA, TAMM_EUNSUPPORTED, TAMM_ETIMEOUT, TAMM_ECHECK = range(7)
+TAMM_OK, TAMM_EINVAL, TAMM_ENOMEM, TAMM_ECUDA, TAMM_EUNSUPPORTED, TAMM_ETIMEOUT, TAMM_ECHECK, TAMM_ELIMIT = range(8)
 TAMM_SYM_DENSE, TAMM_SYM_SPIN, TAMM_SYM_SPIN_IRREP = 0, 1, 2
 TAMM_PREC_F64, TAMM_PREC_OZAKI_BF16, TAMM_PREC_OZAKI_I8 = 0, 1, 2
 KERNEL_CLASSES = ("add", "reduce", "gemm_f64", "slice", "gemm_ozaki")
@@ -31,7 +31,7 @@ TAMM_OPT_OZAKI_CHUNK_K = 0
 SYM = {"dense": TAMM_SYM_DENSE, "spin": TAMM_SYM_SPIN, "spin_irrep": TAMM_SYM_SPIN_IRREP}
 PREC = {"f64": TAMM_PREC_F64, "ozaki_bf16": TAMM_PREC_OZAKI_BF16, "ozaki_i8": TAMM_PREC_OZAKI_I8}
 STATUS_NAMES = {0: "TAMM_OK", 1: "TAMM_EINVAL", 2: "TAMM_ENOMEM", 3: "TAMM_ECUDA", 4: "TAMM_EUNSUPPORTED",
-                5: "TAMM_ETIMEOUT", 6: "TAMM_ECHECK"}
+                5: "TAMM_ETIMEOUT", 6: "TAMM_ECHECK", 7: "TAMM_ELIMIT"}
 
 # C prototypes: (name, restype, argtypes)
 _vp, _i, _i64, _d = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double
@@ -71,6 +71,7 @@ PROTOTYPES = [
     ("tamm_energy_async", _i, [_vp, _d, _vp, _cp, _vp, _cp, _vp]),
     ("tamm_norm", _i, [_vp, _vp, _dp]),
     ("tamm_norm_async", _i, [_vp, _vp, _vp]),
+    ("tamm_norm_noalloc", _i, [_vp, _i64, _vp, _vp]),
 ]
 
 
