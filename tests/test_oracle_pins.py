@@ -367,3 +367,36 @@ def test_contract_boxes_match_single_box(small):
     for (b, lo, ext), got in zip(boxes, outs):
         ref = O.contract_box(0.5, R, "abij", 0.0, T["V_vvvv"], "abef", T["T"], "efij", b, lo, ext)
         assert np.array_equal(got, ref)
+
+
+def _paper_values():
+    vals = {}
+    for line in open(os.path.join(HERE, "golden", "paper_values.txt")):
+        line = line.split("#")[0].strip()
+        if line:
+            k, v = (x.strip() for x in line.split("="))
+            vals[k] = v
+    return vals
+
+
+def test_paper_printed_tiling_example():
+    v = _paper_values()
+    rows = [int(x) for x in v["tensor_const_tiles_rows"].split(",")]
+    cols = [int(x) for x in v["tensor_const_tiles_cols"].split(",")]
+    tM = O.Space([(int(v["tensor_const_rows"]), 1, 0)], tile_sizes=rows)
+    tK = O.Space([(int(v["tensor_const_cols"]), 1, 0)], tile=cols[0])
+    A = O.Tensor([tM, tK], 1, "dense")
+    assert A.n_blocks == int(v["tensor_const_blocks"])
+    assert [t[1] for t in tK.tiles] == cols
+
+
+def test_oracle_regression_values():
+    import json
+
+    g = json.load(open(os.path.join(HERE, "golden", "oracle_config1.json")))
+    w = wl.config1()
+    _, T = O.build_workload(w)
+    O.run_workload(w, T)
+    assert abs(O.norm(T["R"]) - g["norm_R"]) <= 1e-13 * g["norm_R"]
+    assert abs(O.energy(1.0, T["R"], "abij", T["T"], "abij") - g["R_dot_T"]) <= 1e-13 * abs(g["R_dot_T"])
+    assert T["R"].n_blocks == g["n_blocks_R"] and T["V_vvvv"].n_elems == g["n_elems_V_vvvv"]
