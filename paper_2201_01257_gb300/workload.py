@@ -98,6 +98,7 @@ class Runner:
         return None
 
     def run(self, precision="f64", slices: int = 0, steps=None, energy_out=None) -> dict:
+        """Run `steps` (default: every step of the recipe) in order; returns {energy step name: value}."""
         out = {}
         for s in steps if steps is not None else self.w.steps:
             r = self.run_step(s, precision, slices, energy_out)
