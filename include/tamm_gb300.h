@@ -64,6 +64,9 @@ typedef int tamm_status;
 #define TAMM_PREC_OZAKI_BF16 1 /* FP64 operands split into BF16 integer slices, tensor-core products with
                                   exact FP32 accumulation per chunk, FP64 reconstruction */
 #define TAMM_PREC_OZAKI_I8 2   /* INT8 slices: sm_103a has no tcgen05 kind::i8, always TAMM_EUNSUPPORTED */
+#define TAMM_PREC_BF16X3 3     /* each FP64 element rounded to FP32 and split into three BF16 pieces
+                                  (floating, ~24 bits of the element); the six products k+l <= 4 with
+                                  FP32 tensor-core accumulation (error ~1e-7) */
 
 typedef struct tamm_ctx tamm_ctx;
 typedef struct tamm_space tamm_space;

@@ -128,6 +128,30 @@ __device__ __forceinline__ void pack_digits(const double x0, const double x1, in
   }
 }
 
+// bf16 bits of a float, round to nearest even (finite inputs).
+__device__ __forceinline__ uint32_t bf16_rne(float f) {
+  const uint32_t u = __float_as_uint(f);
+  return (u + 0x7FFFu + ((u >> 16) & 1u)) >> 16;
+}
+
+// Floating three-piece split (BF16x3): x ~ a1 + a2 + a3 with each a_i the BF16
+// rounding of what the previous pieces left of fl32(x); the pieces carry about
+// 24 bits relative to x itself.  Products a_k b_l of different k + l land in
+// the same accumulator regions as the integer digits.
+__device__ __forceinline__ void pack_float3(const double x0, const double x1, uint32_t (&w)[3]) {
+  float r[2] = {__double2float_rn(x0), __double2float_rn(x1)};
+  uint32_t b[3][2];
+#pragma unroll
+  for (int k = 0; k < 3; ++k)
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      b[k][j] = bf16_rne(r[j]);
+      r[j] = __fsub_rn(r[j], __uint_as_float(b[k][j] << 16));  // exact: r and the piece share the leading bits
+    }
+#pragma unroll
+  for (int k = 0; k < 3; ++k) w[k] = b[k][0] | (b[k][1] << 16);
+}
+
 // One CTA slices rows [r0, r0+nr) of one block.
 // Dense summed range: the strip is brought into shared memory by 1-D bulk
 // copies (one per row), row maxima come from warp reductions, and each lane
@@ -135,7 +159,7 @@ __device__ __forceinline__ void pack_digits(const double x0, const double x1, in
 // reads are conflict-free and every warp store fills whole 32-byte sectors.
 // Other layouts: 8-wide units read straight from global memory twice, lanes
 // walking rows fastest so that the contiguous direction is coalesced.
-template <int S>
+template <int S, bool kFloat>
 __global__ void __launch_bounds__(256) ozaki_slice_kernel(const double* __restrict__ src,
                                                           const SliceBlock* __restrict__ blocks,
                                                           const SliceItem* __restrict__ items,
@@ -218,6 +242,7 @@ __global__ void __launch_bounds__(256) ozaki_slice_kernel(const double* __restri
       if (lane == 0) {
         int e = kOzExpZero;
         if (m != 0ull) (void)frexp(__longlong_as_double((long long)m), &e);
+        if (kFloat && m != 0ull) e = 6;  // floating pieces: unit scale
         rexp[r] = e;
         exps[B.exp_off + it.r0 + r] = e;
       }
@@ -235,7 +260,8 @@ __global__ void __launch_bounds__(256) ozaki_slice_kernel(const double* __restri
       if (roff[r] >= 0 && e != kOzExpZero && k < K) {
         const double x0 = strip[(size_t)r * K + k];
         const double x1 = k + 1 < K ? strip[(size_t)r * K + k + 1] : 0.0;
-        pack_digits<S>(x0, x1, e, wd, lut);
+        if constexpr (kFloat) pack_float3(x0, x1, wd);
+        else pack_digits<S>(x0, x1, e, wd, lut);
       }
       const int32_t grow = it.r0 + r;
       const int32_t rr = grow % kOzTileM;
@@ -271,6 +297,7 @@ __global__ void __launch_bounds__(256) ozaki_slice_kernel(const double* __restri
   for (int r = tid; r < nr; r += blockDim.x) {
     int e = kOzExpZero;
     if (rmax[r] != 0ull) (void)frexp(__longlong_as_double((long long)rmax[r]), &e);
+    if (kFloat && rmax[r] != 0ull) e = 6;
     rexp[r] = e;
     exps[B.exp_off + it.r0 + r] = e;
   }
@@ -293,7 +320,8 @@ __global__ void __launch_bounds__(256) ozaki_slice_kernel(const double* __restri
 #pragma unroll
       for (int j = 0; j < 8; j += 2) {
         uint32_t wd[S];
-        pack_digits<S>(xs[j], xs[j + 1], e, wd, lut);
+        if constexpr (kFloat) pack_float3(xs[j], xs[j + 1], wd);
+        else pack_digits<S>(xs[j], xs[j + 1], e, wd, lut);
 #pragma unroll
         for (int q = 0; q < S; ++q) packed[q][j >> 1] = wd[q];
       }
@@ -584,7 +612,14 @@ __global__ void __launch_bounds__(kThreads, 1) ozaki_gemm_kernel(const __grid_co
             sm100::tmem_ld8(trow + 0 * 128 + col, r0);
             sm100::tmem_ld8(trow + 1 * 128 + col, r1);
             sm100::tmem_ld8(trow + 2 * 128 + col, r2);
-            sm100::tmem_ld8(trow + 3 * 128 + col, r3);
+            // with S < 4 no product has k + l >= 5: region 3 is never written and holds stale
+            // TMEM contents of an earlier kernel, so it must not be read
+            if constexpr (S >= 4) {
+              sm100::tmem_ld8(trow + 3 * 128 + col, r3);
+            } else {
+#pragma unroll
+              for (int j = 0; j < 8; ++j) r3[j] = 0.0f;
+            }
             sm100::tmem_wait_ld();
 #pragma unroll
             for (int j = 0; j < 8; ++j)
@@ -629,26 +664,31 @@ __global__ void __launch_bounds__(kThreads, 1) ozaki_gemm_kernel(const __grid_co
 // Launchers
 // ======================================================================
 
-template <int S>
+template <int S, bool kFloat = false>
 static cudaError_t slice_dispatch(tamm_ctx* ctx, const double* src, const SliceBlock* blocks, const SliceItem* items,
                                   int64_t n_items, uint8_t* tiles, int32_t* exps) {
   static bool attr = false;
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(ozaki_slice_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         kOzStageBytes);
+    cudaError_t e = cudaFuncSetAttribute(ozaki_slice_kernel<S, kFloat>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, kOzStageBytes);
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  ozaki_slice_kernel<S><<<(unsigned)n_items, 256, kOzStageBytes, ctx->stream>>>(src, blocks, items, tiles, exps,
-                                                                                ctx->d_status);
+  ozaki_slice_kernel<S, kFloat><<<(unsigned)n_items, 256, kOzStageBytes, ctx->stream>>>(src, blocks, items, tiles,
+                                                                                        exps, ctx->d_status);
   return cudaGetLastError();
 }
 
 cudaError_t launch_ozaki_slice(tamm_ctx* ctx, const double* src, const SliceBlock* blocks, const SliceItem* items,
-                               int64_t n_items, int S, uint8_t* tiles, int32_t* exps) {
+                               int64_t n_items, int S, bool float_split, uint8_t* tiles, int32_t* exps) {
   if (n_items == 0) return cudaSuccess;
   kernel_begin(ctx, TAMM_KERNEL_SLICE);
   cudaError_t e = cudaErrorInvalidValue;
+  if (float_split) {
+    if (S == 3) e = slice_dispatch<3, true>(ctx, src, blocks, items, n_items, tiles, exps);
+    kernel_end(ctx, TAMM_KERNEL_SLICE);
+    return e;
+  }
   switch (S) {
     case 3: e = slice_dispatch<3>(ctx, src, blocks, items, n_items, tiles, exps); break;
     case 4: e = slice_dispatch<4>(ctx, src, blocks, items, n_items, tiles, exps); break;
@@ -877,7 +917,8 @@ struct OzakiPlan : Plan {
 };
 
 void run_contract_ozaki(tamm_ctx* ctx, double alpha, tamm_tensor* C, const char* lc, double beta,
-                        const tamm_tensor* A, const char* la, const tamm_tensor* B, const char* lb, int slices) {
+                        const tamm_tensor* A, const char* la, const tamm_tensor* B, const char* lb, int slices,
+                        bool float_split) {
   if (slices == 0) slices = kOzDefaultSlices;
   if (slices < kOzMinSlices || slices > kOzMaxSlices)
     throw Error(TAMM_EINVAL, "ozaki: slices must be %d..%d (0 = %d)", kOzMinSlices, kOzMaxSlices, kOzDefaultSlices);
@@ -898,8 +939,10 @@ void run_contract_ozaki(tamm_ctx* ctx, double alpha, tamm_tensor* C, const char*
   int32_t* eb = (int32_t*)(scratch + p->off_eb);
   const double* lp = p->lay.swap ? B->data : A->data;
   const double* rp = p->lay.swap ? A->data : B->data;
-  cuda_check(launch_ozaki_slice(ctx, lp, p->d_sa, p->d_ia, p->n_ia, slices, ta, ea), "ozaki slice (left)");
-  cuda_check(launch_ozaki_slice(ctx, rp, p->d_sb, p->d_ib, p->n_ib, slices, tb, eb), "ozaki slice (right)");
+  cuda_check(launch_ozaki_slice(ctx, lp, p->d_sa, p->d_ia, p->n_ia, slices, float_split, ta, ea),
+             "ozaki slice (left)");
+  cuda_check(launch_ozaki_slice(ctx, rp, p->d_sb, p->d_ib, p->n_ib, slices, float_split, tb, eb),
+             "ozaki slice (right)");
   double* out = p->perm_out ? (double*)(scratch + p->off_x) : C->data;
   OzProblem prob;
   prob.a_tiles = ta;

@@ -128,8 +128,9 @@ __host__ __device__ constexpr OzSched oz_schedule(int S, bool fuse) {
 
 constexpr int kOzStageBytes = 48 * 1024;  // shared-memory strip of one slicing CTA
 
+// float_split (S = 3 only): BF16x3 floating pieces instead of integer digits.
 cudaError_t launch_ozaki_slice(tamm_ctx* ctx, const double* src, const SliceBlock* blocks, const SliceItem* items,
-                               int64_t n_items, int S, uint8_t* tiles, int32_t* exps);
+                               int64_t n_items, int S, bool float_split, uint8_t* tiles, int32_t* exps);
 // Persistent launch over `n_items` work items of up to kOzMaxProblems problems.
 cudaError_t launch_ozaki_gemm(tamm_ctx* ctx, const OzProblem* problems, int n_problems, const OzItem* items,
                               int64_t n_items, int S, int chunk_tiles);

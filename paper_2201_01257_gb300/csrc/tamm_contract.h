@@ -73,7 +73,9 @@ struct ContractLayout {
   void enumerate();
 };
 
+// slices: integer digit slices (3..8); float_split: BF16x3 floating pieces (slices must be 3)
 void run_contract_ozaki(tamm_ctx* ctx, double alpha, tamm_tensor* C, const char* lc, double beta,
-                        const tamm_tensor* A, const char* la, const tamm_tensor* B, const char* lb, int slices);
+                        const tamm_tensor* A, const char* la, const tamm_tensor* B, const char* lb, int slices,
+                        bool float_split);
 
 }  // namespace tamm

@@ -368,7 +368,12 @@ void run_contract(tamm_ctx* ctx, double alpha, tamm_tensor* C, const char* lc, d
   if (precision == TAMM_PREC_OZAKI_I8)
     throw Error(TAMM_EUNSUPPORTED, "INT8 slices: sm_103a has no tcgen05 kind::i8 tensor-core product");
   if (precision == TAMM_PREC_OZAKI_BF16) {
-    run_contract_ozaki(ctx, alpha, C, lc, beta, A, la, B, lb, slices);
+    run_contract_ozaki(ctx, alpha, C, lc, beta, A, la, B, lb, slices, false);
+    return;
+  }
+  if (precision == TAMM_PREC_BF16X3) {
+    if (slices != 0 && slices != 3) throw Error(TAMM_EINVAL, "bf16x3 uses exactly three slices");
+    run_contract_ozaki(ctx, alpha, C, lc, beta, A, la, B, lb, 3, true);
     return;
   }
   if (precision != TAMM_PREC_F64) throw Error(TAMM_EINVAL, "contract: unknown precision %d", precision);

@@ -161,3 +161,23 @@ def test_bad_slice_count(gpu_lib):
     with pytest.raises(tg.TammError) as e:
         ctx.contract(0.5, t["R"], "abij", 0.0, t["V_vvvv"], "abef", t["T"], "efij", "ozaki_bf16", 12)
     assert e.value.status == tg.TAMM_EINVAL
+
+
+def test_three_slices_after_six_slices(gpu_lib):
+    """TMEM keeps an earlier kernel's accumulators: a 3-slice product (no tail region) run after a
+    6-slice one must not pick them up, in either split form."""
+    rng = np.random.default_rng(12)
+    fill = lambda k, n: rng.standard_normal(n) if k != "R" else np.zeros(n)
+    tg = gpu_lib
+    ctx = tg.Context(0)
+    o = ctx.space([(4, 1, 0), (4, -1, 0)], 4)
+    v = ctx.space([(12, 1, 0), (12, -1, 0)], 4)
+    T = ctx.tensor([v, v, o, o], 2)
+    V = ctx.tensor([v] * 4, 2)
+    T.upload(rng.standard_normal(T.n_elems))
+    ctx.contract(0.5, V, "abef", 0.0, T, "abij", T, "efij", "f64", 0)
+    ref = V.download()
+    ctx.contract(0.5, V, "abef", 0.0, T, "abij", T, "efij", "ozaki_bf16", 6)
+    for prec, S, tol in (("bf16x3", 0, 1e-6), ("ozaki_bf16", 3, 1e-5)):
+        ctx.contract(0.5, V, "abef", 0.0, T, "abij", T, "efij", prec, S)
+        assert rel_err(V.download(), ref) <= tol, prec
