@@ -71,6 +71,7 @@ typedef int tamm_status;
 typedef struct tamm_ctx tamm_ctx;
 typedef struct tamm_space tamm_space;
 typedef struct tamm_tensor tamm_tensor;
+typedef struct tamm_graph tamm_graph;
 
 /* Stream-ordered device allocator: return `bytes` of device memory usable by
  * work enqueued on `stream` after this call, or NULL.  `release` may be
@@ -256,6 +257,51 @@ TAMM_API tamm_status tamm_norm_async(tamm_ctx* ctx, const tamm_tensor* t, double
  * Errors: TAMM_EINVAL (n < 0 or a null pointer), TAMM_ELIMIT (n above the
  * limit), TAMM_ECUDA (no usable current device or a failed launch). */
 TAMM_API tamm_status tamm_norm_noalloc(const double* x_device, int64_t n, double* result_device, void* stream);
+
+/* ------------------------------------------------------ grouped execution */
+
+/* Contraction groups: the independent contractions of one dependency level
+ * executed together (Sec. III.A deferred execution; the scheduler runs the
+ * operations of a level as one batch with no synchronisation between them).
+ * Between tamm_group_begin and tamm_group_end, split-precision tamm_contract
+ * calls (TAMM_PREC_OZAKI_BF16 / TAMM_PREC_BF16X3) are validated, planned and
+ * recorded but not run; every other operation (FP64 contractions, adds,
+ * energies, norms, stream changes) is refused with TAMM_EINVAL.  tamm_group_end
+ * checks that no recorded output overlaps another contraction's input or
+ * output (TAMM_EINVAL otherwise, and nothing runs), then enqueues, on the
+ * context's stream: the operand slicing of every contraction, one persistent
+ * grouped tcgen05 GEMM launch over all their block tasks per slice count (at
+ * most 64 contractions per launch), and the output permutations.  Results are
+ * bitwise those of running the contractions one by one.  The group's scratch
+ * (all operand slice images at once) comes from the context's scratch buffer.
+ * Errors: TAMM_EINVAL (nesting, refused call, aliasing), TAMM_ENOMEM,
+ * TAMM_ECUDA. */
+TAMM_API tamm_status tamm_group_begin(tamm_ctx* ctx);
+TAMM_API tamm_status tamm_group_end(tamm_ctx* ctx);
+/* Close the open group without running what it recorded.  Errors: TAMM_EINVAL (no open group). */
+TAMM_API tamm_status tamm_group_cancel(tamm_ctx* ctx);
+
+/* CUDA-graph capture of a sequence of library calls on the context's stream,
+ * replayed with one launch (Sec. III.A: the deferred operation list executed
+ * as a unit).  The context must be on a created stream (not the legacy or
+ * per-thread default stream) and not profiling.  Calls between begin and end
+ * are captured, not run; they may not allocate device memory (plans, scratch
+ * and reduction buffers must already exist: run the same calls once before
+ * capturing) nor synchronise (tamm_energy, tamm_norm, tamm_sync are refused;
+ * use the _async forms).  A refused call makes tamm_graph_end fail.  Groups
+ * may be opened and closed inside a capture.  The graph holds the device
+ * pointers it was captured with: the tensors and their data must stay alive
+ * and bound to the same buffers while it is launched; their contents may
+ * change between launches.  tamm_graph_launch enqueues the graph on the
+ * context's stream and adds its kernel count to tamm_ctx_launch_count.
+ * Errors: TAMM_EINVAL, TAMM_ECUDA. */
+TAMM_API tamm_status tamm_graph_begin(tamm_ctx* ctx);
+TAMM_API tamm_status tamm_graph_end(tamm_ctx* ctx, tamm_graph** graph);
+TAMM_API tamm_status tamm_graph_launch(tamm_graph* graph);
+/* Number of library kernels one launch of the graph runs. */
+TAMM_API tamm_status tamm_graph_info(const tamm_graph* graph, int64_t* kernel_launches);
+/* NULL is ignored.  The graph must not be running (synchronise first). */
+TAMM_API void tamm_graph_destroy(tamm_graph* graph);
 
 #ifdef __cplusplus
 }

@@ -11,9 +11,11 @@ is present, calls raise instead of falling back.
 """
 from __future__ import annotations
 
+import contextlib
 import ctypes
 import os
 import threading
+import types
 
 import numpy as np
 
@@ -73,6 +75,14 @@ PROTOTYPES = [
     ("tamm_norm", _i, [_vp, _vp, _dp]),
     ("tamm_norm_async", _i, [_vp, _vp, _vp]),
     ("tamm_norm_noalloc", _i, [_vp, _i64, _vp, _vp]),
+    ("tamm_group_begin", _i, [_vp]),
+    ("tamm_group_end", _i, [_vp]),
+    ("tamm_group_cancel", _i, [_vp]),
+    ("tamm_graph_begin", _i, [_vp]),
+    ("tamm_graph_end", _i, [_vp, ctypes.POINTER(_vp)]),
+    ("tamm_graph_launch", _i, [_vp]),
+    ("tamm_graph_info", _i, [_vp, _i64p]),
+    ("tamm_graph_destroy", None, [_vp]),
 ]
 
 
@@ -249,6 +259,42 @@ class Context:
         self.check(self.lib.tamm_ctx_profile_read(self.handle, ms, cnt), "tamm_ctx_profile_read")
         return {k: (ms[i], cnt[i]) for i, k in enumerate(KERNEL_CLASSES)}
 
+    # grouped execution ---------------------------------------------------
+    def group_begin(self) -> None:
+        self.check(self.lib.tamm_group_begin(self.handle), "tamm_group_begin")
+
+    def group_end(self) -> None:
+        self.check(self.lib.tamm_group_end(self.handle), "tamm_group_end")
+
+    @contextlib.contextmanager
+    def group(self):
+        """Split-precision contractions issued inside run as one grouped launch on exit."""
+        self.group_begin()
+        try:
+            yield self
+        except BaseException:
+            self.lib.tamm_group_cancel(self.handle)  # drop what was recorded; the error propagates
+            raise
+        self.group_end()
+
+    def graph_begin(self) -> None:
+        self.check(self.lib.tamm_graph_begin(self.handle), "tamm_graph_begin")
+
+    def graph_end(self) -> "Graph":
+        h = ctypes.c_void_p()
+        self.check(self.lib.tamm_graph_end(self.handle, ctypes.byref(h)), "tamm_graph_end")
+        return Graph(self, h)
+
+    @contextlib.contextmanager
+    def capture(self):
+        """Capture the library calls of the block into a Graph (``with ctx.capture() as g: ...; g.graph.launch()``)."""
+        holder = types.SimpleNamespace(graph=None)
+        self.graph_begin()
+        try:
+            yield holder
+        finally:
+            holder.graph = self.graph_end()
+
     def copy_from_host(self, T, host: np.ndarray) -> None:
         assert host.dtype == np.float64 and host.flags.c_contiguous and host.size >= T.n_elems
         self.check(self.lib.tamm_tensor_copy_from_host(self.handle, T.handle, ctypes.c_void_p(host.ctypes.data)),
@@ -258,6 +304,34 @@ class Context:
         assert host.dtype == np.float64 and host.flags.c_contiguous and host.size >= T.n_elems
         self.check(self.lib.tamm_tensor_copy_to_host(self.handle, T.handle, ctypes.c_void_p(host.ctypes.data)),
                    "tamm_tensor_copy_to_host")
+
+
+class Graph:
+    """A captured sequence of library calls (tamm_graph), replayed with one CUDA-graph launch."""
+
+    def __init__(self, ctx: Context, handle):
+        self.ctx = ctx
+        self.handle = handle
+
+    def launch(self) -> None:
+        self.ctx.check(self.ctx.lib.tamm_graph_launch(self.handle), "tamm_graph_launch")
+
+    @property
+    def kernel_launches(self) -> int:
+        n = ctypes.c_int64()
+        self.ctx.check(self.ctx.lib.tamm_graph_info(self.handle, ctypes.byref(n)), "tamm_graph_info")
+        return n.value
+
+    def destroy(self) -> None:
+        if self.handle:
+            self.ctx.lib.tamm_graph_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
 
 
 class Space:

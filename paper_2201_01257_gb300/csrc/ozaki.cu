@@ -343,7 +343,6 @@ __global__ void __launch_bounds__(256) ozaki_slice_kernel(const double* __restri
 // ======================================================================
 
 struct OzParams {
-  const OzItem* items;
   int64_t n_items;
   int* status;
   int stages;
@@ -425,6 +424,13 @@ __device__ __forceinline__ void issue_ops(uint32_t tmem, uint64_t a0, uint64_t b
   }
 }
 
+// Problem and work item of global item i (problems hold consecutive item ranges).
+__device__ __forceinline__ int problem_of(const OzParams& p, int64_t i) {
+  int q = 0;
+  while (q + 1 < p.n_problems && i >= p.problems[q + 1].item_begin) ++q;
+  return q;
+}
+
 template <int S>
 __global__ void __launch_bounds__(kThreads, 1) ozaki_gemm_kernel(const __grid_constant__ OzParams p) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
@@ -473,11 +479,12 @@ __global__ void __launch_bounds__(kThreads, 1) ozaki_gemm_kernel(const __grid_co
       int stage = 0;
       uint32_t phase = 0, issued_mask = 0, issued_parity = 0;
       for (int64_t i = blockIdx.x; i < p.n_items && !*abort_flag; i += gridDim.x) {
-        const OzItem it = p.items[i];
-        const OzTask* tasks = p.problems[it.problem].tasks;
-        const uint8_t* a_tiles = p.problems[it.problem].a_tiles;
-        const uint8_t* b_tiles = p.problems[it.problem].b_tiles;
-        const OzGroup g = p.problems[it.problem].groups[it.group];
+        const int q = problem_of(p, i);
+        const OzItem it = p.problems[q].items[i - p.problems[q].item_begin];
+        const OzTask* tasks = p.problems[q].tasks;
+        const uint8_t* a_tiles = p.problems[q].a_tiles;
+        const uint8_t* b_tiles = p.problems[q].b_tiles;
+        const OzGroup g = p.problems[q].groups[it.group];
         for (int t = g.task_begin; t < g.task_end && !*abort_flag; ++t) {
           const OzTask tk = tasks[t];
           const uint8_t* a = a_tiles + (size_t)(tk.a_tile + (int64_t)it.mt * tk.k_tiles) * half_bytes;
@@ -513,9 +520,10 @@ __global__ void __launch_bounds__(kThreads, 1) ozaki_gemm_kernel(const __grid_co
       uint32_t phase = 0, acc_phase = 0;
       bool ok = true;
       for (int64_t i = blockIdx.x; i < p.n_items && ok; i += gridDim.x) {
-        const OzItem it = p.items[i];
-        const OzTask* tasks = p.problems[it.problem].tasks;
-        const OzGroup g = p.problems[it.problem].groups[it.group];
+        const int q = problem_of(p, i);
+        const OzItem it = p.problems[q].items[i - p.problems[q].item_begin];
+        const OzTask* tasks = p.problems[q].tasks;
+        const OzGroup g = p.problems[q].groups[it.group];
         const int n_valid = min(kOzTileN, g.N - it.nt * kOzTileN);
         const bool full_tile = n_valid == kOzTileN;
         const uint32_t idesc_ragged = sm100::idesc_bf16_f32(128, (uint32_t)((n_valid + 15) & ~15));
@@ -570,11 +578,12 @@ __global__ void __launch_bounds__(kThreads, 1) ozaki_gemm_kernel(const __grid_co
     bool ok = true;
     // Every epilogue warp passes the same named barriers on every path (also after a timeout).
     for (int64_t i = blockIdx.x; i < p.n_items; i += gridDim.x) {
-      const OzItem it = p.items[i];
-      const OzTask* tasks = p.problems[it.problem].tasks;
-      const int32_t* a_exp = p.problems[it.problem].a_exp;
-      const int32_t* b_exp = p.problems[it.problem].b_exp;
-      const OzGroup g = p.problems[it.problem].groups[it.group];
+      const int q = problem_of(p, i);
+      const OzItem it = p.problems[q].items[i - p.problems[q].item_begin];
+      const OzTask* tasks = p.problems[q].tasks;
+      const int32_t* a_exp = p.problems[q].a_exp;
+      const int32_t* b_exp = p.problems[q].b_exp;
+      const OzGroup g = p.problems[q].groups[it.group];
       const int n_valid = min(kOzTileN, g.N - it.nt * kOzTileN);
       epi_barrier();  // the previous item's output writes (which read fref) are done
       int Eref = kOzExpZero;
@@ -634,8 +643,8 @@ __global__ void __launch_bounds__(kThreads, 1) ozaki_gemm_kernel(const __grid_co
       if (ok) {
         const int grow = it.mt * kOzTileM + row;
         if (grow < g.M) {
-          double* crow = p.problems[it.problem].c + g.c_off + (int64_t)grow * g.N + (int64_t)it.nt * kOzTileN;
-          const double alpha = p.problems[it.problem].alpha, beta = p.problems[it.problem].beta;
+          double* crow = p.problems[q].c + g.c_off + (int64_t)grow * g.N + (int64_t)it.nt * kOzTileN;
+          const double alpha = p.problems[q].alpha, beta = p.problems[q].beta;
 #pragma unroll
           for (int j = 0; j < 64; ++j) {
             const int col = c0 + j;
@@ -725,13 +734,17 @@ static cudaError_t gemm_dispatch(tamm_ctx* ctx, const OzParams& p, int grid) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_ozaki_gemm(tamm_ctx* ctx, const OzProblem* problems, int n_problems, const OzItem* items,
-                              int64_t n_items, int S, int chunk_tiles) {
-  if (n_items == 0) return cudaSuccess;
+cudaError_t launch_ozaki_gemm(tamm_ctx* ctx, OzProblem* problems, const int64_t* n_items_per_problem,
+                              int n_problems, int S, int chunk_tiles) {
   if (chunk_tiles < 1 || chunk_tiles > kOzChunkTiles) return cudaErrorInvalidValue;
   if (n_problems < 1 || n_problems > kOzMaxProblems) return cudaErrorInvalidValue;
+  int64_t n_items = 0;
+  for (int i = 0; i < n_problems; ++i) {
+    problems[i].item_begin = n_items;
+    n_items += n_items_per_problem[i];
+  }
+  if (n_items == 0) return cudaSuccess;
   static OzParams p;  // large parameter block; copied into the launch
-  p.items = items;
   p.n_items = n_items;
   p.status = ctx->d_status;
   p.stages = oz_stages(S);
@@ -929,36 +942,89 @@ void run_contract_ozaki(tamm_ctx* ctx, double alpha, tamm_tensor* C, const char*
   if (itp != ctx->plans.end()) {
     p = static_cast<OzakiPlan*>(itp->second.get());
   } else {
+    if (ctx->capturing) throw Error(TAMM_EINVAL, "a new contraction plan cannot be built during graph capture");
     p = new OzakiPlan(ctx, C, lc, A, la, B, lb, slices);
     ctx->plans[key].reset(p);
   }
-  char* scratch = (char*)ctx_scratch(ctx, p->scratch_bytes);
-  uint8_t* ta = (uint8_t*)(scratch + p->off_ta);
-  uint8_t* tb = (uint8_t*)(scratch + p->off_tb);
-  int32_t* ea = (int32_t*)(scratch + p->off_ea);
-  int32_t* eb = (int32_t*)(scratch + p->off_eb);
-  const double* lp = p->lay.swap ? B->data : A->data;
-  const double* rp = p->lay.swap ? A->data : B->data;
-  cuda_check(launch_ozaki_slice(ctx, lp, p->d_sa, p->d_ia, p->n_ia, slices, float_split, ta, ea),
-             "ozaki slice (left)");
-  cuda_check(launch_ozaki_slice(ctx, rp, p->d_sb, p->d_ib, p->n_ib, slices, float_split, tb, eb),
-             "ozaki slice (right)");
-  double* out = p->perm_out ? (double*)(scratch + p->off_x) : C->data;
-  OzProblem prob;
-  prob.a_tiles = ta;
-  prob.b_tiles = tb;
-  prob.a_exp = ea;
-  prob.b_exp = eb;
-  prob.groups = p->d_groups;
-  prob.tasks = p->d_tasks;
-  prob.c = out;
-  prob.alpha = alpha;
-  prob.beta = p->perm_out ? 0.0 : beta;
-  cuda_check(launch_ozaki_gemm(ctx, &prob, 1, p->d_items, p->n_items, slices, ctx->oz_chunk_k / kOzTileK),
-             "ozaki gemm");
-  if (p->perm_out) {
-    const double one = 1.0;
-    p->perm_out->run(C->data, out, beta, &one);
+  OzOpRecord op;
+  op.plan = p;
+  op.slices = slices;
+  op.float_split = float_split;
+  op.alpha = alpha;
+  op.beta = beta;
+  op.c = C->data;
+  const tamm_tensor* L = p->lay.swap ? B : A;
+  const tamm_tensor* R = p->lay.swap ? A : B;
+  op.left = L->data;
+  op.right = R->data;
+  op.c_bytes = (size_t)C->n_elems * 8;
+  op.left_bytes = (size_t)L->n_elems * 8;
+  op.right_bytes = (size_t)R->n_elems * 8;
+  if (ctx->group_active) {
+    ctx->group_ops.push_back(op);
+    return;
+  }
+  execute_ozaki(ctx, {op});
+}
+
+void execute_ozaki(tamm_ctx* ctx, const std::vector<OzOpRecord>& ops) {
+  if (ops.empty()) return;
+  auto align = [](size_t x) { return (x + 1023) & ~size_t(1023); };
+  std::vector<size_t> base(ops.size());
+  size_t total = 0;
+  for (size_t i = 0; i < ops.size(); ++i) {
+    base[i] = total;
+    total += align(static_cast<OzakiPlan*>(ops[i].plan)->scratch_bytes);
+  }
+  char* scratch = (char*)ctx_scratch(ctx, total);
+  std::vector<OzProblem> probs(ops.size());
+  std::vector<int64_t> counts(ops.size());
+  for (size_t i = 0; i < ops.size(); ++i) {
+    const OzakiPlan* p = static_cast<const OzakiPlan*>(ops[i].plan);
+    char* s = scratch + base[i];
+    uint8_t* ta = (uint8_t*)(s + p->off_ta);
+    uint8_t* tb = (uint8_t*)(s + p->off_tb);
+    int32_t* ea = (int32_t*)(s + p->off_ea);
+    int32_t* eb = (int32_t*)(s + p->off_eb);
+    cuda_check(launch_ozaki_slice(ctx, ops[i].left, p->d_sa, p->d_ia, p->n_ia, ops[i].slices, ops[i].float_split,
+                                  ta, ea),
+               "ozaki slice (left)");
+    cuda_check(launch_ozaki_slice(ctx, ops[i].right, p->d_sb, p->d_ib, p->n_ib, ops[i].slices,
+                                  ops[i].float_split, tb, eb),
+               "ozaki slice (right)");
+    OzProblem& pr = probs[i];
+    pr.a_tiles = ta;
+    pr.b_tiles = tb;
+    pr.a_exp = ea;
+    pr.b_exp = eb;
+    pr.groups = p->d_groups;
+    pr.tasks = p->d_tasks;
+    pr.items = p->d_items;
+    pr.c = p->perm_out ? (double*)(s + p->off_x) : ops[i].c;
+    pr.alpha = ops[i].alpha;
+    pr.beta = p->perm_out ? 0.0 : ops[i].beta;
+    counts[i] = p->n_items;
+  }
+  // one GEMM launch per slice count, at most kOzMaxProblems problems each
+  std::vector<bool> done(ops.size(), false);
+  for (size_t i = 0; i < ops.size(); ++i) {
+    if (done[i]) continue;
+    std::vector<OzProblem> batch;
+    std::vector<int64_t> n;
+    for (size_t j = i; j < ops.size() && (int)batch.size() < kOzMaxProblems; ++j) {
+      if (done[j] || ops[j].slices != ops[i].slices) continue;
+      batch.push_back(probs[j]);
+      n.push_back(counts[j]);
+      done[j] = true;
+    }
+    cuda_check(launch_ozaki_gemm(ctx, batch.data(), n.data(), (int)batch.size(), ops[i].slices,
+                                 ctx->oz_chunk_k / kOzTileK),
+               "ozaki gemm");
+  }
+  const double one = 1.0;
+  for (size_t i = 0; i < ops.size(); ++i) {
+    const OzakiPlan* p = static_cast<const OzakiPlan*>(ops[i].plan);
+    if (p->perm_out) p->perm_out->run(ops[i].c, (double*)(scratch + base[i] + p->off_x), ops[i].beta, &one);
   }
 }
 

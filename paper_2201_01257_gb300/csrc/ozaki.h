@@ -74,7 +74,8 @@ struct OzTask {
   int32_t pad;
 };
 
-// One contraction inside a (possibly grouped) persistent GEMM launch.
+// One contraction inside a (possibly grouped) persistent GEMM launch.  Its
+// work items are global items [item_begin, item_begin + n_items) of the launch.
 struct OzProblem {
   const uint8_t* a_tiles;
   const uint8_t* b_tiles;
@@ -82,6 +83,8 @@ struct OzProblem {
   const int32_t* b_exp;
   const OzGroup* groups;
   const OzTask* tasks;
+  const struct OzItem* items;
+  int64_t item_begin;
   double* c;
   double alpha, beta;
 };
@@ -131,8 +134,9 @@ constexpr int kOzStageBytes = 48 * 1024;  // shared-memory strip of one slicing 
 // float_split (S = 3 only): BF16x3 floating pieces instead of integer digits.
 cudaError_t launch_ozaki_slice(tamm_ctx* ctx, const double* src, const SliceBlock* blocks, const SliceItem* items,
                                int64_t n_items, int S, bool float_split, uint8_t* tiles, int32_t* exps);
-// Persistent launch over `n_items` work items of up to kOzMaxProblems problems.
-cudaError_t launch_ozaki_gemm(tamm_ctx* ctx, const OzProblem* problems, int n_problems, const OzItem* items,
-                              int64_t n_items, int S, int chunk_tiles);
+// One launch over the work items of up to kOzMaxProblems problems (item_begin
+// of each problem is filled in here); `n_items` is the total.
+cudaError_t launch_ozaki_gemm(tamm_ctx* ctx, OzProblem* problems, const int64_t* n_items_per_problem,
+                              int n_problems, int S, int chunk_tiles);
 
 }  // namespace tamm

@@ -10,6 +10,7 @@
 #include <stdexcept>
 
 #include "tamm_internal.h"
+#include "tamm_contract.h"
 #include "tamm_plan.h"
 
 using namespace tamm;
@@ -41,14 +42,23 @@ static tamm_status guarded(tamm_ctx* ctx, F&& f) {
     return TAMM_OK;
   } catch (const Error& e) {
     if (ctx) ctx->last_error = e.msg;
+    if (ctx && ctx->capturing) ctx->capture_failed = true;
     return e.status;
   } catch (const std::bad_alloc&) {
     if (ctx) ctx->last_error = "host allocation failed";
+    if (ctx && ctx->capturing) ctx->capture_failed = true;
     return TAMM_ENOMEM;
   } catch (const std::exception& e) {
     if (ctx) ctx->last_error = e.what();
+    if (ctx && ctx->capturing) ctx->capture_failed = true;
     return TAMM_EINVAL;
   }
+}
+
+// Operations other than split-precision contractions run at once, so inside a
+// group they would overtake the recorded contractions: refuse them.
+static void no_group(tamm_ctx* ctx, const char* what) {
+  if (ctx->group_active) throw Error(TAMM_EINVAL, "%s cannot be issued inside a contraction group", what);
 }
 
 // --------------------------------------------------------------- allocation
@@ -61,6 +71,9 @@ void require_device(tamm_ctx* ctx) {
 
 void* ctx_alloc(tamm_ctx* ctx, size_t bytes) {
   require_device(ctx);
+  if (ctx->capturing)
+    throw Error(TAMM_EINVAL, "device allocation of %zu bytes during graph capture (run the same operations once "
+                "before capturing so that plans and scratch exist)", bytes);
   if (bytes == 0) bytes = 256;
   void* p = nullptr;
   if (ctx->allocator.alloc) {
@@ -88,6 +101,7 @@ void ctx_free(tamm_ctx* ctx, void* p, size_t bytes) {
 void* ctx_scratch(tamm_ctx* ctx, size_t bytes) {
   bytes = (bytes + 255) & ~size_t(255);
   if (ctx->scratch.bytes < bytes) {
+    if (ctx->capturing) throw Error(TAMM_EINVAL, "scratch growth during graph capture");
     const size_t grow = std::max(bytes, ctx->scratch.bytes + ctx->scratch.bytes / 4);
     ctx_free(ctx, ctx->scratch.ptr, ctx->scratch.bytes);
     ctx->scratch.ptr = nullptr;
@@ -100,6 +114,7 @@ void* ctx_scratch(tamm_ctx* ctx, size_t bytes) {
 
 double* ctx_reduce_buffer(tamm_ctx* ctx, size_t n) {
   if (ctx->reduce_cap < n) {
+    if (ctx->capturing) throw Error(TAMM_EINVAL, "reduction buffer growth during graph capture");
     ctx_free(ctx, ctx->d_reduce, ctx->reduce_cap * sizeof(double));
     ctx->d_reduce = nullptr;
     ctx->reduce_cap = 0;
@@ -157,6 +172,7 @@ extern "C" tamm_status tamm_ctx_set_stream(tamm_ctx* ctx, void* stream) {
   if (!ctx) return TAMM_EINVAL;
   return guarded(ctx, [&] {
     require_device(ctx);
+    if (ctx->capturing || ctx->group_active) throw Error(TAMM_EINVAL, "stream change inside a group or capture");
     cuda_check(cudaStreamSynchronize(ctx->stream), "stream sync");
     ctx->stream = (cudaStream_t)stream;
   });
@@ -206,6 +222,7 @@ extern "C" const char* tamm_last_error(const tamm_ctx* ctx) { return ctx ? ctx->
 namespace tamm {
 // Synchronise and turn a recorded device status into an error.
 void sync_and_check(tamm_ctx* ctx) {
+  if (ctx->capturing) throw Error(TAMM_EINVAL, "synchronising call during graph capture");
   cuda_check(cudaStreamSynchronize(ctx->stream), "stream synchronize");
   int st = 0;
   cuda_check(cudaMemcpy(&st, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost), "status read");
@@ -478,6 +495,8 @@ extern "C" tamm_status tamm_contract(tamm_ctx* ctx, double alpha, tamm_tensor* C
   if (!ctx) return TAMM_EINVAL;
   return guarded(ctx, [&] {
     require_device(ctx);
+    if (ctx->group_active && precision != TAMM_PREC_OZAKI_BF16 && precision != TAMM_PREC_BF16X3)
+      throw Error(TAMM_EINVAL, "only split-precision contractions can be grouped");
     run_contract(ctx, alpha, C, lc, beta, A, la, B, lb, precision, slices);
   });
 }
@@ -494,6 +513,7 @@ extern "C" tamm_status tamm_add(tamm_ctx* ctx, tamm_tensor* C, const char* lc, d
   if (!ctx) return TAMM_EINVAL;
   return guarded(ctx, [&] {
     require_device(ctx);
+    no_group(ctx, "an add");
     run_add(ctx, C, lc, beta, A, n_terms, la, alpha);
   });
 }
@@ -504,6 +524,7 @@ extern "C" tamm_status tamm_energy_async(tamm_ctx* ctx, double alpha, const tamm
   return guarded(ctx, [&] {
     require_device(ctx);
     if (!result_device) throw Error(TAMM_EINVAL, "energy: null result pointer");
+    no_group(ctx, "an energy");
     run_energy(ctx, alpha, A, la, B, lb, result_device);
   });
 }
@@ -514,6 +535,8 @@ extern "C" tamm_status tamm_energy(tamm_ctx* ctx, double alpha, const tamm_tenso
   return guarded(ctx, [&] {
     require_device(ctx);
     if (!result_host) throw Error(TAMM_EINVAL, "energy: null result pointer");
+    no_group(ctx, "an energy");
+    if (ctx->capturing) throw Error(TAMM_EINVAL, "synchronising call during graph capture");
     double* out = result_slot(ctx, 0);
     run_energy(ctx, alpha, A, la, B, lb, out);
     cuda_check(cudaMemcpyAsync(ctx->h_result, out, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream), "D2H");
@@ -527,6 +550,7 @@ extern "C" tamm_status tamm_norm_async(tamm_ctx* ctx, const tamm_tensor* t, doub
   return guarded(ctx, [&] {
     require_device(ctx);
     if (!result_device) throw Error(TAMM_EINVAL, "norm: null result pointer");
+    no_group(ctx, "a norm");
     run_norm(ctx, t, result_device);
   });
 }
@@ -536,10 +560,147 @@ extern "C" tamm_status tamm_norm(tamm_ctx* ctx, const tamm_tensor* t, double* re
   return guarded(ctx, [&] {
     require_device(ctx);
     if (!result_host) throw Error(TAMM_EINVAL, "norm: null result pointer");
+    no_group(ctx, "a norm");
+    if (ctx->capturing) throw Error(TAMM_EINVAL, "synchronising call during graph capture");
     double* out = result_slot(ctx, 1);
     run_norm(ctx, t, out);
     cuda_check(cudaMemcpyAsync(ctx->h_result, out, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream), "D2H");
     sync_and_check(ctx);
     *result_host = ctx->h_result[0];
   });
+}
+
+// ------------------------------------------------- groups and graph capture
+
+namespace {
+
+bool overlaps(const void* a, size_t na, const void* b, size_t nb) {
+  if (!a || !b || !na || !nb) return false;
+  const char* x = (const char*)a;
+  const char* y = (const char*)b;
+  return x < y + nb && y < x + na;
+}
+
+}  // namespace
+
+struct tamm_graph {
+  tamm_ctx* ctx = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  int64_t launches = 0;  // kernels one replay runs
+};
+
+extern "C" tamm_status tamm_group_begin(tamm_ctx* ctx) {
+  if (!ctx) return TAMM_EINVAL;
+  return guarded(ctx, [&] {
+    require_device(ctx);
+    if (ctx->group_active) throw Error(TAMM_EINVAL, "a contraction group is already open");
+    ctx->group_active = true;
+    ctx->group_ops.clear();
+  });
+}
+
+extern "C" tamm_status tamm_group_end(tamm_ctx* ctx) {
+  if (!ctx) return TAMM_EINVAL;
+  return guarded(ctx, [&] {
+    require_device(ctx);
+    if (!ctx->group_active) throw Error(TAMM_EINVAL, "no contraction group is open");
+    std::vector<OzOpRecord> ops;
+    ops.swap(ctx->group_ops);
+    ctx->group_active = false;
+    // every contraction of a group reads inputs that no other one writes, and
+    // no two write overlapping outputs: they may then run in any order
+    for (size_t i = 0; i < ops.size(); ++i) {
+      for (size_t j = 0; j < ops.size(); ++j) {
+        if (overlaps(ops[i].c, ops[i].c_bytes, ops[j].left, ops[j].left_bytes) ||
+            overlaps(ops[i].c, ops[i].c_bytes, ops[j].right, ops[j].right_bytes))
+          throw Error(TAMM_EINVAL, "group: output of contraction %zu overlaps an input of contraction %zu", i, j);
+        if (j > i && overlaps(ops[i].c, ops[i].c_bytes, ops[j].c, ops[j].c_bytes))
+          throw Error(TAMM_EINVAL, "group: contractions %zu and %zu write overlapping outputs", i, j);
+      }
+    }
+    execute_ozaki(ctx, ops);
+  });
+}
+
+extern "C" tamm_status tamm_group_cancel(tamm_ctx* ctx) {
+  if (!ctx) return TAMM_EINVAL;
+  return guarded(ctx, [&] {
+    if (!ctx->group_active) throw Error(TAMM_EINVAL, "no contraction group is open");
+    ctx->group_active = false;
+    ctx->group_ops.clear();
+  });
+}
+
+extern "C" tamm_status tamm_graph_begin(tamm_ctx* ctx) {
+  if (!ctx) return TAMM_EINVAL;
+  return guarded(ctx, [&] {
+    require_device(ctx);
+    if (ctx->capturing) throw Error(TAMM_EINVAL, "a graph capture is already open");
+    if (ctx->group_active) throw Error(TAMM_EINVAL, "graph capture cannot start inside a contraction group");
+    if (ctx->stream == nullptr || ctx->stream == cudaStreamLegacy || ctx->stream == cudaStreamPerThread)
+      throw Error(TAMM_EINVAL, "graph capture needs the context on a created (non-default) stream");
+    if (ctx->profiling) throw Error(TAMM_EINVAL, "switch profiling off before graph capture");
+    cuda_check(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal), "cudaStreamBeginCapture");
+    ctx->capturing = true;
+    ctx->capture_failed = false;
+    ctx->capture_launch0 = ctx->launches;
+  });
+}
+
+extern "C" tamm_status tamm_graph_end(tamm_ctx* ctx, tamm_graph** out) {
+  if (!ctx || !out) return TAMM_EINVAL;
+  *out = nullptr;
+  return guarded(ctx, [&] {
+    require_device(ctx);
+    if (!ctx->capturing) throw Error(TAMM_EINVAL, "no graph capture is open");
+    if (ctx->group_active) throw Error(TAMM_EINVAL, "close the contraction group before ending the capture");
+    cudaGraph_t g = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(ctx->stream, &g);
+    ctx->capturing = false;
+    const int64_t n = ctx->launches - ctx->capture_launch0;
+    if (ctx->capture_failed || e != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      (void)cudaGetLastError();
+      ctx->capture_failed = false;
+      throw Error(e != cudaSuccess ? TAMM_ECUDA : TAMM_EINVAL, "graph capture failed%s%s",
+                  e != cudaSuccess ? ": " : " (an operation inside it failed)",
+                  e != cudaSuccess ? cudaGetErrorString(e) : "");
+    }
+    std::unique_ptr<tamm_graph> G(new tamm_graph());
+    G->ctx = ctx;
+    G->graph = g;
+    G->launches = n;
+    const cudaError_t ei = cudaGraphInstantiate(&G->exec, g, 0);
+    if (ei != cudaSuccess) {
+      cudaGraphDestroy(g);
+      G->graph = nullptr;
+      cuda_check(ei, "cudaGraphInstantiate");
+    }
+    *out = G.release();
+  });
+}
+
+extern "C" tamm_status tamm_graph_launch(tamm_graph* g) {
+  if (!g || !g->ctx) return TAMM_EINVAL;
+  tamm_ctx* ctx = g->ctx;
+  return guarded(ctx, [&] {
+    if (ctx->capturing || ctx->group_active) throw Error(TAMM_EINVAL, "graph launch inside a group or capture");
+    cuda_check(cudaGraphLaunch(g->exec, ctx->stream), "cudaGraphLaunch");
+    ctx->launches += g->launches;
+  });
+}
+
+extern "C" tamm_status tamm_graph_info(const tamm_graph* g, int64_t* kernel_launches) {
+  if (!g || !kernel_launches) return TAMM_EINVAL;
+  *kernel_launches = g->launches;
+  return TAMM_OK;
+}
+
+extern "C" void tamm_graph_destroy(tamm_graph* g) {
+  if (!g) return;
+  if (g->exec) cudaGraphExecDestroy(g->exec);
+  if (g->graph) cudaGraphDestroy(g->graph);
+  (void)cudaGetLastError();
+  delete g;
 }

@@ -73,9 +73,13 @@ struct ContractLayout {
   void enumerate();
 };
 
-// slices: integer digit slices (3..8); float_split: BF16x3 floating pieces (slices must be 3)
+// slices: integer digit slices (3..8); float_split: BF16x3 floating pieces (slices must be 3).
+// Inside a group the contraction is recorded; otherwise it runs at once.
 void run_contract_ozaki(tamm_ctx* ctx, double alpha, tamm_tensor* C, const char* lc, double beta,
                         const tamm_tensor* A, const char* la, const tamm_tensor* B, const char* lb, int slices,
                         bool float_split);
+// Run recorded split-precision contractions: all slicing, then their GEMMs as few launches as the
+// slice counts and the per-launch problem limit allow, then output permutations.
+void execute_ozaki(tamm_ctx* ctx, const std::vector<OzOpRecord>& ops);
 
 }  // namespace tamm

@@ -76,6 +76,18 @@ struct DevBuf {
 
 struct Plan;  // contraction / add / energy plans, cached per context
 
+// A split-precision contraction ready to run (recorded inside a group).
+struct OzOpRecord {
+  Plan* plan;  // the contraction's cached split-precision plan
+  int slices;
+  bool float_split;
+  double alpha, beta;
+  double* c;
+  const double* left;   // GEMM-left operand data
+  const double* right;  // GEMM-right operand data
+  size_t c_bytes, left_bytes, right_bytes;
+};
+
 }  // namespace tamm
 
 struct tamm_space {
@@ -132,6 +144,11 @@ struct tamm_ctx {
   };
   std::vector<TimedLaunch> timed;
   std::vector<cudaEvent_t> event_pool;
+  bool group_active = false;                  // between tamm_group_begin and tamm_group_end
+  std::vector<tamm::OzOpRecord> group_ops;    // recorded split-precision contractions
+  bool capturing = false;                     // between tamm_graph_begin and tamm_graph_end
+  bool capture_failed = false;                // an operation failed while capturing
+  int64_t capture_launch0 = 0;
 };
 
 namespace tamm {

@@ -105,3 +105,33 @@ class Runner:
             if r is not None:
                 out[s.name] = r
         return out
+
+    def run_grouped(self, steps, precision="ozaki_bf16", slices: int = 0) -> None:
+        """Independent contraction steps as one contraction group (one grouped GEMM launch), then the
+        output antisymmetrisers of those that have one."""
+        T, ctx = self.tensors, self.ctx
+        after = []
+        with ctx.group():
+            for step in steps:
+                if not isinstance(step, wl.ContractSpec):
+                    raise ValueError(f"{step.name}: only contractions can be grouped")
+                if step.antisym:
+                    X, lx = self.scratch_for(step)
+                    ctx.contract(step.alpha, X, lx, 0.0, T[step.a], step.la, T[step.b], step.lb, precision, slices)
+                    after.append((step, X, lx))
+                else:
+                    ctx.contract(step.alpha, T[step.c], step.lc, step.beta, T[step.a], step.la, T[step.b], step.lb,
+                                 precision, slices)
+        for step, X, lx in after:
+            ctx.add(T[step.c], step.lc, step.beta, X, antisym_terms(step.lc, lx))
+
+
+def build_batch(ctx: Context, sizes, seed: int, scale_tiles: tuple = (20, 40)) -> list:
+    """Independent ladder problems R = 1/2 V_vvvv T of the given (O, V) sizes, each with its own tensors
+    (seeded per problem index)."""
+    out = []
+    for k, (o, v) in enumerate(sizes):
+        w = wl.ladder_problem(o, v, seed + k, *scale_tiles)
+        sp, ts = build(ctx, w)
+        out.append((w, Runner(ctx, w, sp, ts)))
+    return out

@@ -190,3 +190,84 @@ def small_doubles(O: int = 8, V: int = 24, to: int = 2, tv: int = 4, seed_k: int
 
 
 CONFIGS = {1: config1, 2: config2, 4: config4, 5: config5}
+
+
+# ------------------------------------------------------------ D2h irreps
+
+def irrep_space(name: str, n_spin_orbitals: int, rng, tile_lo: int = 8, tile_hi: int = 96) -> SpaceSpec:
+    """Spin orbitals split half alpha / half beta; each spin's orbitals are assigned to the eight
+    D2h irreps (labelled 0..7 so that the product is XOR) by one seeded multinomial draw shared by
+    alpha and beta; every (spin, irrep) group is cut into tiles of sizes drawn from U{tile_lo..tile_hi}
+    (the last tile of a group takes what is left)."""
+    half = n_spin_orbitals // 2
+    counts = rng.multinomial(half, [1.0 / 8] * 8)
+    groups, tiles = [], []
+    for spin in (1, -1):
+        for irrep in range(8):
+            n = int(counts[irrep])
+            if n == 0:
+                continue
+            groups.append((n, spin, irrep))
+            left = n
+            while left > 0:
+                t = min(int(rng.integers(tile_lo, tile_hi + 1)), left)
+                tiles.append(t)
+                left -= t
+    return SpaceSpec(name, tuple(groups), tile=0, tile_sizes=tuple(tiles))
+
+
+def config3(seed_k: int = 3) -> Workload:
+    """Uneven D2h blocks: O=64, V=384 spin-orbitals, irrep counts and tile cuts seeded; the vvvv
+    ladder and the ring term (spin and irrep block sparsity)."""
+    import numpy as np
+
+    seed = SEED_BASE + seed_k
+    rng = np.random.default_rng(seed)
+    occ = irrep_space("occ", 64, rng)
+    virt = irrep_space("virt", 384, rng)
+    w = Workload("irrep_doubles_O64_V384", seed, {"occ": occ, "virt": virt}, {})
+    si = "spin_irrep"
+    w.tensors = {
+        "V_vvvv": TensorSpec("V_vvvv", ("virt",) * 4, 2, si, sigma=0.1, stream=1, anti01=True, anti23=True),
+        "T": TensorSpec("T", ("virt", "virt", "occ", "occ"), 2, si, sigma=0.01, stream=2, anti01=True, anti23=True),
+        "V_ovvo": TensorSpec("V_ovvo", ("occ", "virt", "virt", "occ"), 2, si, sigma=0.1, stream=5),
+        "R": TensorSpec("R", ("virt", "virt", "occ", "occ"), 2, si),
+        "R2": TensorSpec("R2", ("virt", "virt", "occ", "occ"), 2, si),
+    }
+    w.steps = [
+        ContractSpec("ladder", "R", "abij", "V_vvvv", "abef", "T", "efij", 0.5, beta=0.0),
+        ContractSpec("ring", "R2", "abij", "T", "aeim", "V_ovvo", "mbej", 1.0, beta=0.0, antisym=True),
+    ]
+    return w
+
+
+def config3_batch_sizes(n: int = 32, seed_k: int = 3, o_range=(16, 64), v_range=(64, 320)) -> list:
+    """(O, V) of the independent ladder problems: even spin-orbital counts drawn uniformly."""
+    import numpy as np
+
+    rng = np.random.default_rng(SEED_BASE + 100 + seed_k)
+    out = []
+    for _ in range(n):
+        o = 2 * int(rng.integers(o_range[0] // 2, o_range[1] // 2 + 1))
+        v = 2 * int(rng.integers(v_range[0] // 2, v_range[1] // 2 + 1))
+        out.append((o, v))
+    return out
+
+
+def ladder_problem(O: int, V: int, seed: int, to: int = 20, tv: int = 40) -> Workload:
+    """One ladder R = 1/2 V_vvvv T of the batch (spin block sparsity)."""
+    w = Workload(f"ladder_O{O}_V{V}", seed, {"occ": spin_space("occ", O, to), "virt": spin_space("virt", V, tv)}, {})
+    w.tensors = {
+        "V_vvvv": TensorSpec("V_vvvv", ("virt",) * 4, 2, sigma=0.1, stream=1, anti01=True, anti23=True),
+        "T": TensorSpec("T", ("virt", "virt", "occ", "occ"), 2, sigma=0.01, stream=2, anti01=True, anti23=True),
+        "R": TensorSpec("R", ("virt", "virt", "occ", "occ"), 2),
+    }
+    w.steps = [ContractSpec("ladder", "R", "abij", "V_vvvv", "abef", "T", "efij", 0.5, beta=0.0)]
+    return w
+
+
+def batch_memory_bytes(O: int, V: int, slices: int = 6) -> int:
+    """Device bytes of one batch ladder: FP64 V_vvvv, T, R and the slice images of V_vvvv and T."""
+    vvvv = 3 * V ** 4 // 8
+    t = 3 * V ** 2 * O ** 2 // 8
+    return 8 * (vvvv + 2 * t) + 2 * slices * (vvvv + t)

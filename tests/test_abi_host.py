@@ -143,3 +143,15 @@ def test_permuted_tensor_stores_images_of_blocks(hctx):
     assert {tuple(t) for t in X.block_tiles} == imgs
     with pytest.raises(tg.TammError):
         hctx.tensor_permuted(R, [0, 0, 1, 3])
+
+
+def test_group_and_graph_calls_need_a_device(hctx):
+    assert hctx.lib.tamm_group_begin(hctx.handle) == tg.TAMM_ECUDA
+    assert hctx.lib.tamm_graph_begin(hctx.handle) == tg.TAMM_ECUDA
+    assert hctx.lib.tamm_group_cancel(hctx.handle) == tg.TAMM_EINVAL  # no group is open
+    import ctypes as ct
+
+    g = ct.c_void_p()
+    assert hctx.lib.tamm_graph_end(hctx.handle, ct.byref(g)) == tg.TAMM_ECUDA and not g.value
+    assert hctx.lib.tamm_graph_launch(None) == tg.TAMM_EINVAL
+    hctx.lib.tamm_graph_destroy(None)
