@@ -201,7 +201,8 @@ TAMM_API void tamm_tensor_destroy(tamm_tensor* t);
  * permutation where the block layout needs it, a dense block GEMM and an
  * accumulation into the output block.  `precision` is a TAMM_PREC_*; for
  * TAMM_PREC_OZAKI_BF16, `slices` is the number of BF16 slices per operand
- * (3..8; 0 = automatic, 6).  C must not alias A or B.
+ * (3..8; 0 = the autotuned choice for these tensors and labels if
+ * tamm_autotune ran on them, else 6 with the context's chunk length).  C must not alias A or B.
  * Errors: TAMM_EINVAL (labels/spaces/beta), TAMM_EUNSUPPORTED (precision),
  * TAMM_ENOMEM, TAMM_ECUDA. */
 TAMM_API tamm_status tamm_contract(tamm_ctx* ctx, double alpha, tamm_tensor* C, const char* lc, double beta,
@@ -257,6 +258,24 @@ TAMM_API tamm_status tamm_norm_async(tamm_ctx* ctx, const tamm_tensor* t, double
  * Errors: TAMM_EINVAL (n < 0 or a null pointer), TAMM_ELIMIT (n above the
  * limit), TAMM_ECUDA (no usable current device or a failed launch). */
 TAMM_API tamm_status tamm_norm_noalloc(const double* x_device, int64_t n, double* result_device, void* stream);
+
+/* Autotuner of the split-precision path (TAMM_PREC_OZAKI_BF16) for one
+ * contraction, the same tensors and labels as tamm_contract.  It runs the FP64
+ * contraction once as the reference, then for each exact-chunk length (1280,
+ * 640, 320 summed indices) the smallest slice count (3..8) whose normwise
+ * relative error against that reference is at most target_rel_err / 2 on the
+ * given operands, times each such candidate (CUDA events, mean of three runs
+ * after one untimed run) and keeps the fastest.  C's data is not touched: the
+ * trial outputs go to two temporary buffers of C's size from the context
+ * allocator.  The choice is remembered in the context and used by every later
+ * tamm_contract of the same tensors and labels with precision
+ * TAMM_PREC_OZAKI_BF16 and slices = 0.  Outputs (each may be NULL): the slice
+ * count, the chunk length, the measured error and the mean time in ms of the
+ * chosen configuration.  Synchronises.  Errors: TAMM_EINVAL, TAMM_ENOMEM,
+ * TAMM_ECUDA, TAMM_EUNSUPPORTED (no candidate reaches the target). */
+TAMM_API tamm_status tamm_autotune(tamm_ctx* ctx, const tamm_tensor* C, const char* lc, const tamm_tensor* A,
+                                   const char* la, const tamm_tensor* B, const char* lb, double target_rel_err,
+                                   int* slices, int* chunk_k, double* rel_err, double* ms);
 
 /* ------------------------------------------------------ grouped execution */
 

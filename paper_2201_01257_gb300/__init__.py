@@ -75,6 +75,7 @@ PROTOTYPES = [
     ("tamm_norm", _i, [_vp, _vp, _dp]),
     ("tamm_norm_async", _i, [_vp, _vp, _vp]),
     ("tamm_norm_noalloc", _i, [_vp, _i64, _vp, _vp]),
+    ("tamm_autotune", _i, [_vp, _vp, _cp, _vp, _cp, _vp, _cp, _d, _ip, _ip, _dp, _dp]),
     ("tamm_group_begin", _i, [_vp]),
     ("tamm_group_end", _i, [_vp]),
     ("tamm_group_cancel", _i, [_vp]),
@@ -258,6 +259,15 @@ class Context:
         ms, cnt = (ctypes.c_double * n)(), (ctypes.c_int64 * n)()
         self.check(self.lib.tamm_ctx_profile_read(self.handle, ms, cnt), "tamm_ctx_profile_read")
         return {k: (ms[i], cnt[i]) for i, k in enumerate(KERNEL_CLASSES)}
+
+    def autotune(self, C, lc, A, la, B, lb, target: float = 1e-10) -> dict:
+        """Pick slices and chunk length for this split-precision contraction (used when slices = 0)."""
+        s, ck = ctypes.c_int(), ctypes.c_int()
+        err, ms = ctypes.c_double(), ctypes.c_double()
+        self.check(self.lib.tamm_autotune(self.handle, C.handle, lc.encode(), A.handle, la.encode(), B.handle,
+                                          lb.encode(), float(target), ctypes.byref(s), ctypes.byref(ck),
+                                          ctypes.byref(err), ctypes.byref(ms)), "tamm_autotune")
+        return {"slices": s.value, "chunk_k": ck.value, "rel_err": err.value, "ms": ms.value}
 
     # grouped execution ---------------------------------------------------
     def group_begin(self) -> None:

@@ -93,6 +93,20 @@ __global__ void __launch_bounds__(256) sumsq_partials_kernel(const double* __res
   if (threadIdx.x == 0) partials[blockIdx.x] = s;
 }
 
+__global__ void __launch_bounds__(256) diff_sumsq_partials_kernel(const double* __restrict__ x,
+                                                                  const double* __restrict__ y, int64_t n,
+                                                                  int64_t per, double* __restrict__ partials) {
+  const int64_t lo = (int64_t)blockIdx.x * per;
+  const int64_t hi = min(n, lo + per);
+  double acc = 0.0;
+  for (int64_t e = lo + threadIdx.x; e < hi; e += blockDim.x) {
+    const double d = x[e] - y[e];
+    acc = fma(d, d, acc);
+  }
+  double s = block_sum<256>(acc);
+  if (threadIdx.x == 0) partials[blockIdx.x] = s;
+}
+
 __global__ void __launch_bounds__(1024) reduce_final_kernel(const double* __restrict__ p, int64_t n, double alpha,
                                                             int take_sqrt, double* __restrict__ out) {
   double acc = 0.0;
@@ -211,6 +225,16 @@ cudaError_t launch_sumsq_partials(tamm_ctx* ctx, const double* x, int64_t n, dou
   const int64_t per = (n + n_parts - 1) / n_parts;
   kernel_begin(ctx, TAMM_KERNEL_REDUCE);
   sumsq_partials_kernel<<<(unsigned)n_parts, 256, 0, ctx->stream>>>(x, n, per, partials);
+  kernel_end(ctx, TAMM_KERNEL_REDUCE);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_diff_sumsq_partials(tamm_ctx* ctx, const double* x, const double* y, int64_t n,
+                                       double* partials, int64_t n_parts) {
+  if (n_parts == 0) return cudaSuccess;
+  const int64_t per = (n + n_parts - 1) / n_parts;
+  kernel_begin(ctx, TAMM_KERNEL_REDUCE);
+  diff_sumsq_partials_kernel<<<(unsigned)n_parts, 256, 0, ctx->stream>>>(x, y, n, per, partials);
   kernel_end(ctx, TAMM_KERNEL_REDUCE);
   return cudaGetLastError();
 }

@@ -932,7 +932,17 @@ struct OzakiPlan : Plan {
 void run_contract_ozaki(tamm_ctx* ctx, double alpha, tamm_tensor* C, const char* lc, double beta,
                         const tamm_tensor* A, const char* la, const tamm_tensor* B, const char* lb, int slices,
                         bool float_split) {
-  if (slices == 0) slices = kOzDefaultSlices;
+  int chunk_k = ctx->oz_chunk_k;
+  if (slices == 0) {
+    slices = kOzDefaultSlices;
+    if (!float_split) {
+      auto t = ctx->tuned.find(tune_key(C, lc, A, la, B, lb));
+      if (t != ctx->tuned.end()) {
+        slices = t->second.slices;
+        chunk_k = t->second.chunk_k;
+      }
+    }
+  }
   if (slices < kOzMinSlices || slices > kOzMaxSlices)
     throw Error(TAMM_EINVAL, "ozaki: slices must be %d..%d (0 = %d)", kOzMinSlices, kOzMaxSlices, kOzDefaultSlices);
   const std::string key = "oz" + std::to_string(slices) + "|" + std::to_string(C->id) + "|" + lc + "|" +
@@ -960,6 +970,7 @@ void run_contract_ozaki(tamm_ctx* ctx, double alpha, tamm_tensor* C, const char*
   op.c_bytes = (size_t)C->n_elems * 8;
   op.left_bytes = (size_t)L->n_elems * 8;
   op.right_bytes = (size_t)R->n_elems * 8;
+  op.chunk_k = chunk_k;
   if (ctx->group_active) {
     ctx->group_ops.push_back(op);
     return;
@@ -1005,20 +1016,20 @@ void execute_ozaki(tamm_ctx* ctx, const std::vector<OzOpRecord>& ops) {
     pr.beta = p->perm_out ? 0.0 : ops[i].beta;
     counts[i] = p->n_items;
   }
-  // one GEMM launch per slice count, at most kOzMaxProblems problems each
+  // one GEMM launch per (slice count, chunk length), at most kOzMaxProblems problems each
   std::vector<bool> done(ops.size(), false);
   for (size_t i = 0; i < ops.size(); ++i) {
     if (done[i]) continue;
     std::vector<OzProblem> batch;
     std::vector<int64_t> n;
     for (size_t j = i; j < ops.size() && (int)batch.size() < kOzMaxProblems; ++j) {
-      if (done[j] || ops[j].slices != ops[i].slices) continue;
+      if (done[j] || ops[j].slices != ops[i].slices || ops[j].chunk_k != ops[i].chunk_k) continue;
       batch.push_back(probs[j]);
       n.push_back(counts[j]);
       done[j] = true;
     }
     cuda_check(launch_ozaki_gemm(ctx, batch.data(), n.data(), (int)batch.size(), ops[i].slices,
-                                 ctx->oz_chunk_k / kOzTileK),
+                                 ops[i].chunk_k / kOzTileK),
                "ozaki gemm");
   }
   const double one = 1.0;

@@ -86,6 +86,13 @@ struct OzOpRecord {
   const double* left;   // GEMM-left operand data
   const double* right;  // GEMM-right operand data
   size_t c_bytes, left_bytes, right_bytes;
+  int chunk_k;  // summed indices per exact FP32 chunk
+};
+
+// Split-precision configuration picked by the autotuner for one contraction.
+struct TunedConfig {
+  int slices;
+  int chunk_k;
 };
 
 }  // namespace tamm
@@ -146,6 +153,7 @@ struct tamm_ctx {
   std::vector<cudaEvent_t> event_pool;
   bool group_active = false;                  // between tamm_group_begin and tamm_group_end
   std::vector<tamm::OzOpRecord> group_ops;    // recorded split-precision contractions
+  std::map<std::string, tamm::TunedConfig> tuned;  // autotuned contractions (used when slices = 0)
   bool capturing = false;                     // between tamm_graph_begin and tamm_graph_end
   bool capture_failed = false;                // an operation failed while capturing
   int64_t capture_launch0 = 0;
@@ -169,6 +177,9 @@ cudaError_t launch_add(tamm_ctx* ctx, double* dst, const double* src, const AddB
 cudaError_t launch_energy_partials(tamm_ctx* ctx, const double* a, const double* b, const AddBlock* blocks,
                                    const ChunkItem* items, int64_t n_items, double* partials);
 cudaError_t launch_sumsq_partials(tamm_ctx* ctx, const double* x, int64_t n, double* partials, int64_t n_parts);
+// partial sums of (x - y)^2
+cudaError_t launch_diff_sumsq_partials(tamm_ctx* ctx, const double* x, const double* y, int64_t n,
+                                       double* partials, int64_t n_parts);
 cudaError_t launch_reduce_final(tamm_ctx* ctx, const double* partials, int64_t n, double alpha, int take_sqrt,
                                 double* out_device);
 cudaError_t launch_gemm_f64(tamm_ctx* ctx, const double* a, const double* b, double* c, const GemmGroup* groups,

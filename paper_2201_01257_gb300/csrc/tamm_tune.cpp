@@ -1,0 +1,144 @@
+// Autotuner of the split-precision contraction: picks the number of BF16
+// slices per operand and the length of the exact FP32 accumulation chunk for
+// one contraction, given a normwise relative error target.
+//
+// Both knobs trade accuracy for speed.  Fewer slices mean fewer slice
+// products (S(S+1)/2 of them) but a coarser representation of the operands
+// (about 7 bits per slice); a longer chunk means fewer FP32-to-double folds
+// but a larger rounding error in the inexact tail products, which grows with
+// the chunk length.  The tuner measures, on the caller's own operands:
+//   * the FP64 contraction (the reference), once;
+//   * for each chunk length, the split-precision contraction with 3, 4, ...
+//     slices until its error against the reference is at most
+//     kSafety * target (the first passing count is the fastest one for that
+//     chunk, since time grows with the slice count);
+//   * the run time of every passing candidate (CUDA events, after one
+//     untimed run);
+// and keeps the fastest.  The result is remembered per (tensors, labels) and
+// used by tamm_contract whenever slices = 0.
+#include <algorithm>
+#include <cmath>
+
+#include "ozaki.h"
+#include "tamm_plan.h"
+
+namespace tamm {
+
+std::string tune_key(const tamm_tensor* C, const char* lc, const tamm_tensor* A, const char* la,
+                     const tamm_tensor* B, const char* lb) {
+  return "tune|" + std::to_string(C->id) + "|" + lc + "|" + std::to_string(A->id) + "|" + la + "|" +
+         std::to_string(B->id) + "|" + lb;
+}
+
+}  // namespace tamm
+
+using namespace tamm;
+
+namespace {
+
+constexpr double kSafety = 0.5;  // margin for other data of the same contraction
+constexpr int kChunks[] = {1280, 640, 320};
+constexpr int kTimedRuns = 3;
+
+// A view of C's block structure on another buffer (same id: the same cached plans).
+struct Shadow {
+  tamm_tensor t;
+  Shadow(const tamm_tensor& C, double* data) : t(C) {
+    t.data = data;
+    t.owned = false;
+    t.owned_bytes = 0;
+  }
+};
+
+double host_scalar(tamm_ctx* ctx, const double* dev) {
+  cuda_check(cudaMemcpyAsync(ctx->h_result, dev, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream), "D2H");
+  sync_and_check(ctx);
+  return ctx->h_result[0];
+}
+
+double diff_norm(tamm_ctx* ctx, const double* x, const double* y, int64_t n) {
+  const int64_t parts = std::max<int64_t>(1, std::min<int64_t>((n + 8191) / 8192, 4L * ctx->sm_count * 8));
+  double* partials = ctx_reduce_buffer(ctx, (size_t)parts);
+  double* out = result_slot(ctx, 2);
+  if (n == 0) cuda_check(cudaMemsetAsync(partials, 0, sizeof(double), ctx->stream), "memset");
+  else cuda_check(launch_diff_sumsq_partials(ctx, x, y, n, partials, parts), "diff kernel");
+  cuda_check(launch_reduce_final(ctx, partials, parts, 1.0, 1, out), "reduce kernel");
+  return host_scalar(ctx, out);
+}
+
+}  // namespace
+
+extern "C" tamm_status tamm_autotune(tamm_ctx* ctx, const tamm_tensor* C, const char* lc, const tamm_tensor* A,
+                                     const char* la, const tamm_tensor* B, const char* lb, double target_rel_err,
+                                     int* slices, int* chunk_k, double* rel_err, double* ms) {
+  if (!ctx) return TAMM_EINVAL;
+  void* ref = nullptr;
+  void* trial = nullptr;
+  size_t bytes = 0;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  const int saved_chunk = ctx->oz_chunk_k;
+  tamm_status st = TAMM_OK;
+  try {
+    if (ctx->host_only) throw Error(TAMM_ECUDA, "host-only context (device -1) cannot run device work");
+    if (!C || !A || !B || !lc || !la || !lb) throw Error(TAMM_EINVAL, "autotune: null argument");
+    if (!(target_rel_err > 0.0)) throw Error(TAMM_EINVAL, "autotune: target error must be positive");
+    if (ctx->group_active || ctx->capturing) throw Error(TAMM_EINVAL, "autotune inside a group or capture");
+    if (!A->data || !B->data) throw Error(TAMM_EINVAL, "autotune: operand without data");
+    bytes = (size_t)std::max<int64_t>(C->n_elems, 1) * sizeof(double);
+    ref = ctx_alloc(ctx, bytes);
+    trial = ctx_alloc(ctx, bytes);
+    Shadow R(*C, (double*)ref), X(*C, (double*)trial);
+    run_contract(ctx, 1.0, &R.t, lc, 0.0, A, la, B, lb, TAMM_PREC_F64, 0);
+    run_norm(ctx, &R.t, result_slot(ctx, 3));
+    const double ref_norm = host_scalar(ctx, result_slot(ctx, 3));
+    const double denom = ref_norm > 0.0 ? ref_norm : 1.0;
+    cuda_check(cudaEventCreate(&e0), "cudaEventCreate");
+    cuda_check(cudaEventCreate(&e1), "cudaEventCreate");
+    int best_s = 0, best_chunk = 0;
+    double best_ms = 0.0, best_err = 0.0;
+    for (int chunk : kChunks) {
+      ctx->oz_chunk_k = chunk;
+      for (int s = kOzMinSlices; s <= kOzMaxSlices; ++s) {
+        run_contract(ctx, 1.0, &X.t, lc, 0.0, A, la, B, lb, TAMM_PREC_OZAKI_BF16, s);
+        const double err = diff_norm(ctx, (const double*)trial, (const double*)ref, C->n_elems) / denom;
+        if (!(err <= kSafety * target_rel_err)) continue;
+        cuda_check(cudaEventRecord(e0, ctx->stream), "cudaEventRecord");
+        for (int r = 0; r < kTimedRuns; ++r)
+          run_contract(ctx, 1.0, &X.t, lc, 0.0, A, la, B, lb, TAMM_PREC_OZAKI_BF16, s);
+        cuda_check(cudaEventRecord(e1, ctx->stream), "cudaEventRecord");
+        sync_and_check(ctx);
+        float f = 0.0f;
+        cuda_check(cudaEventElapsedTime(&f, e0, e1), "cudaEventElapsedTime");
+        const double t = f / kTimedRuns;
+        if (best_s == 0 || t < best_ms) {
+          best_s = s;
+          best_chunk = chunk;
+          best_ms = t;
+          best_err = err;
+        }
+        break;  // more slices only cost more time at this chunk length
+      }
+    }
+    if (best_s == 0)
+      throw Error(TAMM_EUNSUPPORTED, "autotune: no slice count (<= %d) reaches %.3g on these operands", kOzMaxSlices,
+                  target_rel_err);
+    ctx->tuned[tune_key(C, lc, A, la, B, lb)] = {best_s, best_chunk};
+    if (slices) *slices = best_s;
+    if (chunk_k) *chunk_k = best_chunk;
+    if (rel_err) *rel_err = best_err;
+    if (ms) *ms = best_ms;
+    ctx->last_error.clear();
+  } catch (const Error& e) {
+    ctx->last_error = e.msg;
+    st = e.status;
+  } catch (const std::exception& e) {
+    ctx->last_error = e.what();
+    st = TAMM_EINVAL;
+  }
+  ctx->oz_chunk_k = saved_chunk;
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (ref) ctx_free(ctx, ref, bytes);
+  if (trial) ctx_free(ctx, trial, bytes);
+  return st;
+}
