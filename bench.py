@@ -111,6 +111,24 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+# ------------------------------------------------------------ multi-rank
+
+def max_over_ranks(x: float, dist, device: str) -> float:
+    """The largest of every rank's value (the job's time is its slowest rank's); identity without dist."""
+    if dist is None:
+        return x
+    import torch
+
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world: int, flops_per_rank_step: float, ms_per_step: float) -> float:
+    """Whole-job TFLOP/s: every rank runs its own full step (weak scaling), timed by the slowest rank."""
+    return world * flops_per_rank_step / (ms_per_step * 1e-3) / 1e12
+
+
 # ------------------------------------------------------------------ ours
 
 def run_ours(args, rank: int, world: int) -> dict | None:
@@ -220,15 +238,7 @@ def run_ours(args, rank: int, world: int) -> dict | None:
     barrier()
     ms_e2e = ev4.elapsed_time(ev5) / e2e_k
 
-    # max over ranks
-    def max_all(x):
-        if dist is None:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device=f"cuda:{dev}")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
-
-    ms, ms_e2e, ms_f64 = max_all(ms), max_all(ms_e2e), max_all(ms_f64)
+    ms, ms_e2e, ms_f64 = (max_over_ranks(x, dist, f"cuda:{dev}") for x in (ms, ms_e2e, ms_f64))
     if dist is not None:
         dist.destroy_process_group()
     if rank != 0:
@@ -241,7 +251,7 @@ def run_ours(args, rank: int, world: int) -> dict | None:
     achieved = tensor_flops_per_step * args.steps / (gemm_ms * 1e-3) / 1e12 if gemm_ms else None
     peak = peaks.get("bf16_tflops_sustained", 1700.0)
     traffic = MEASURED_TRAFFIC.get(kernel_source_hash())
-    value = world * flops / (ms * 1e-3) / 1e12
+    value = job_throughput(world, flops, ms)
     return {
         "metric": METRIC,
         "value": round(value, 3),
@@ -264,11 +274,11 @@ def run_ours(args, rank: int, world: int) -> dict | None:
             "l2": "inputs larger than L2 (V_vvvv 9.95 GB per step)",
             "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
         },
-        "f64": {"value": round(world * flops / (ms_f64 * 1e-3) / 1e12, 4), "unit": UNIT,
+        "f64": {"value": round(job_throughput(world, flops, ms_f64), 4), "unit": UNIT,
                 "ms_per_step": round(ms_f64, 2), "steps": f64_steps},
         "speedup_vs_f64": round(ms_f64 / ms, 2),
         "rel_err_vs_f64": {"R": rel(r_oz, r_64), "W": rel(w_oz, w_64), "energy": abs(e_oz - e_64) / abs(e_64)},
-        "e2e": {"value": round(world * flops / (ms_e2e * 1e-3) / 1e12, 3), "unit": UNIT,
+        "e2e": {"value": round(job_throughput(world, flops, ms_e2e), 3), "unit": UNIT,
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": round(ms_e2e, 3),
                 "steps": e2e_k},
         "gpu_launches": launches,
