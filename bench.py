@@ -169,12 +169,23 @@ def run_ours(args, rank: int, world: int) -> dict | None:
     ctx.sync()
     run = gw.Runner(ctx, w, spaces, T)
     flops = sum(run.flops(s) for s in w.steps)
-    n_products = SLICES * (SLICES + 1) // 2
+
     energy_dev = torch.zeros(1, dtype=torch.float64, device=f"cuda:{dev}")
     stream = torch.cuda.current_stream()
 
+    # split-precision configuration per contraction: autotuned (slices, chunk, tile policy) for
+    # rel err <= 1e-10 with a factor-2 margin, or a fixed slice count
+    tuned = None
+    if args.slices == 0:
+        # one FP64 step first, so that intermediates (W) hold the values the step's contractions see
+        run.run("f64", 0, energy_out=energy_dev.data_ptr())
+        t0 = time.time()
+        tuned = run.autotune(1e-10)
+        tune_s = time.time() - t0
+    oz_slices = args.slices
+
     def step(prec):
-        run.run("ozaki_bf16" if prec == "oz" else "f64", SLICES if prec == "oz" else 0,
+        run.run("ozaki_bf16" if prec == "oz" else "f64", oz_slices if prec == "oz" else 0,
                 energy_out=energy_dev.data_ptr())
 
     # --- device-resident timed region (split precision) ---
@@ -247,7 +258,12 @@ def run_ours(args, rank: int, world: int) -> dict | None:
     peaks = measured_peaks()
     gemm_ms, gemm_n = prof["gemm_ozaki"]
     dominant = max(prof, key=lambda k: prof[k][0])
-    tensor_flops_per_step = flops * n_products  # BF16 slice products issued per step (algorithmic)
+    # BF16 slice products per step (algorithmic): S(S+1)/2 products of every nonzero block pair
+    def n_products(s):
+        return s * (s + 1) // 2
+
+    tensor_flops_per_step = sum(run.flops(st) * n_products(tuned[st.name]["slices"] if tuned else oz_slices)
+                                for st in w.steps if isinstance(st, wl.ContractSpec))
     achieved = tensor_flops_per_step * args.steps / (gemm_ms * 1e-3) / 1e12 if gemm_ms else None
     peak = peaks.get("bf16_tflops_sustained", 1700.0)
     traffic = MEASURED_TRAFFIC.get(kernel_source_hash())
@@ -263,13 +279,19 @@ def run_ours(args, rank: int, world: int) -> dict | None:
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "bf16 slices (6 per f64 operand, f32 accumulate, f64 reconstruct)",
+        "dtype": "bf16 slices (f32 accumulate, f64 reconstruct)",
         "data": "synthetic (seeded Philox normals, antisymmetrised; V~N(0,0.1), T~N(0,0.01))",
         "config": {
             "workload": "ccsd_doubles_O40_V240: vvvv ladder + W copy + intermediate + oooo ladder + ring with "
                         "P(ab)P(ij) + T1 term + energy",
             "O": 40, "V": 240, "tiles": [20, 40], "symmetry": "spin",
-            "precision": "ozaki_bf16", "slices": SLICES,
+            "precision": "ozaki_bf16",
+            "slices": ({k: v["slices"] for k, v in tuned.items()} if tuned else oz_slices),
+            "autotuned": ({k: {"slices": v["slices"], "chunk_k": v["chunk_k"], "tile_policy": v["tile_policy"],
+                               "persistent": v["persistent"], "rel_err_vs_f64_gpu": v["rel_err"],
+                               "ms": round(v["ms"], 3)}
+                           for k, v in tuned.items()} if tuned else None),
+            "autotune_seconds": round(tune_s, 2) if tuned else None,
             "nonzero_block_flops_per_step": flops,
             "l2": "inputs larger than L2 (V_vvvv 9.95 GB per step)",
             "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
@@ -465,6 +487,61 @@ def run_ladder_case(args) -> dict:
             "TFLOP/s": round(fl / ms / 1e9, 3), "nonzero_block_flops": fl}
 
 
+def run_config3_case(args) -> dict:
+    """Uneven D2h blocks (O=64, V=384): the ladder and the ring as one contraction group, eager and as a
+    CUDA graph, against the same contractions launched one by one and the FP64 path."""
+    import torch
+
+    import paper_2201_01257_gb300 as tg
+    from paper_2201_01257_gb300 import workload as gw
+    from tamm_synth import workloads as wl
+
+    w = wl.config3()
+    stream = torch.cuda.Stream(0)
+    ctx = tg.Context(0, stream=stream)
+    with torch.cuda.stream(stream):
+        sp, T = gw.build(ctx, w)
+    run = gw.Runner(ctx, w, sp, T)
+    flops = sum(run.flops(s) for s in w.steps)
+
+    def timed(fn, k):
+        for _ in range(args.warmup):
+            fn()
+        ctx.sync()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(k):
+            fn()
+        b.record(stream)
+        ctx.sync()
+        return a.elapsed_time(b) / k
+
+    out = {"case": "irrep_doubles_O64_V384: vvvv ladder + ring with P(ab)P(ij), D2h irreps, tiles U{8..96}",
+           "nonzero_block_flops": flops, "blocks": {k: T[k].n_blocks for k in ("V_vvvv", "T", "R")}}
+    with torch.cuda.stream(stream):
+        for policy in (0, 1, 2):
+            ctx.set_option(tg.TAMM_OPT_OZAKI_TILE_POLICY, policy)
+            ms_g = timed(lambda: run.run_grouped(w.steps, "ozaki_bf16", SLICES), args.steps)
+            ms_s = timed(lambda: run.run("ozaki_bf16", SLICES), args.steps)
+            run.run_grouped(w.steps, "ozaki_bf16", SLICES)
+            ctx.sync()
+            ctx.graph_begin()
+            try:
+                run.run_grouped(w.steps, "ozaki_bf16", SLICES)
+            finally:
+                g = ctx.graph_end()
+            ms_graph = timed(g.launch, args.steps)
+            out[f"tile_policy_{policy}"] = {
+                "grouped_ms": round(ms_g, 3), "separate_ms": round(ms_s, 3), "graph_ms": round(ms_graph, 3),
+                "graph_kernels": g.kernel_launches, "TFLOP/s_graph": round(flops / ms_graph / 1e9, 3)}
+            g.destroy()
+        ctx.set_option(tg.TAMM_OPT_OZAKI_TILE_POLICY, 1)
+        ms64 = timed(lambda: run.run("f64", 0), max(1, min(args.steps, 2)))
+    out["f64_ms"] = round(ms64, 3)
+    out["f64_TFLOP/s"] = round(flops / ms64 / 1e9, 4)
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -474,11 +551,16 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="size of the CPU-baseline sample")
     ap.add_argument("--ref-seconds", type=float, default=6.0, help="CPU work per reference-arm step")
     ap.add_argument("--ladder", default="", help="O,V: time one split-precision ladder of that size instead")
+    ap.add_argument("--slices", type=int, default=0,
+                    help="split-precision slices per operand; 0 = autotune every contraction for 1e-10")
+    ap.add_argument("--config3", action="store_true", help="time the uneven-irrep grouped ladder + ring instead")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     if args.ladder:
         out = run_ladder_case(args)
+    elif args.config3:
+        out = run_config3_case(args)
     elif args.impl == "reference":
         out = run_reference(args, rank)
     else:

@@ -106,6 +106,10 @@ TAMM_API const char* tamm_last_error(const tamm_ctx* ctx);
                                     accumulators more often and shrink the rounding of the tail group */
 #define TAMM_OPT_OZAKI_PERSISTENT 1 /* split precision: 1 = one CTA per SM walks the work items, 0 = one CTA
                                        per work item (default) */
+#define TAMM_OPT_OZAKI_TILE_POLICY 2 /* split precision: output columns per work item (= rows per sliced B
+                                        tile) for an output block of N columns.  0 = 128; 1 (default) = 128,
+                                        or N rounded up to 16 when N < 128; 2 = the fewest tiles of at most
+                                        128 columns, of equal width rounded up to 16 (N = 400 -> 4 x 112) */
 /* Set option `option` to `value`.  Errors: TAMM_EINVAL (unknown option or value out of range). */
 TAMM_API tamm_status tamm_ctx_set_option(tamm_ctx* ctx, int option, int64_t value);
 
@@ -264,18 +268,23 @@ TAMM_API tamm_status tamm_norm_noalloc(const double* x_device, int64_t n, double
  * contraction once as the reference, then for each exact-chunk length (1280,
  * 640, 320 summed indices) the smallest slice count (3..8) whose normwise
  * relative error against that reference is at most target_rel_err / 2 on the
- * given operands, times each such candidate (CUDA events, mean of three runs
- * after one untimed run) and keeps the fastest.  C's data is not touched: the
+ * given operands, times each such candidate under every tile policy
+ * (TAMM_OPT_OZAKI_TILE_POLICY) and grid kind (TAMM_OPT_OZAKI_PERSISTENT;
+ * CUDA events, mean of three runs after one untimed run) and keeps the
+ * fastest.  C's data is not touched: the
  * trial outputs go to two temporary buffers of C's size from the context
- * allocator.  The choice is remembered in the context and used by every later
- * tamm_contract of the same tensors and labels with precision
- * TAMM_PREC_OZAKI_BF16 and slices = 0.  Outputs (each may be NULL): the slice
- * count, the chunk length, the measured error and the mean time in ms of the
- * chosen configuration.  Synchronises.  Errors: TAMM_EINVAL, TAMM_ENOMEM,
+ * allocator.  The choice (slices, chunk, tile policy, grid) is remembered in the
+ * context and used by every later tamm_contract of the same tensors and
+ * labels with precision TAMM_PREC_OZAKI_BF16 and slices = 0.  Outputs (each
+ * may be NULL): the slice count, the chunk length, the tile policy, the grid
+ * kind (1 = persistent), the measured error and the mean time in ms of the
+ * chosen configuration.  Tune
+ * on representative operands: a zero product is refused (TAMM_EINVAL).  Synchronises.  Errors: TAMM_EINVAL, TAMM_ENOMEM,
  * TAMM_ECUDA, TAMM_EUNSUPPORTED (no candidate reaches the target). */
 TAMM_API tamm_status tamm_autotune(tamm_ctx* ctx, const tamm_tensor* C, const char* lc, const tamm_tensor* A,
                                    const char* la, const tamm_tensor* B, const char* lb, double target_rel_err,
-                                   int* slices, int* chunk_k, double* rel_err, double* ms);
+                                   int* slices, int* chunk_k, int* tile_policy, int* persistent, double* rel_err,
+                                   double* ms);
 
 /* ------------------------------------------------------ grouped execution */
 

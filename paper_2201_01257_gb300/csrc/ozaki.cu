@@ -14,67 +14,63 @@ namespace tamm {
 // ======================================================================
 namespace {
 
-// bf16 bits of d (|d| <= 64), exact; the slice-k value d * 2^(-7k) subtracts 7k from the exponent.
-__host__ __device__ constexpr uint32_t bf16_of_small_int(int d) {
-  if (d == 0) return 0u;
-  const uint32_t s = d < 0 ? 0x8000u : 0u;
-  const uint32_t a = (uint32_t)(d < 0 ? -d : d);
-  int p = 0;
-  while ((a >> (p + 1)) != 0u) ++p;  // floor(log2 a), 0..6
-  return s | ((uint32_t)(127 + p) << 7) | ((a << (7 - p)) & 0x7Fu);
-}
-
 __host__ __device__ constexpr unsigned long long digit_bias(int S) {
   unsigned long long b = 0;
   for (int j = 0; j + 1 < S; ++j) b |= 64ull << (7 * j);
   return b;
 }
 
-// Balanced base-2^7 digits of x / 2^(e-6), S of them (first digit 6 bits):
-// F = round(|x| 2^(7S-1-e)) from the FP64 bit pattern.  Adding 64 to every
-// lower digit position, G = F + 64 (1 + 2^7 + ... + 2^(7(S-2))), makes the
-// balanced digits plain fields: d_k = field_k(G) - 64 (k >= 2), d_1 = G >> 7(S-1).
+__host__ __device__ constexpr float pow2_neg7(int k) {
+  float f = 1.0f;
+  for (int i = 0; i < 7 * k; ++i) f *= 0.5f;
+  return f;
+}
+
+// Slice values of x for row exponent e: v_k = d_k 2^(-7k), k = 0..S-1, where
+// d_0 (6 bits) and the balanced base-2^7 digits d_1..d_{S-1} (|d| <= 64)
+// represent round(|x| 2^(7S-1-e)) with the sign of x.  F = round(|x|
+// 2^(7S-1-e)) comes from the FP64 bit pattern; adding 64 to every lower
+// digit position, G = F + 64 (1 + 2^7 + ... + 2^(7(S-2))), turns the
+// balanced digits into plain 7-bit fields, d_k = field_k(G) - 64 (k >= 1),
+// d_0 = G >> 7(S-1).  A field becomes an exact float through the 2^23
+// bit-pattern trick, and the scaling by +-2^(-7k) is exact (at most 7
+// significant bits), so every value is also an exact BF16.
 template <int S>
-__device__ __forceinline__ void digits_of(double x, int e, int (&d)[S]) {
-#pragma unroll
-  for (int k = 0; k < S; ++k) d[k] = 0;
+__device__ __forceinline__ void slice_values(double x, int e, float (&v)[S]) {
   const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
   int E = (int)((bits >> 52) & 0x7FF);
   unsigned long long M = bits & ((1ull << 52) - 1);
   if (E == 0) E = 1; else M |= 1ull << 52;
   const int shift = E - 1075 + 7 * S - 1 - e;
-  if (M == 0 || shift <= -63) return;
-  unsigned long long F;
-  if (shift >= 0) {
-    F = M << shift;
-  } else {
-    const int rs = -shift;
-    F = (M >> rs) + ((M >> (rs - 1)) & 1ull);
+  unsigned long long F = 0;
+  if (M != 0 && shift > -63) {
+    if (shift >= 0) {
+      F = M << shift;
+    } else {
+      const int rs = -shift;
+      F = (M >> rs) + ((M >> (rs - 1)) & 1ull);
+    }
   }
   constexpr unsigned long long kBias = digit_bias(S);
   const unsigned long long G = F + kBias;
-  const uint32_t lo = (uint32_t)G, hi = (uint32_t)(G >> 32);
+  const float sgn = (bits >> 63) ? -1.0f : 1.0f;
 #pragma unroll
-  for (int k = 1; k < S; ++k) {
+  for (int k = 0; k < S; ++k) {
     const int sh = 7 * (S - 1 - k);
-    uint32_t u;
-    if (sh + 7 <= 32) u = (lo >> sh) & 127u;
-    else if (sh >= 32) u = (hi >> (sh - 32)) & 127u;
-    else u = ((lo >> sh) | (hi << (32 - sh))) & 127u;
-    d[k] = (int)u - 64;
+    const uint32_t field = k == 0 ? (uint32_t)(G >> sh) : (uint32_t)(G >> sh) & 127u;
+    const float d = __fsub_rn(__uint_as_float(0x4B000000u | field), k == 0 ? 8388608.0f : 8388672.0f);
+    v[k] = __fmul_rn(d, sgn * pow2_neg7(k));
   }
-  {
-    constexpr int sh = 7 * (S - 1);
-    uint32_t u;
-    if constexpr (sh >= 32) u = hi >> (sh - 32);
-    else if constexpr (sh == 0) u = lo;
-    else u = (lo >> sh) | (hi << (32 - sh));
-    d[0] = (int)u;
-  }
-  if (bits >> 63) {
+}
+
+// BF16 pairs of the slice values of two adjacent elements: x0 in the low half of each word.
+template <int S>
+__device__ __forceinline__ void pack_digits(const double x0, const double x1, int e, uint32_t (&w)[S]) {
+  float v0[S], v1[S];
+  slice_values<S>(x0, e, v0);
+  slice_values<S>(x1, e, v1);
 #pragma unroll
-    for (int k = 0; k < S; ++k) d[k] = -d[k];
-  }
+  for (int k = 0; k < S; ++k) w[k] = __byte_perm(__float_as_uint(v0[k]), __float_as_uint(v1[k]), 0x7632);
 }
 
 __device__ __forceinline__ int64_t mixed_offset(int32_t idx, int n, const int32_t* dim, const int32_t* stride) {
@@ -114,20 +110,6 @@ __device__ __forceinline__ void k_offsets8(const SliceBlock& B, int32_t k0, int6
   }
 }
 
-template <int S>
-__device__ __forceinline__ void pack_digits(const double x0, const double x1, int e, uint32_t (&w)[S],
-                                            const uint32_t* lut) {
-  int d0[S], d1[S];
-  digits_of<S>(x0, e, d0);
-  digits_of<S>(x1, e, d1);
-#pragma unroll
-  for (int s = 0; s < S; ++s) {
-    const uint32_t v0 = lut[d0[s] + 64], v1 = lut[d1[s] + 64];
-    const uint32_t sub = (uint32_t)(7 * s << 7);
-    w[s] = (v0 ? v0 - sub : 0u) | ((v1 ? v1 - sub : 0u) << 16);
-  }
-}
-
 // bf16 bits of a float, round to nearest even (finite inputs).
 __device__ __forceinline__ uint32_t bf16_rne(float f) {
   const uint32_t u = __float_as_uint(f);
@@ -152,128 +134,124 @@ __device__ __forceinline__ void pack_float3(const double x0, const double x1, ui
   for (int k = 0; k < 3; ++k) w[k] = b[k][0] | (b[k][1] << 16);
 }
 
-// One CTA slices rows [r0, r0+nr) of one block.
-// Dense summed range: the strip is brought into shared memory by 1-D bulk
-// copies (one per row), row maxima come from warp reductions, and each lane
-// turns two consecutive elements into one 32-bit word per slice, so shared
-// reads are conflict-free and every warp store fills whole 32-byte sectors.
+constexpr long long kSliceWaitCycles = 4000000000ll;  // ~2 s at 2 GHz: a bounded wait gives up after this
+
+// One CTA (W = blockDim.x / 32 warps) slices rows [r0, r0+nr) of one block.
+// Dense summed range (every row one contiguous run): one warp per row, nr <=
+// W.  The row comes into the warp's shared buffer through one 1-D bulk copy
+// of its 16-byte-aligned span (the start rounded down, so element k sits at
+// k + shift; the at most one element past the rounded-down end by a plain
+// load), so HBM is read once.  The row maximum comes from conflict-free
+// strided reads and a warp reduction; then each lane turns two adjacent
+// elements into one 32-bit word per slice, a warp's stores filling whole
+// 32-byte sectors of four tiles.
 // Other layouts: 8-wide units read straight from global memory twice, lanes
 // walking rows fastest so that the contiguous direction is coalesced.
+// `kbuf`: doubles per warp buffer (>= K + 2 of every dense block, even);
+// `bulk`: the source base is 16-byte aligned, so that rounding a row's start
+// down stays inside the tensor.
 template <int S, bool kFloat>
 __global__ void __launch_bounds__(256) ozaki_slice_kernel(const double* __restrict__ src,
                                                           const SliceBlock* __restrict__ blocks,
                                                           const SliceItem* __restrict__ items,
                                                           uint8_t* __restrict__ tiles, int32_t* __restrict__ exps,
-                                                          int* __restrict__ status) {
-  extern __shared__ __align__(16) double strip[];
+                                                          int kbuf, int bulk, int* __restrict__ status) {
+  extern __shared__ __align__(16) double rowbuf[];
   __shared__ unsigned long long rmax[kOzSliceMaxRows];
   __shared__ int rexp[kOzSliceMaxRows];
   __shared__ int64_t roff[kOzSliceMaxRows];
-  __shared__ uint32_t lut[129];
-  __shared__ __align__(8) uint64_t bar;
-  __shared__ int bulk_ok;
+  __shared__ __align__(8) uint64_t wbar[8];
   const SliceItem it = items[blockIdx.x];
   const SliceBlock& B = blocks[it.block];
   const int tid = threadIdx.x, lane = tid % 32, warp = tid / 32;
   const int nr = it.nr;
+  const int K = B.K;
+  const int H = B.tile_rows;
+  const size_t slice_bytes = (size_t)H * 32;  // one slice of one tile: H rows x 16 bf16
+  const size_t tile_bytes = (size_t)S * slice_bytes;
+
+  if (B.k_dense) {
+    if (warp >= nr) return;  // no block-wide barrier on this path
+    const int32_t grow = it.r0 + warp;
+    const bool live = grow < B.rows;
+    double* buf = rowbuf + (size_t)warp * kbuf;
+    int shift = 0;
+    if (live) {
+      const double* xr = src + B.src_off + mixed_offset(grow, B.nr, B.rdim, B.rstride);
+      int copied = 0;  // elements of the row now in buf
+      if (bulk) {
+        const uintptr_t s0 = reinterpret_cast<uintptr_t>(xr);
+        const uintptr_t a0 = s0 & ~uintptr_t(15), a1 = (s0 + (uintptr_t)K * 8) & ~uintptr_t(15);
+        shift = (int)((s0 - a0) >> 3);
+        if (a1 > a0) {
+          const uint32_t nbytes = (uint32_t)(a1 - a0);
+          copied = (int)(nbytes >> 3) - shift;
+          if (lane == 0) {
+            sm100::mbar_init(&wbar[warp], 1);
+            sm100::fence_mbar_init();
+            sm100::mbar_arrive_expect_tx(&wbar[warp], nbytes);
+            sm100::bulk_g2s(buf, reinterpret_cast<const void*>(a0), nbytes, &wbar[warp]);
+          }
+          __syncwarp();
+          const long long t0 = clock64();
+          bool ok = true;
+          while (!sm100::mbar_try_wait(&wbar[warp], 0)) {
+            if (clock64() - t0 > kSliceWaitCycles) {
+              ok = false;
+              break;
+            }
+          }
+          if (!__all_sync(0xffffffffu, ok)) {
+            if (lane == 0) atomicExch(status, TAMM_ETIMEOUT);
+            const long long t1 = clock64();  // the copy must land before the CTA may exit
+            while (!sm100::mbar_try_wait(&wbar[warp], 0) && clock64() - t1 < kSliceWaitCycles) {
+            }
+            return;
+          }
+        }
+      }
+      for (int k = copied + lane; k < K; k += 32) buf[shift + k] = __ldg(xr + k);
+      __syncwarp();
+    }
+    unsigned long long m = 0ull;
+    if (live)
+      for (int k = lane; k < K; k += 32)
+        m = max(m, (unsigned long long)__double_as_longlong(buf[shift + k]) & 0x7FFFFFFFFFFFFFFFull);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+    int e = kOzExpZero;
+    if (m != 0ull) (void)frexp(__longlong_as_double((long long)m), &e);
+    if (kFloat && m != 0ull) e = 6;  // floating pieces: unit scale
+    if (lane == 0) exps[B.exp_off + grow] = e;
+    const int32_t rr = grow % H;
+    uint8_t* rbase = tiles + B.tile_off + (size_t)(grow / H) * B.k_tiles * tile_bytes + rr * 32;
+    const int swz_row = (rr >> 2) & 1;
+    const int npairs = B.k_tiles * 8;  // 32-bit words (element pairs) per row of the padded K range
+    for (int pw = lane; pw < npairs; pw += 32) {
+      uint32_t wd[S];
+#pragma unroll
+      for (int q = 0; q < S; ++q) wd[q] = 0u;
+      const int k = 2 * pw;
+      if (e != kOzExpZero && k < K) {
+        const double x0 = buf[shift + k];
+        const double x1 = k + 1 < K ? buf[shift + k + 1] : 0.0;
+        if constexpr (kFloat) pack_float3(x0, x1, wd);
+        else pack_digits<S>(x0, x1, e, wd);
+      }
+      const int wt = pw & 7;
+      uint8_t* base = rbase + (size_t)(pw >> 3) * tile_bytes + (((wt >> 2) ^ swz_row) * 16) + (wt & 3) * 4;
+#pragma unroll
+      for (int q = 0; q < S; ++q) *reinterpret_cast<uint32_t*>(base + (size_t)q * slice_bytes) = wd[q];
+    }
+    return;
+  }
+
   for (int r = tid; r < nr; r += blockDim.x) {
     const int32_t grow = it.r0 + r;
     rmax[r] = 0ull;
     roff[r] = grow < B.rows ? B.src_off + mixed_offset(grow, B.nr, B.rdim, B.rstride) : -1;
   }
-  if (tid < 129) lut[tid] = bf16_of_small_int(tid - 64);
   __syncthreads();
-  const int K = B.K;
-  constexpr size_t tile_bytes = (size_t)S * kOzTileBytesPerSlice;
-  const bool staged = B.k_dense && (int64_t)nr * K * 8 <= kOzStageBytes;
-
-  if (staged) {
-    if (tid == 0) {
-      bool ok = (K % 2) == 0 && (reinterpret_cast<uintptr_t>(src) & 15) == 0;
-      for (int r = 0; r < nr; ++r)
-        if (roff[r] >= 0 && (roff[r] & 1)) ok = false;
-      bulk_ok = ok;
-      if (ok) {
-        sm100::mbar_init(&bar, 1);
-        sm100::fence_mbar_init();
-      }
-    }
-    __syncthreads();
-    if (bulk_ok) {
-      if (tid == 0) {
-        uint32_t bytes = 0;
-        for (int r = 0; r < nr; ++r)
-          if (roff[r] >= 0) bytes += (uint32_t)K * 8u;
-        sm100::mbar_arrive_expect_tx(&bar, bytes);
-        for (int r = 0; r < nr; ++r)
-          if (roff[r] >= 0) sm100::bulk_g2s(strip + (size_t)r * K, src + roff[r], (uint32_t)K * 8u, &bar);
-      }
-      // every thread waits (bounded) for the strip; a timeout is reported, then the copies are drained
-      const long long t0 = clock64();
-      bool ok = true;
-      while (!sm100::mbar_try_wait(&bar, 0)) {
-        if (clock64() - t0 > 4000000000ll) {
-          ok = false;
-          break;
-        }
-      }
-      if (!ok) {
-        if (tid == 0) atomicExch(status, TAMM_ETIMEOUT);
-        const long long t1 = clock64();
-        while (!sm100::mbar_try_wait(&bar, 0) && clock64() - t1 < 4000000000ll) {
-        }
-        return;
-      }
-    } else {
-      for (int i = tid; i < nr * K; i += blockDim.x) {
-        const int r = i / K;
-        strip[i] = roff[r] >= 0 ? __ldg(src + roff[r] + (i - r * K)) : 0.0;
-      }
-      __syncthreads();
-    }
-    // row maxima: one warp per row
-    for (int r = warp; r < nr; r += blockDim.x / 32) {
-      unsigned long long m = 0ull;
-      if (roff[r] >= 0)
-        for (int k = lane; k < K; k += 32)
-          m = max(m, (unsigned long long)__double_as_longlong(strip[(size_t)r * K + k]) & 0x7FFFFFFFFFFFFFFFull);
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
-      if (lane == 0) {
-        int e = kOzExpZero;
-        if (m != 0ull) (void)frexp(__longlong_as_double((long long)m), &e);
-        if (kFloat && m != 0ull) e = 6;  // floating pieces: unit scale
-        rexp[r] = e;
-        exps[B.exp_off + it.r0 + r] = e;
-      }
-    }
-    __syncthreads();
-    // digits: unit u = (row r, 32-bit word w of the padded K range), two elements per word
-    const int nw = B.k_tiles * 8;
-    for (int u = tid; u < nr * nw; u += blockDim.x) {
-      const int r = u / nw, w = u - r * nw;
-      uint32_t wd[S];
-#pragma unroll
-      for (int q = 0; q < S; ++q) wd[q] = 0u;
-      const int e = rexp[r];
-      const int k = 2 * w;
-      if (roff[r] >= 0 && e != kOzExpZero && k < K) {
-        const double x0 = strip[(size_t)r * K + k];
-        const double x1 = k + 1 < K ? strip[(size_t)r * K + k + 1] : 0.0;
-        if constexpr (kFloat) pack_float3(x0, x1, wd);
-        else pack_digits<S>(x0, x1, e, wd, lut);
-      }
-      const int32_t grow = it.r0 + r;
-      const int32_t rr = grow % kOzTileM;
-      const int wt = w & 7;
-      const int swz = (wt >> 2) ^ ((rr >> 2) & 1);
-      const int64_t tile = B.tile_off + (int64_t)(grow / kOzTileM) * B.k_tiles + (w >> 3);
-      uint8_t* base = tiles + (size_t)tile * tile_bytes + rr * 32 + swz * 16 + (wt & 3) * 4;
-#pragma unroll
-      for (int q = 0; q < S; ++q) *reinterpret_cast<uint32_t*>(base + (size_t)q * kOzTileBytesPerSlice) = wd[q];
-    }
-    return;
-  }
 
   // ---- general layouts: two passes over global memory
   const int nch = (K + 7) / 8;
@@ -321,19 +299,19 @@ __global__ void __launch_bounds__(256) ozaki_slice_kernel(const double* __restri
       for (int j = 0; j < 8; j += 2) {
         uint32_t wd[S];
         if constexpr (kFloat) pack_float3(xs[j], xs[j + 1], wd);
-        else pack_digits<S>(xs[j], xs[j + 1], e, wd, lut);
+        else pack_digits<S>(xs[j], xs[j + 1], e, wd);
 #pragma unroll
         for (int q = 0; q < S; ++q) packed[q][j >> 1] = wd[q];
       }
     }
     const int32_t grow = it.r0 + r;
-    const int32_t rr = grow % kOzTileM;
-    const int64_t tile = B.tile_off + (int64_t)(grow / kOzTileM) * B.k_tiles + ch / 2;
+    const int32_t rr = grow % H;
+    const int64_t tile = (int64_t)(grow / H) * B.k_tiles + ch / 2;
     const int swz = (ch & 1) ^ ((rr >> 2) & 1);
-    uint8_t* base = tiles + (size_t)tile * tile_bytes + rr * 32 + swz * 16;
+    uint8_t* base = tiles + B.tile_off + (size_t)tile * tile_bytes + rr * 32 + swz * 16;
 #pragma unroll
     for (int q = 0; q < S; ++q)
-      *reinterpret_cast<uint4*>(base + (size_t)q * kOzTileBytesPerSlice) =
+      *reinterpret_cast<uint4*>(base + (size_t)q * slice_bytes) =
           make_uint4(packed[q][0], packed[q][1], packed[q][2], packed[q][3]);
   }
 }
@@ -410,17 +388,19 @@ __device__ __forceinline__ void epi_barrier() { asm volatile("bar.sync 1, %0;" :
 
 // Issue the MMAs of one K step for schedule (S, fuse), op I onwards; every
 // operand offset, shape and flag is a compile-time constant.
+// B slices are H rows apart (2H descriptor units of 16 bytes) and accumulator
+// regions H TMEM columns apart; idesc1 / idesc2 are the instruction
+// descriptors of one B slice and of two adjacent fused ones.
 template <int S, bool kFuse, int I>
-__device__ __forceinline__ void issue_ops(uint32_t tmem, uint64_t a0, uint64_t b0, uint32_t idesc_ragged,
-                                          bool first) {
+__device__ __forceinline__ void issue_ops(uint32_t tmem, uint64_t a0, uint64_t b0, uint32_t H, uint32_t idesc1,
+                                          uint32_t idesc2, bool first) {
   constexpr OzSched sch = oz_schedule(S, kFuse);
   if constexpr (I < sch.n) {
     constexpr OzOp op = sch.op[I];
-    constexpr uint32_t idesc_full = sm100::idesc_bf16_f32(128, 128 * op.nb);
-    // descriptor start address counts 16-byte units: one 4096-byte slice is +256
-    sm100::mma_bf16(tmem + 128u * op.region, a0 + (uint64_t)(256 * op.a), b0 + (uint64_t)(256 * op.b),
-                    kFuse ? idesc_full : idesc_ragged, (op.first && first) ? 0u : 1u);
-    issue_ops<S, kFuse, I + 1>(tmem, a0, b0, idesc_ragged, first);
+    // descriptor start address counts 16-byte units: one 4096-byte A slice is +256
+    sm100::mma_bf16(tmem + H * (uint32_t)op.region, a0 + (uint64_t)(256 * op.a), b0 + (uint64_t)(2u * H * op.b),
+                    op.nb == 2 ? idesc2 : idesc1, (op.first && first) ? 0u : 1u);
+    issue_ops<S, kFuse, I + 1>(tmem, a0, b0, H, idesc1, idesc2, first);
   }
 }
 
@@ -436,7 +416,7 @@ __global__ void __launch_bounds__(kThreads, 1) ozaki_gemm_kernel(const __grid_co
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const int stages = p.stages;
-  constexpr uint32_t half_bytes = (uint32_t)S * kOzTileBytesPerSlice;  // A (or B) part of a stage
+  constexpr uint32_t half_bytes = (uint32_t)S * kOzTileBytesPerSlice;  // A part of a stage (B part: at most this)
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + (size_t)stages * 2 * half_bytes);
   uint64_t* full = bars;
   uint64_t* empty = bars + stages;
@@ -485,16 +465,17 @@ __global__ void __launch_bounds__(kThreads, 1) ozaki_gemm_kernel(const __grid_co
         const uint8_t* a_tiles = p.problems[q].a_tiles;
         const uint8_t* b_tiles = p.problems[q].b_tiles;
         const OzGroup g = p.problems[q].groups[it.group];
+        const uint32_t b_bytes = (uint32_t)S * 32u * (uint32_t)g.n_tile;
         for (int t = g.task_begin; t < g.task_end && !*abort_flag; ++t) {
           const OzTask tk = tasks[t];
-          const uint8_t* a = a_tiles + (size_t)(tk.a_tile + (int64_t)it.mt * tk.k_tiles) * half_bytes;
-          const uint8_t* b = b_tiles + (size_t)(tk.b_tile + (int64_t)it.nt * tk.k_tiles) * half_bytes;
+          const uint8_t* a = a_tiles + tk.a_off + (size_t)((int64_t)it.mt * tk.k_tiles) * half_bytes;
+          const uint8_t* b = b_tiles + tk.b_off + (size_t)((int64_t)it.nt * tk.k_tiles) * b_bytes;
           for (int kt = 0; kt < tk.k_tiles; ++kt) {
             if (!wait_bounded(&empty[stage], phase ^ 1u, abort_flag, p.status)) break;
             uint8_t* sa = smem + (size_t)stage * 2 * half_bytes;
-            sm100::mbar_arrive_expect_tx(&full[stage], 2 * half_bytes);
+            sm100::mbar_arrive_expect_tx(&full[stage], half_bytes + b_bytes);
             sm100::bulk_g2s(sa, a + (size_t)kt * half_bytes, half_bytes, &full[stage]);
-            sm100::bulk_g2s(sa + half_bytes, b + (size_t)kt * half_bytes, half_bytes, &full[stage]);
+            sm100::bulk_g2s(sa + half_bytes, b + (size_t)kt * b_bytes, b_bytes, &full[stage]);
             issued_mask |= 1u << stage;
             issued_parity = (issued_parity & ~(1u << stage)) | (phase << stage);
             if (++stage == stages) {
@@ -524,9 +505,12 @@ __global__ void __launch_bounds__(kThreads, 1) ozaki_gemm_kernel(const __grid_co
         const OzItem it = p.problems[q].items[i - p.problems[q].item_begin];
         const OzTask* tasks = p.problems[q].tasks;
         const OzGroup g = p.problems[q].groups[it.group];
-        const int n_valid = min(kOzTileN, g.N - it.nt * kOzTileN);
-        const bool full_tile = n_valid == kOzTileN;
-        const uint32_t idesc_ragged = sm100::idesc_bf16_f32(128, (uint32_t)((n_valid + 15) & ~15));
+        const uint32_t H = (uint32_t)g.n_tile;
+        const int n_valid = min((int)H, g.N - it.nt * (int)H);
+        const bool full_tile = n_valid == (int)H;
+        // a ragged tile runs unfused with N rounded up to 16 columns
+        const uint32_t idesc1 = sm100::idesc_bf16_f32(128, full_tile ? H : (uint32_t)((n_valid + 15) & ~15));
+        const uint32_t idesc2 = sm100::idesc_bf16_f32(128, 2u * H);
         for (int t = g.task_begin; t < g.task_end && ok; ++t) {
           const int k_tiles = tasks[t].k_tiles;
           int in_chunk = 0;  // position inside the current chunk (no division on the issue path)
@@ -544,8 +528,8 @@ __global__ void __launch_bounds__(kThreads, 1) ozaki_gemm_kernel(const __grid_co
             // operand offsets add straight onto the stage-0 descriptor
             const uint64_t a0 = desc_stage0 + (uint64_t)((uint32_t)stage * (2u * half_bytes >> 4));
             const uint64_t b0 = a0 + (half_bytes >> 4);
-            if (full_tile) issue_ops<S, true, 0>(tmem, a0, b0, idesc_ragged, first);
-            else issue_ops<S, false, 0>(tmem, a0, b0, idesc_ragged, first);
+            if (full_tile) issue_ops<S, true, 0>(tmem, a0, b0, H, idesc1, idesc2, first);
+            else issue_ops<S, false, 0>(tmem, a0, b0, H, idesc1, idesc2, first);
             sm100::mma_commit(&empty[stage]);
             if (last) {
               sm100::mma_commit(acc_full);
@@ -584,15 +568,16 @@ __global__ void __launch_bounds__(kThreads, 1) ozaki_gemm_kernel(const __grid_co
       const int32_t* a_exp = p.problems[q].a_exp;
       const int32_t* b_exp = p.problems[q].b_exp;
       const OzGroup g = p.problems[q].groups[it.group];
-      const int n_valid = min(kOzTileN, g.N - it.nt * kOzTileN);
+      const int H = g.n_tile;
+      const int n_valid = min(H, g.N - it.nt * H);
       epi_barrier();  // the previous item's output writes (which read fref) are done
       int Eref = kOzExpZero;
       for (int t = g.task_begin; t < g.task_end; ++t)
         Eref = max(Eref, a_exp[tasks[t].a_exp + (int64_t)it.mt * kOzTileM + row]);
-      if (etid < kOzTileN) {
+      if (etid < H) {
         int F = kOzExpZero;
         for (int t = g.task_begin; t < g.task_end; ++t)
-          F = max(F, b_exp[tasks[t].b_exp + (int64_t)it.nt * kOzTileN + etid]);
+          F = max(F, b_exp[tasks[t].b_exp + (int64_t)it.nt * H + etid]);
         fref[etid] = F;
       }
       float hi[64], lo[64];
@@ -602,8 +587,8 @@ __global__ void __launch_bounds__(kThreads, 1) ozaki_gemm_kernel(const __grid_co
         const OzTask tk = tasks[t];
         float* sbuf = sB + (task_count & 1u) * 128;
         epi_barrier();  // fref is set, and sbuf's previous readers (two tasks ago) are done
-        if (etid < kOzTileN) {
-          const int eb = b_exp[tk.b_exp + (int64_t)it.nt * kOzTileN + etid];
+        if (etid < H) {
+          const int eb = b_exp[tk.b_exp + (int64_t)it.nt * H + etid];
           sbuf[etid] = (eb == kOzExpZero) ? 0.0f : pow2f(eb - fref[etid]);
         }
         epi_barrier();
@@ -618,13 +603,13 @@ __global__ void __launch_bounds__(kThreads, 1) ozaki_gemm_kernel(const __grid_co
             const int col = c0 + 8 * g8;
             if (col >= n_valid) break;  // columns past a ragged tile's width were not computed
             float r0[8], r1[8], r2[8], r3[8];
-            sm100::tmem_ld8(trow + 0 * 128 + col, r0);
-            sm100::tmem_ld8(trow + 1 * 128 + col, r1);
-            sm100::tmem_ld8(trow + 2 * 128 + col, r2);
+            sm100::tmem_ld8(trow + 0 * H + col, r0);
+            sm100::tmem_ld8(trow + 1 * H + col, r1);
+            sm100::tmem_ld8(trow + 2 * H + col, r2);
             // with S < 4 no product has k + l >= 5: region 3 is never written and holds stale
             // TMEM contents of an earlier kernel, so it must not be read
             if constexpr (S >= 4) {
-              sm100::tmem_ld8(trow + 3 * 128 + col, r3);
+              sm100::tmem_ld8(trow + 3 * H + col, r3);
             } else {
 #pragma unroll
               for (int j = 0; j < 8; ++j) r3[j] = 0.0f;
@@ -643,7 +628,7 @@ __global__ void __launch_bounds__(kThreads, 1) ozaki_gemm_kernel(const __grid_co
       if (ok) {
         const int grow = it.mt * kOzTileM + row;
         if (grow < g.M) {
-          double* crow = p.problems[q].c + g.c_off + (int64_t)grow * g.N + (int64_t)it.nt * kOzTileN;
+          double* crow = p.problems[q].c + g.c_off + (int64_t)grow * g.N + (int64_t)it.nt * H;
           const double alpha = p.problems[q].alpha, beta = p.problems[q].beta;
 #pragma unroll
           for (int j = 0; j < 64; ++j) {
@@ -675,36 +660,42 @@ __global__ void __launch_bounds__(kThreads, 1) ozaki_gemm_kernel(const __grid_co
 
 template <int S, bool kFloat = false>
 static cudaError_t slice_dispatch(tamm_ctx* ctx, const double* src, const SliceBlock* blocks, const SliceItem* items,
-                                  int64_t n_items, uint8_t* tiles, int32_t* exps) {
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(ozaki_slice_kernel<S, kFloat>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, kOzStageBytes);
+                                  int64_t n_items, uint8_t* tiles, int32_t* exps, int warps, int kbuf) {
+  static size_t attr_bytes = 0;  // dynamic shared memory opted in so far (per instantiation)
+  const size_t smem = (size_t)warps * kbuf * sizeof(double);
+  if (smem > attr_bytes) {
+    cudaError_t e = cudaFuncSetAttribute(ozaki_slice_kernel<S, kFloat>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
     if (e != cudaSuccess) return e;
-    attr = true;
+    attr_bytes = smem;
   }
-  ozaki_slice_kernel<S, kFloat><<<(unsigned)n_items, 256, kOzStageBytes, ctx->stream>>>(src, blocks, items, tiles,
-                                                                                        exps, ctx->d_status);
+  const int bulk = (reinterpret_cast<uintptr_t>(src) & 15) == 0 ? 1 : 0;
+  ozaki_slice_kernel<S, kFloat><<<(unsigned)n_items, 32 * warps, smem, ctx->stream>>>(src, blocks, items, tiles,
+                                                                                      exps, kbuf, bulk,
+                                                                                      ctx->d_status);
   return cudaGetLastError();
 }
 
 cudaError_t launch_ozaki_slice(tamm_ctx* ctx, const double* src, const SliceBlock* blocks, const SliceItem* items,
-                               int64_t n_items, int S, bool float_split, uint8_t* tiles, int32_t* exps) {
+                               int64_t n_items, int S, bool float_split, uint8_t* tiles, int32_t* exps, int warps,
+                               int kbuf) {
   if (n_items == 0) return cudaSuccess;
+  if (warps < 1 || warps > 8 || kbuf < 2 || (size_t)warps * kbuf * sizeof(double) > kOzSliceSmemMax)
+    return cudaErrorInvalidValue;
   kernel_begin(ctx, TAMM_KERNEL_SLICE);
   cudaError_t e = cudaErrorInvalidValue;
   if (float_split) {
-    if (S == 3) e = slice_dispatch<3, true>(ctx, src, blocks, items, n_items, tiles, exps);
+    if (S == 3) e = slice_dispatch<3, true>(ctx, src, blocks, items, n_items, tiles, exps, warps, kbuf);
     kernel_end(ctx, TAMM_KERNEL_SLICE);
     return e;
   }
   switch (S) {
-    case 3: e = slice_dispatch<3>(ctx, src, blocks, items, n_items, tiles, exps); break;
-    case 4: e = slice_dispatch<4>(ctx, src, blocks, items, n_items, tiles, exps); break;
-    case 5: e = slice_dispatch<5>(ctx, src, blocks, items, n_items, tiles, exps); break;
-    case 6: e = slice_dispatch<6>(ctx, src, blocks, items, n_items, tiles, exps); break;
-    case 7: e = slice_dispatch<7>(ctx, src, blocks, items, n_items, tiles, exps); break;
-    case 8: e = slice_dispatch<8>(ctx, src, blocks, items, n_items, tiles, exps); break;
+    case 3: e = slice_dispatch<3>(ctx, src, blocks, items, n_items, tiles, exps, warps, kbuf); break;
+    case 4: e = slice_dispatch<4>(ctx, src, blocks, items, n_items, tiles, exps, warps, kbuf); break;
+    case 5: e = slice_dispatch<5>(ctx, src, blocks, items, n_items, tiles, exps, warps, kbuf); break;
+    case 6: e = slice_dispatch<6>(ctx, src, blocks, items, n_items, tiles, exps, warps, kbuf); break;
+    case 7: e = slice_dispatch<7>(ctx, src, blocks, items, n_items, tiles, exps, warps, kbuf); break;
+    case 8: e = slice_dispatch<8>(ctx, src, blocks, items, n_items, tiles, exps, warps, kbuf); break;
   }
   kernel_end(ctx, TAMM_KERNEL_SLICE);
   return e;
@@ -735,7 +726,7 @@ static cudaError_t gemm_dispatch(tamm_ctx* ctx, const OzParams& p, int grid) {
 }
 
 cudaError_t launch_ozaki_gemm(tamm_ctx* ctx, OzProblem* problems, const int64_t* n_items_per_problem,
-                              int n_problems, int S, int chunk_tiles) {
+                              int n_problems, int S, int chunk_tiles, bool persistent) {
   if (chunk_tiles < 1 || chunk_tiles > kOzChunkTiles) return cudaErrorInvalidValue;
   if (n_problems < 1 || n_problems > kOzMaxProblems) return cudaErrorInvalidValue;
   int64_t n_items = 0;
@@ -752,7 +743,7 @@ cudaError_t launch_ozaki_gemm(tamm_ctx* ctx, OzProblem* problems, const int64_t*
   p.n_problems = n_problems;
   for (int i = 0; i < n_problems; ++i) p.problems[i] = problems[i];
   // persistent: one CTA per SM walks items round-robin; otherwise one CTA per item
-  const int grid = ctx->oz_persistent ? (int)std::min<int64_t>(n_items, std::max(1, ctx->sm_count))
+  const int grid = persistent ? (int)std::min<int64_t>(n_items, std::max(1, ctx->sm_count))
                                       : (int)std::min<int64_t>(n_items, 0x7FFFFFFF);
   kernel_begin(ctx, TAMM_KERNEL_GEMM_OZ);
   cudaError_t e = cudaErrorInvalidValue;
@@ -787,12 +778,16 @@ struct OzakiPlan : Plan {
   int64_t n_items = 0;
   std::unique_ptr<AddPlan> perm_out;
   size_t off_ta = 0, off_tb = 0, off_ea = 0, off_eb = 0, off_x = 0, scratch_bytes = 0;
+  int warps_a = 8, kbuf_a = 2, warps_b = 8, kbuf_b = 2;  // slicing launch shapes
 
   // Slice records for the GEMM-order operand `gemm` (blocks of `native`
   // permuted by perm); row modes are [r0, r0+nr), summed modes [k0, k0+nk).
+  // tile_policy < 0: 128-row tiles (A operands); else oz_tile_rows(rows, tile_policy) (B operands).
+  // `bytes` accumulates the sliced image size of S slices, `exps` the exponent count; `warps` and
+  // `kbuf` are the slicing launch's warps per CTA and doubles per warp row buffer.
   static void slice_blocks(const tamm_tensor& native, const tamm_tensor& gemm, const std::vector<int>& perm,
-                           int r0, int nr, int k0, int nk, std::vector<SliceBlock>& out,
-                           std::vector<SliceItem>& items, int64_t& tiles, int64_t& exps) {
+                           int r0, int nr, int k0, int nk, int S, int tile_policy, std::vector<SliceBlock>& out,
+                           std::vector<SliceItem>& items, int64_t& bytes, int64_t& exps, int& warps, int& kbuf) {
     out.resize((size_t)gemm.n_blocks);
     for (int64_t b = 0; b < gemm.n_blocks; ++b) {
       const int64_t* gt = &gemm.tiles[(size_t)(b * gemm.nm)];
@@ -825,7 +820,9 @@ struct OzakiPlan : Plan {
       if (rows > (1 << 30) || K > (1 << 30)) throw Error(TAMM_EUNSUPPORTED, "ozaki: block too large");
       B.rows = (int32_t)rows;
       B.K = (int32_t)K;
-      B.row_tiles = (int32_t)((rows + kOzTileM - 1) / kOzTileM);
+      const int H = tile_policy < 0 ? kOzTileM : oz_tile_rows(rows, tile_policy);
+      B.tile_rows = H;
+      B.row_tiles = (int32_t)((rows + H - 1) / H);
       B.k_tiles = (int32_t)((K + kOzTileK - 1) / kOzTileK);
       B.k_contig = (nk > 0 && B.kstride[nk - 1] == 1) ? 1 : 0;
       if (nk == 0) B.k_contig = 1;
@@ -837,27 +834,42 @@ struct OzakiPlan : Plan {
           st *= B.kdim[m];
         }
       }
-      B.tile_off = tiles;
+      B.tile_off = bytes;
       B.exp_off = exps;
-      tiles += (int64_t)B.row_tiles * B.k_tiles;
-      exps += (int64_t)B.row_tiles * kOzTileM;
-      // rows per slicing CTA: a power of two <= 32; for a dense summed range the
-      // largest strip that fits the shared-memory stage, else 32 rows
+      bytes += (int64_t)B.row_tiles * B.k_tiles * S * H * 32;
+      exps += (int64_t)B.row_tiles * H;
+    }
+    // warp row buffers: K + 2 doubles (room for the aligned-down start), for the longest dense row;
+    // as many warps (<= 8) as fit the shared-memory budget.  Rows too long for one warp buffer go
+    // through the general path.
+    int64_t kmax = 0;
+    for (const SliceBlock& B : out)
+      if (B.k_dense) kmax = std::max<int64_t>(kmax, B.K);
+    kbuf = (int)((kmax + 2 + 1) & ~int64_t(1));
+    warps = (int)std::min<int64_t>(8, (int64_t)kOzSliceSmemBudget / ((int64_t)kbuf * 8));
+    if (warps < 1) {
+      for (SliceBlock& B : out) B.k_dense = 0;
+      warps = 8;
+      kbuf = 2;
+    }
+    for (int64_t b = 0; b < gemm.n_blocks; ++b) {
+      const SliceBlock& B = out[(size_t)b];
+      // rows per slicing CTA: one per warp for a dense summed range, else enough rows for every
+      // thread to have work, at least 32 for coalescing along rows
       int R;
       if (B.k_dense) {
-        R = 1;
-        while (R < kOzSliceMaxRows && (int64_t)(2 * R) * K * 8 <= kOzStageBytes) R *= 2;
+        R = warps;
       } else {
-        // enough rows for every thread to have work, at least 32 for coalescing along rows
         R = 32;
-        while (R < kOzSliceMaxRows && (int64_t)R * ((K + 7) / 8) < 1024) R *= 2;
+        while (R < kOzSliceMaxRows && (int64_t)R * ((B.K + 7) / 8) < 32 * warps * 4) R *= 2;
       }
-      for (int32_t r = 0; r < B.row_tiles * kOzTileM; r += R) items.push_back({(int32_t)b, r, R, 0});
+      const int32_t padded = B.row_tiles * B.tile_rows;
+      for (int32_t r = 0; r < padded; r += R) items.push_back({(int32_t)b, r, std::min<int32_t>(R, padded - r), 0});
     }
   }
 
   OzakiPlan(tamm_ctx* c, const tamm_tensor* C, const char* lc, const tamm_tensor* A, const char* la,
-            const tamm_tensor* B, const char* lb, int slices)
+            const tamm_tensor* B, const char* lb, int slices, int tile_policy)
       : Plan(c), lay(c, C, lc, A, la, B, lb), S(slices) {
     const int nfl = (int)lay.free_left.size(), nfr = (int)lay.free_right.size(), nk = (int)lay.summed.size();
     auto perm_of = [](const std::string& need, const std::string& have) {
@@ -868,16 +880,15 @@ struct OzakiPlan : Plan {
     std::vector<SliceBlock> sa, sb;
     std::vector<SliceItem> ia, ib;
     int64_t ta = 0, tb = 0, ea = 0, eb = 0;
-    slice_blocks(*lay.left, lay.left_gemm(), perm_of(lay.need_left, lay.label_left), 0, nfl, nfl, nk, sa, ia, ta,
-                 ea);
-    slice_blocks(*lay.right, lay.right_gemm(), perm_of(lay.need_right, lay.label_right), nk, nfr, 0, nk, sb, ib,
-                 tb, eb);
+    slice_blocks(*lay.left, lay.left_gemm(), perm_of(lay.need_left, lay.label_left), 0, nfl, nfl, nk, S, -1, sa,
+                 ia, ta, ea, warps_a, kbuf_a);
+    slice_blocks(*lay.right, lay.right_gemm(), perm_of(lay.need_right, lay.label_right), nk, nfr, 0, nk, S,
+                 tile_policy, sb, ib, tb, eb, warps_b, kbuf_b);
     auto align = [](size_t x) { return (x + 1023) & ~size_t(1023); };
-    const size_t tile_bytes = (size_t)S * kOzTileBytesPerSlice;
     off_ta = 0;
-    scratch_bytes = align((size_t)ta * tile_bytes);
+    scratch_bytes = align((size_t)ta);
     off_tb = scratch_bytes;
-    scratch_bytes += align((size_t)tb * tile_bytes);
+    scratch_bytes += align((size_t)tb);
     off_ea = scratch_bytes;
     scratch_bytes += align((size_t)ea * 4);
     off_eb = scratch_bytes;
@@ -897,6 +908,8 @@ struct OzakiPlan : Plan {
       gg.c_off = O.off[(size_t)g.out_block];
       gg.M = (int32_t)g.M;
       gg.N = (int32_t)g.N;
+      gg.n_tile = oz_tile_rows(g.N, tile_policy);
+      gg.pad = 0;
       gg.task_begin = (int32_t)tasks.size();
       int64_t Ksum = 0;
       for (int64_t t = g.task_begin; t < g.task_end; ++t) {
@@ -904,6 +917,8 @@ struct OzakiPlan : Plan {
         const SliceBlock& A_ = sa[(size_t)tk.left_block];
         const SliceBlock& B_ = sb[(size_t)tk.right_block];
         if (A_.k_tiles != B_.k_tiles) throw Error(TAMM_EINVAL, "ozaki: K mismatch");
+        if (B_.rows != gg.N || B_.tile_rows != gg.n_tile)
+          throw Error(TAMM_EINVAL, "ozaki: B block rows differ from the output columns");
         tasks.push_back({A_.tile_off, B_.tile_off, A_.exp_off, B_.exp_off, A_.k_tiles, 0});
         Ksum += (int64_t)A_.k_tiles * kOzTileK;
       }
@@ -912,7 +927,7 @@ struct OzakiPlan : Plan {
       gg.task_end = (int32_t)tasks.size();
       const int32_t gi = (int32_t)groups.size();
       groups.push_back(gg);
-      const int32_t mts = (gg.M + kOzTileM - 1) / kOzTileM, nts = (gg.N + kOzTileN - 1) / kOzTileN;
+      const int32_t mts = (gg.M + kOzTileM - 1) / kOzTileM, nts = (gg.N + gg.n_tile - 1) / gg.n_tile;
       for (int32_t mt = 0; mt < mts; ++mt)
         for (int32_t nt = 0; nt < nts; ++nt) items.push_back({0, gi, mt, nt});
     }
@@ -933,6 +948,8 @@ void run_contract_ozaki(tamm_ctx* ctx, double alpha, tamm_tensor* C, const char*
                         const tamm_tensor* A, const char* la, const tamm_tensor* B, const char* lb, int slices,
                         bool float_split) {
   int chunk_k = ctx->oz_chunk_k;
+  int tile_policy = ctx->oz_tile_policy;
+  bool persistent = ctx->oz_persistent;
   if (slices == 0) {
     slices = kOzDefaultSlices;
     if (!float_split) {
@@ -940,20 +957,23 @@ void run_contract_ozaki(tamm_ctx* ctx, double alpha, tamm_tensor* C, const char*
       if (t != ctx->tuned.end()) {
         slices = t->second.slices;
         chunk_k = t->second.chunk_k;
+        tile_policy = t->second.tile_policy;
+        persistent = t->second.persistent;
       }
     }
   }
   if (slices < kOzMinSlices || slices > kOzMaxSlices)
     throw Error(TAMM_EINVAL, "ozaki: slices must be %d..%d (0 = %d)", kOzMinSlices, kOzMaxSlices, kOzDefaultSlices);
-  const std::string key = "oz" + std::to_string(slices) + "|" + std::to_string(C->id) + "|" + lc + "|" +
-                          std::to_string(A->id) + "|" + la + "|" + std::to_string(B->id) + "|" + lb;
+  const std::string key = "oz" + std::to_string(slices) + "|" + std::to_string(tile_policy) + "|" +
+                          std::to_string(C->id) + "|" + lc + "|" + std::to_string(A->id) + "|" + la + "|" +
+                          std::to_string(B->id) + "|" + lb;
   OzakiPlan* p;
   auto itp = ctx->plans.find(key);
   if (itp != ctx->plans.end()) {
     p = static_cast<OzakiPlan*>(itp->second.get());
   } else {
     if (ctx->capturing) throw Error(TAMM_EINVAL, "a new contraction plan cannot be built during graph capture");
-    p = new OzakiPlan(ctx, C, lc, A, la, B, lb, slices);
+    p = new OzakiPlan(ctx, C, lc, A, la, B, lb, slices, tile_policy);
     ctx->plans[key].reset(p);
   }
   OzOpRecord op;
@@ -971,6 +991,7 @@ void run_contract_ozaki(tamm_ctx* ctx, double alpha, tamm_tensor* C, const char*
   op.left_bytes = (size_t)L->n_elems * 8;
   op.right_bytes = (size_t)R->n_elems * 8;
   op.chunk_k = chunk_k;
+  op.persistent = persistent;
   if (ctx->group_active) {
     ctx->group_ops.push_back(op);
     return;
@@ -998,10 +1019,10 @@ void execute_ozaki(tamm_ctx* ctx, const std::vector<OzOpRecord>& ops) {
     int32_t* ea = (int32_t*)(s + p->off_ea);
     int32_t* eb = (int32_t*)(s + p->off_eb);
     cuda_check(launch_ozaki_slice(ctx, ops[i].left, p->d_sa, p->d_ia, p->n_ia, ops[i].slices, ops[i].float_split,
-                                  ta, ea),
+                                  ta, ea, p->warps_a, p->kbuf_a),
                "ozaki slice (left)");
     cuda_check(launch_ozaki_slice(ctx, ops[i].right, p->d_sb, p->d_ib, p->n_ib, ops[i].slices,
-                                  ops[i].float_split, tb, eb),
+                                  ops[i].float_split, tb, eb, p->warps_b, p->kbuf_b),
                "ozaki slice (right)");
     OzProblem& pr = probs[i];
     pr.a_tiles = ta;
@@ -1016,20 +1037,22 @@ void execute_ozaki(tamm_ctx* ctx, const std::vector<OzOpRecord>& ops) {
     pr.beta = p->perm_out ? 0.0 : ops[i].beta;
     counts[i] = p->n_items;
   }
-  // one GEMM launch per (slice count, chunk length), at most kOzMaxProblems problems each
+  // one GEMM launch per (slice count, chunk length, grid kind), at most kOzMaxProblems problems each
   std::vector<bool> done(ops.size(), false);
   for (size_t i = 0; i < ops.size(); ++i) {
     if (done[i]) continue;
     std::vector<OzProblem> batch;
     std::vector<int64_t> n;
     for (size_t j = i; j < ops.size() && (int)batch.size() < kOzMaxProblems; ++j) {
-      if (done[j] || ops[j].slices != ops[i].slices || ops[j].chunk_k != ops[i].chunk_k) continue;
+      if (done[j] || ops[j].slices != ops[i].slices || ops[j].chunk_k != ops[i].chunk_k ||
+          ops[j].persistent != ops[i].persistent)
+        continue;
       batch.push_back(probs[j]);
       n.push_back(counts[j]);
       done[j] = true;
     }
     cuda_check(launch_ozaki_gemm(ctx, batch.data(), n.data(), (int)batch.size(), ops[i].slices,
-                                 ops[i].chunk_k / kOzTileK),
+                                 ops[i].chunk_k / kOzTileK, ops[i].persistent),
                "ozaki gemm");
   }
   const double one = 1.0;

@@ -19,6 +19,8 @@
 //     C = beta*C + alpha * 2^(Eref+Fref-12) * (hi + lo).
 #pragma once
 
+#include <algorithm>
+
 #include "tamm_contract.h"
 
 namespace tamm {
@@ -41,7 +43,7 @@ constexpr int kOzMaxOps = 40;
 // with r, k decomposed row-major over rdim / kdim.
 struct SliceBlock {
   int64_t src_off;
-  int64_t tile_off;  // first tile of this block in the sliced buffer (tiles ordered [row tile][k tile])
+  int64_t tile_off;  // byte offset of this block's first tile in the sliced buffer (tiles ordered [row tile][k tile])
   int64_t exp_off;   // exponent of row 0
   int32_t rows, K;
   int32_t row_tiles, k_tiles;
@@ -50,13 +52,17 @@ struct SliceBlock {
   int32_t kdim[4], kstride[4];
   int32_t k_contig;  // consecutive k are adjacent in memory (else consecutive rows are)
   int32_t k_dense;   // the whole summed range is one contiguous run: offset of k is k
+  int32_t tile_rows; // rows per tile H (a multiple of 16, <= 128): a tile is S slices of H x 16 bf16
+  int32_t pad;
 };
 
 constexpr int kOzSliceMaxRows = 128;  // rows per slicing CTA
+constexpr size_t kOzSliceSmemBudget = 104 * 1024;  // warp row buffers of one slicing CTA (two CTAs per SM)
+constexpr size_t kOzSliceSmemMax = 200 * 1024;     // launch check
 
 struct SliceItem {
   int32_t block;
-  int32_t r0;  // first row (padding rows up to row_tiles*128 are written as zeros)
+  int32_t r0;  // first row (padding rows up to row_tiles * tile_rows are written as zeros)
   int32_t nr;
   int32_t pad;
 };
@@ -65,10 +71,12 @@ struct OzGroup {
   int64_t c_off;
   int32_t M, N;
   int32_t task_begin, task_end;
+  int32_t n_tile;  // output columns per work item = rows per B tile (a multiple of 16, <= 128)
+  int32_t pad;
 };
 
 struct OzTask {
-  int64_t a_tile, b_tile;  // first tile of the A / B block
+  int64_t a_off, b_off;    // byte offsets of the A / B block's first tile
   int64_t a_exp, b_exp;    // exponent offsets of the A / B block
   int32_t k_tiles;
   int32_t pad;
@@ -129,14 +137,33 @@ __host__ __device__ constexpr OzSched oz_schedule(int S, bool fuse) {
   return s;
 }
 
-constexpr int kOzStageBytes = 48 * 1024;  // shared-memory strip of one slicing CTA
+
+// Rows per B tile (= output columns per work item) for a B block of `rows`
+// rows, a multiple of 16 in [16, 128].
+//   policy 0: always 128 (a block's last tile is ragged; its MMAs run with N
+//             rounded up to 16, but its image is padded to 128 rows);
+//   policy 1: 128, or rows rounded up to 16 when the block has fewer rows
+//             (same tiles, smaller images and copies for narrow blocks);
+//   policy 2: the fewest tiles of 128 at most, of equal width rounded up to
+//             16 (no ragged tile, so every tile runs the fused N = 2H MMAs).
+inline int oz_tile_rows(int64_t rows, int policy) {
+  if (rows <= 0) return 128;
+  const auto up16 = [](int64_t x) { return (int)std::max<int64_t>(16, (x + 15) / 16 * 16); };
+  if (policy == 1) return rows >= 128 ? 128 : up16(rows);
+  if (policy == 2) {
+    const int64_t n = (rows + 127) / 128;
+    return std::min(128, up16((rows + n - 1) / n));
+  }
+  return 128;
+}
 
 // float_split (S = 3 only): BF16x3 floating pieces instead of integer digits.
 cudaError_t launch_ozaki_slice(tamm_ctx* ctx, const double* src, const SliceBlock* blocks, const SliceItem* items,
-                               int64_t n_items, int S, bool float_split, uint8_t* tiles, int32_t* exps);
+                               int64_t n_items, int S, bool float_split, uint8_t* tiles, int32_t* exps, int warps,
+                               int kbuf);
 // One launch over the work items of up to kOzMaxProblems problems (item_begin
 // of each problem is filled in here); `n_items` is the total.
 cudaError_t launch_ozaki_gemm(tamm_ctx* ctx, OzProblem* problems, const int64_t* n_items_per_problem,
-                              int n_problems, int S, int chunk_tiles);
+                              int n_problems, int S, int chunk_tiles, bool persistent);
 
 }  // namespace tamm

@@ -208,6 +208,11 @@ extern "C" tamm_status tamm_ctx_set_option(tamm_ctx* ctx, int option, int64_t va
       ctx->oz_chunk_k = (int)value;
       return;
     }
+    if (option == TAMM_OPT_OZAKI_TILE_POLICY) {
+      if (value < 0 || value > 2) throw Error(TAMM_EINVAL, "tile policy must be 0, 1 or 2");
+      ctx->oz_tile_policy = (int)value;
+      return;
+    }
     if (option == TAMM_OPT_OZAKI_PERSISTENT) {
       if (value != 0 && value != 1) throw Error(TAMM_EINVAL, "persistent must be 0 or 1");
       ctx->oz_persistent = value != 0;

@@ -86,13 +86,16 @@ struct OzOpRecord {
   const double* left;   // GEMM-left operand data
   const double* right;  // GEMM-right operand data
   size_t c_bytes, left_bytes, right_bytes;
-  int chunk_k;  // summed indices per exact FP32 chunk
+  int chunk_k;      // summed indices per exact FP32 chunk
+  bool persistent;  // GEMM grid: one CTA per SM walking the work items
 };
 
 // Split-precision configuration picked by the autotuner for one contraction.
 struct TunedConfig {
   int slices;
   int chunk_k;
+  int tile_policy;
+  bool persistent;
 };
 
 }  // namespace tamm
@@ -143,6 +146,7 @@ struct tamm_ctx {
   bool host_only = false;  // device -1: metadata and planning only
   int oz_chunk_k = 640;    // split precision: summed indices per exact FP32 chunk
   bool oz_persistent = false;  // split precision: persistent GEMM grid (one CTA per SM)
+  int oz_tile_policy = 1;      // split precision: output columns per work item (TAMM_OPT_OZAKI_TILE_POLICY)
   int64_t launches = 0;    // kernels launched by this context
   bool profiling = false;  // bracket launches with CUDA events
   struct TimedLaunch {

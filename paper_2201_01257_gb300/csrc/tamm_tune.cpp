@@ -1,6 +1,8 @@
 // Autotuner of the split-precision contraction: picks the number of BF16
 // slices per operand and the length of the exact FP32 accumulation chunk for
-// one contraction, given a normwise relative error target.
+// one contraction, given a normwise relative error target, and the tile
+// policy (output columns per work item) and GEMM grid kind (one CTA per work
+// item, or one per SM walking the items) that run that configuration fastest.
 //
 // Both knobs trade accuracy for speed.  Fewer slices mean fewer slice
 // products (S(S+1)/2 of them) but a coarser representation of the operands
@@ -12,8 +14,9 @@
 //     slices until its error against the reference is at most
 //     kSafety * target (the first passing count is the fastest one for that
 //     chunk, since time grows with the slice count);
-//   * the run time of every passing candidate (CUDA events, after one
-//     untimed run);
+//   * the run time of every passing candidate under each tile policy and
+//     grid kind (CUDA events, after one untimed run); both split the same
+//     arithmetic into different work items, so they change time, not results;
 // and keeps the fastest.  The result is remembered per (tensors, labels) and
 // used by tamm_contract whenever slices = 0.
 #include <algorithm>
@@ -38,6 +41,7 @@ namespace {
 
 constexpr double kSafety = 0.5;  // margin for other data of the same contraction
 constexpr int kChunks[] = {1280, 640, 320};
+constexpr int kPolicies[] = {0, 1, 2};  // tile policies (TAMM_OPT_OZAKI_TILE_POLICY)
 constexpr int kTimedRuns = 3;
 
 // A view of C's block structure on another buffer (same id: the same cached plans).
@@ -70,13 +74,16 @@ double diff_norm(tamm_ctx* ctx, const double* x, const double* y, int64_t n) {
 
 extern "C" tamm_status tamm_autotune(tamm_ctx* ctx, const tamm_tensor* C, const char* lc, const tamm_tensor* A,
                                      const char* la, const tamm_tensor* B, const char* lb, double target_rel_err,
-                                     int* slices, int* chunk_k, double* rel_err, double* ms) {
+                                     int* slices, int* chunk_k, int* tile_policy, int* persistent,
+                                     double* rel_err, double* ms) {
   if (!ctx) return TAMM_EINVAL;
   void* ref = nullptr;
   void* trial = nullptr;
   size_t bytes = 0;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   const int saved_chunk = ctx->oz_chunk_k;
+  const int saved_policy = ctx->oz_tile_policy;
+  const bool saved_persistent = ctx->oz_persistent;
   tamm_status st = TAMM_OK;
   try {
     if (ctx->host_only) throw Error(TAMM_ECUDA, "host-only context (device -1) cannot run device work");
@@ -91,40 +98,63 @@ extern "C" tamm_status tamm_autotune(tamm_ctx* ctx, const tamm_tensor* C, const 
     run_contract(ctx, 1.0, &R.t, lc, 0.0, A, la, B, lb, TAMM_PREC_F64, 0);
     run_norm(ctx, &R.t, result_slot(ctx, 3));
     const double ref_norm = host_scalar(ctx, result_slot(ctx, 3));
-    const double denom = ref_norm > 0.0 ? ref_norm : 1.0;
+    // a zero product says nothing about the error of other operands: refuse rather than pick 3 slices
+    if (!(ref_norm > 0.0)) throw Error(TAMM_EINVAL, "autotune: the FP64 product of these operands is zero");
+    const double denom = ref_norm;
     cuda_check(cudaEventCreate(&e0), "cudaEventCreate");
     cuda_check(cudaEventCreate(&e1), "cudaEventCreate");
-    int best_s = 0, best_chunk = 0;
+    int best_s = 0, best_chunk = 0, best_policy = 0;
+    bool best_persistent = false;
     double best_ms = 0.0, best_err = 0.0;
     for (int chunk : kChunks) {
       ctx->oz_chunk_k = chunk;
-      for (int s = kOzMinSlices; s <= kOzMaxSlices; ++s) {
+      ctx->oz_tile_policy = saved_policy;
+      ctx->oz_persistent = saved_persistent;
+      int s_ok = 0;
+      double err_ok = 0.0;
+      for (int s = kOzMinSlices; s <= kOzMaxSlices && !s_ok; ++s) {
         run_contract(ctx, 1.0, &X.t, lc, 0.0, A, la, B, lb, TAMM_PREC_OZAKI_BF16, s);
         const double err = diff_norm(ctx, (const double*)trial, (const double*)ref, C->n_elems) / denom;
-        if (!(err <= kSafety * target_rel_err)) continue;
+        if (err <= kSafety * target_rel_err) {
+          s_ok = s;  // more slices only cost more time at this chunk length
+          err_ok = err;
+        }
+      }
+      if (!s_ok) continue;
+      // the tile policy and the grid kind change the work split, not the arithmetic of an output
+      // element: time each combination
+      for (int combo = 0; combo < 2 * (int)(sizeof(kPolicies) / sizeof(kPolicies[0])); ++combo) {
+        const int policy = kPolicies[combo / 2];
+        const bool persistent = combo % 2 == 1;
+        ctx->oz_tile_policy = policy;
+        ctx->oz_persistent = persistent;
+        run_contract(ctx, 1.0, &X.t, lc, 0.0, A, la, B, lb, TAMM_PREC_OZAKI_BF16, s_ok);  // builds the plan
         cuda_check(cudaEventRecord(e0, ctx->stream), "cudaEventRecord");
         for (int r = 0; r < kTimedRuns; ++r)
-          run_contract(ctx, 1.0, &X.t, lc, 0.0, A, la, B, lb, TAMM_PREC_OZAKI_BF16, s);
+          run_contract(ctx, 1.0, &X.t, lc, 0.0, A, la, B, lb, TAMM_PREC_OZAKI_BF16, s_ok);
         cuda_check(cudaEventRecord(e1, ctx->stream), "cudaEventRecord");
         sync_and_check(ctx);
         float f = 0.0f;
         cuda_check(cudaEventElapsedTime(&f, e0, e1), "cudaEventElapsedTime");
         const double t = f / kTimedRuns;
         if (best_s == 0 || t < best_ms) {
-          best_s = s;
+          best_s = s_ok;
           best_chunk = chunk;
+          best_policy = policy;
+          best_persistent = persistent;
           best_ms = t;
-          best_err = err;
+          best_err = err_ok;
         }
-        break;  // more slices only cost more time at this chunk length
       }
     }
     if (best_s == 0)
       throw Error(TAMM_EUNSUPPORTED, "autotune: no slice count (<= %d) reaches %.3g on these operands", kOzMaxSlices,
                   target_rel_err);
-    ctx->tuned[tune_key(C, lc, A, la, B, lb)] = {best_s, best_chunk};
+    ctx->tuned[tune_key(C, lc, A, la, B, lb)] = {best_s, best_chunk, best_policy, best_persistent};
     if (slices) *slices = best_s;
     if (chunk_k) *chunk_k = best_chunk;
+    if (tile_policy) *tile_policy = best_policy;
+    if (persistent) *persistent = best_persistent ? 1 : 0;
     if (rel_err) *rel_err = best_err;
     if (ms) *ms = best_ms;
     ctx->last_error.clear();
@@ -136,6 +166,8 @@ extern "C" tamm_status tamm_autotune(tamm_ctx* ctx, const tamm_tensor* C, const 
     st = TAMM_EINVAL;
   }
   ctx->oz_chunk_k = saved_chunk;
+  ctx->oz_tile_policy = saved_policy;
+  ctx->oz_persistent = saved_persistent;
   if (e0) cudaEventDestroy(e0);
   if (e1) cudaEventDestroy(e1);
   if (ref) ctx_free(ctx, ref, bytes);

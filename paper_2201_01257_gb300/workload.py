@@ -106,6 +106,22 @@ class Runner:
                 out[s.name] = r
         return out
 
+    def autotune(self, target: float = 1e-10, steps=None) -> dict:
+        """Autotune every contraction step (split precision); later runs with slices = 0 use the choices.
+
+        Tune on the values the steps will see: intermediates written by earlier steps must already hold
+        them (run the recipe once first)."""
+        T, ctx, out = self.tensors, self.ctx, {}
+        for step in steps if steps is not None else self.w.steps:
+            if not isinstance(step, wl.ContractSpec):
+                continue
+            if step.antisym:
+                X, lx = self.scratch_for(step)
+                out[step.name] = ctx.autotune(X, lx, T[step.a], step.la, T[step.b], step.lb, target)
+            else:
+                out[step.name] = ctx.autotune(T[step.c], step.lc, T[step.a], step.la, T[step.b], step.lb, target)
+        return out
+
     def run_grouped(self, steps, precision="ozaki_bf16", slices: int = 0) -> None:
         """Independent contraction steps as one contraction group (one grouped GEMM launch), then the
         output antisymmetrisers of those that have one."""

@@ -60,15 +60,19 @@ def test_autotune_meets_target_and_is_used(cfg4):
     print("autotune 1e-10:", tight, " 1e-4:", loose)
     assert tight["rel_err"] <= 0.5e-10 and loose["rel_err"] <= 0.5e-4
     assert loose["slices"] <= tight["slices"]
-    assert 3 <= tight["slices"] <= 8 and tight["chunk_k"] in (320, 640, 1280)
+    assert 3 <= tight["slices"] <= 8 and tight["chunk_k"] in (320, 640, 1280) and tight["tile_policy"] in (0, 1, 2)
     # the last tuning (1e-4) is the remembered one: re-tune at 1e-10 and use it through slices = 0
     tight = ctx.autotune(R, "abij", V, "abef", T, "efij", 1e-10)
     ctx.contract(0.5, R, "abij", 0.0, V, "abef", T, "efij", "ozaki_bf16", 0)
     auto = R.download()
     ctx.set_option(tg.TAMM_OPT_OZAKI_CHUNK_K, tight["chunk_k"])
+    ctx.set_option(tg.TAMM_OPT_OZAKI_TILE_POLICY, tight["tile_policy"])
+    ctx.set_option(tg.TAMM_OPT_OZAKI_PERSISTENT, tight["persistent"])
     ctx.contract(0.5, R, "abij", 0.0, V, "abef", T, "efij", "ozaki_bf16", tight["slices"])
     explicit = R.download()
     ctx.set_option(tg.TAMM_OPT_OZAKI_CHUNK_K, 640)
+    ctx.set_option(tg.TAMM_OPT_OZAKI_TILE_POLICY, 1)
+    ctx.set_option(tg.TAMM_OPT_OZAKI_PERSISTENT, 0)
     assert np.array_equal(auto, explicit)
     _, ot = O.build_workload(wl.Workload(w.name, w.seed, w.spaces,
                                          {k: w.tensors[k] for k in ("V_vvvv", "T", "Tp")}))
@@ -104,3 +108,15 @@ def test_autotune_unreachable_target(cfg4):
     with pytest.raises(tg.TammError) as e:
         ctx.autotune(gt["Tp"], "abij", gt["V_vvvv"], "abef", gt["T"], "efij", -1.0)
     assert e.value.status == tg.TAMM_EINVAL
+
+
+def test_autotune_refuses_a_zero_product(cfg4):
+    import torch
+
+    tg, ctx, w, gt = cfg4
+    zero = torch.zeros_like(gt["T"].data)
+    Tz = ctx.tensor_permuted(gt["T"], [0, 1, 2, 3], allocate=False)
+    Tz.bind(zero)
+    with pytest.raises(tg.TammError) as e:
+        ctx.autotune(gt["Tp"], "abij", gt["V_vvvv"], "abef", Tz, "efij", 1e-10)
+    assert e.value.status == tg.TAMM_EINVAL and "zero" in str(e.value)
