@@ -109,7 +109,9 @@ TAMM_API const char* tamm_last_error(const tamm_ctx* ctx);
 #define TAMM_OPT_OZAKI_TILE_POLICY 2 /* split precision: output columns per work item (= rows per sliced B
                                         tile) for an output block of N columns.  0 = 128; 1 (default) = 128,
                                         or N rounded up to 16 when N < 128; 2 = the fewest tiles of at most
-                                        128 columns, of equal width rounded up to 16 (N = 400 -> 4 x 112) */
+                                        128 columns, of equal width rounded up to 16 (N = 400 -> 4 x 112);
+                                        3 = as 2 with at most 64 columns (N = 400 -> 7 x 64).  Tiles of at
+                                        most 64 (32) columns keep two (four) accumulators in flight */
 /* Set option `option` to `value`.  Errors: TAMM_EINVAL (unknown option or value out of range). */
 TAMM_API tamm_status tamm_ctx_set_option(tamm_ctx* ctx, int option, int64_t value);
 

@@ -340,6 +340,15 @@ constexpr int kRegsHigh = 232;
 constexpr int kRegsLaunchNeeded = (128 * kRegsLow + 256 * kRegsHigh + kThreads - 1) / kThreads;
 constexpr long long kWaitCycles = 4000000000ll;  // ~2 s at 2 GHz: a bounded wait gives up after this
 
+// Accumulator buffers in the 512 TMEM columns: each holds four regions of H
+// columns, so items with H <= 64 keep two (H <= 32: four) chunks in flight
+// and the MMAs of one chunk overlap the draining of the previous one.
+constexpr int kAccBufs = 4;
+__device__ __forceinline__ uint32_t acc_buffers(uint32_t H) {
+  const uint32_t n = 128u / H;
+  return n < (uint32_t)kAccBufs ? n : (uint32_t)kAccBufs;
+}
+
 __device__ __forceinline__ bool wait_bounded(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
                                              int* status) {
   const long long t0 = clock64();
@@ -420,9 +429,9 @@ __global__ void __launch_bounds__(kThreads, 1) ozaki_gemm_kernel(const __grid_co
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + (size_t)stages * 2 * half_bytes);
   uint64_t* full = bars;
   uint64_t* empty = bars + stages;
-  uint64_t* acc_full = bars + 2 * stages;
-  uint64_t* acc_empty = acc_full + 1;
-  uint64_t* drain = acc_full + 2;
+  uint64_t* acc_full = bars + 2 * stages;  // [kAccBufs]
+  uint64_t* acc_empty = acc_full + kAccBufs;  // [kAccBufs]
+  uint64_t* drain = acc_empty + kAccBufs;
   uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(drain + 1);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_holder + 1);
   float* sB = reinterpret_cast<float*>(tmem_holder + 4);  // [2][128] per-task column scales
@@ -435,8 +444,10 @@ __global__ void __launch_bounds__(kThreads, 1) ozaki_gemm_kernel(const __grid_co
       sm100::mbar_init(&full[s], 1);
       sm100::mbar_init(&empty[s], 1);
     }
-    sm100::mbar_init(acc_full, 1);
-    sm100::mbar_init(acc_empty, kEpiWarps);
+    for (int b = 0; b < kAccBufs; ++b) {
+      sm100::mbar_init(&acc_full[b], 1);
+      sm100::mbar_init(&acc_empty[b], kEpiWarps);
+    }
     sm100::mbar_init(drain, 1);
     *abort_flag = 0;
     sm100::fence_mbar_init();
@@ -498,7 +509,9 @@ __global__ void __launch_bounds__(kThreads, 1) ozaki_gemm_kernel(const __grid_co
     if (lane == 0) {
       const uint64_t desc_stage0 = sm100::desc_kmajor_sw32(sm100::smem_u32(smem));
       int stage = 0;
-      uint32_t phase = 0, acc_phase = 0;
+      uint32_t phase = 0;
+      // accumulator buffers: parity bit and "ever used" bit per buffer, the buffer of the next chunk
+      uint32_t acc_parity = 0, acc_used = 0, buf = 0, cur_H = 0;
       bool ok = true;
       for (int64_t i = blockIdx.x; i < p.n_items && ok; i += gridDim.x) {
         const int q = problem_of(p, i);
@@ -506,6 +519,16 @@ __global__ void __launch_bounds__(kThreads, 1) ozaki_gemm_kernel(const __grid_co
         const OzTask* tasks = p.problems[q].tasks;
         const OzGroup g = p.problems[q].groups[it.group];
         const uint32_t H = (uint32_t)g.n_tile;
+        const uint32_t nbuf = acc_buffers(H);
+        if (H != cur_H) {
+          // another buffer layout: every buffer still being drained must be free first
+          for (int b = 0; b < kAccBufs && ok; ++b)
+            if ((acc_used >> b) & 1u)
+              ok = wait_bounded(&acc_empty[b], ((acc_parity >> b) & 1u) ^ 1u, abort_flag, p.status);
+          if (!ok) break;
+          buf = 0;
+          cur_H = H;
+        }
         const int n_valid = min((int)H, g.N - it.nt * (int)H);
         const bool full_tile = n_valid == (int)H;
         // a ragged tile runs unfused with N rounded up to 16 columns
@@ -519,7 +542,10 @@ __global__ void __launch_bounds__(kThreads, 1) ozaki_gemm_kernel(const __grid_co
             const bool last = ++in_chunk == p.chunk_tiles || kt + 1 == k_tiles;
             if (last) in_chunk = 0;
             if (first) {
-              if (!wait_bounded(acc_empty, acc_phase ^ 1u, abort_flag, p.status)) { ok = false; break; }
+              if (!wait_bounded(&acc_empty[buf], ((acc_parity >> buf) & 1u) ^ 1u, abort_flag, p.status)) {
+                ok = false;
+                break;
+              }
               sm100::tc_fence_after();
             }
             if (!wait_bounded(&full[stage], phase, abort_flag, p.status)) { ok = false; break; }
@@ -528,12 +554,15 @@ __global__ void __launch_bounds__(kThreads, 1) ozaki_gemm_kernel(const __grid_co
             // operand offsets add straight onto the stage-0 descriptor
             const uint64_t a0 = desc_stage0 + (uint64_t)((uint32_t)stage * (2u * half_bytes >> 4));
             const uint64_t b0 = a0 + (half_bytes >> 4);
-            if (full_tile) issue_ops<S, true, 0>(tmem, a0, b0, H, idesc1, idesc2, first);
-            else issue_ops<S, false, 0>(tmem, a0, b0, H, idesc1, idesc2, first);
+            const uint32_t tacc = tmem + buf * 4u * H;
+            if (full_tile) issue_ops<S, true, 0>(tacc, a0, b0, H, idesc1, idesc2, first);
+            else issue_ops<S, false, 0>(tacc, a0, b0, H, idesc1, idesc2, first);
             sm100::mma_commit(&empty[stage]);
             if (last) {
-              sm100::mma_commit(acc_full);
-              acc_phase ^= 1u;
+              sm100::mma_commit(&acc_full[buf]);
+              acc_parity ^= 1u << buf;
+              acc_used |= 1u << buf;
+              buf = buf + 1 == nbuf ? 0u : buf + 1;
             }
             if (++stage == stages) {
               stage = 0;
@@ -558,7 +587,9 @@ __global__ void __launch_bounds__(kThreads, 1) ozaki_gemm_kernel(const __grid_co
     const int row = q * 32 + lane;
     const int c0 = 64 * h;
     const uint32_t trow = tmem + ((uint32_t)(q * 32) << 16);
-    uint32_t chunk = 0, task_count = 0;
+    uint32_t task_count = 0;
+    uint32_t acc_parity = 0, buf = 0;  // same buffer sequence as the MMA issuer
+    int cur_H = 0;
     bool ok = true;
     // Every epilogue warp passes the same named barriers on every path (also after a timeout).
     for (int64_t i = blockIdx.x; i < p.n_items; i += gridDim.x) {
@@ -570,6 +601,11 @@ __global__ void __launch_bounds__(kThreads, 1) ozaki_gemm_kernel(const __grid_co
       const OzGroup g = p.problems[q].groups[it.group];
       const int H = g.n_tile;
       const int n_valid = min(H, g.N - it.nt * H);
+      const uint32_t nbuf = acc_buffers((uint32_t)H);
+      if (H != cur_H) {
+        buf = 0;
+        cur_H = H;
+      }
       epi_barrier();  // the previous item's output writes (which read fref) are done
       int Eref = kOzExpZero;
       for (int t = g.task_begin; t < g.task_end; ++t)
@@ -595,21 +631,25 @@ __global__ void __launch_bounds__(kThreads, 1) ozaki_gemm_kernel(const __grid_co
         const int ea = a_exp[tk.a_exp + (int64_t)it.mt * kOzTileM + row];
         const float sA = (ea == kOzExpZero) ? 0.0f : pow2f(ea - Eref);
         const int n_chunks = ok ? (tk.k_tiles + p.chunk_tiles - 1) / p.chunk_tiles : 0;
-        for (int ck = 0; ck < n_chunks; ++ck, ++chunk) {
-          if (!wait_bounded(acc_full, chunk & 1u, abort_flag, p.status)) { ok = false; break; }
+        for (int ck = 0; ck < n_chunks; ++ck) {
+          if (!wait_bounded(&acc_full[buf], (acc_parity >> buf) & 1u, abort_flag, p.status)) {
+            ok = false;
+            break;
+          }
           sm100::tc_fence_after();
+          const uint32_t tb = trow + buf * 4u * (uint32_t)H;
 #pragma unroll
           for (int g8 = 0; g8 < 8; ++g8) {
             const int col = c0 + 8 * g8;
             if (col >= n_valid) break;  // columns past a ragged tile's width were not computed
             float r0[8], r1[8], r2[8], r3[8];
-            sm100::tmem_ld8(trow + 0 * H + col, r0);
-            sm100::tmem_ld8(trow + 1 * H + col, r1);
-            sm100::tmem_ld8(trow + 2 * H + col, r2);
+            sm100::tmem_ld8(tb + 0 * H + col, r0);
+            sm100::tmem_ld8(tb + 1 * H + col, r1);
+            sm100::tmem_ld8(tb + 2 * H + col, r2);
             // with S < 4 no product has k + l >= 5: region 3 is never written and holds stale
             // TMEM contents of an earlier kernel, so it must not be read
             if constexpr (S >= 4) {
-              sm100::tmem_ld8(trow + 3 * H + col, r3);
+              sm100::tmem_ld8(tb + 3 * H + col, r3);
             } else {
 #pragma unroll
               for (int j = 0; j < 8; ++j) r3[j] = 0.0f;
@@ -621,7 +661,9 @@ __global__ void __launch_bounds__(kThreads, 1) ozaki_gemm_kernel(const __grid_co
           }
           sm100::tc_fence_before();
           __syncwarp();
-          if (lane == 0) sm100::mbar_arrive(acc_empty);
+          if (lane == 0) sm100::mbar_arrive(&acc_empty[buf]);
+          acc_parity ^= 1u << buf;
+          buf = buf + 1 == nbuf ? 0u : buf + 1;
         }
       }
       if (g.task_begin == g.task_end) epi_barrier();  // keep the fref barrier count uniform

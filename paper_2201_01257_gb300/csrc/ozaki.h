@@ -145,14 +145,17 @@ __host__ __device__ constexpr OzSched oz_schedule(int S, bool fuse) {
 //   policy 1: 128, or rows rounded up to 16 when the block has fewer rows
 //             (same tiles, smaller images and copies for narrow blocks);
 //   policy 2: the fewest tiles of 128 at most, of equal width rounded up to
-//             16 (no ragged tile, so every tile runs the fused N = 2H MMAs).
+//             16 (no ragged tile, so every tile runs the fused N = 2H MMAs);
+//   policy 3: as 2 with tiles of 64 at most, so that two accumulator buffers
+//             fit in TMEM and the MMAs never wait for an accumulator drain.
 inline int oz_tile_rows(int64_t rows, int policy) {
   if (rows <= 0) return 128;
   const auto up16 = [](int64_t x) { return (int)std::max<int64_t>(16, (x + 15) / 16 * 16); };
   if (policy == 1) return rows >= 128 ? 128 : up16(rows);
-  if (policy == 2) {
-    const int64_t n = (rows + 127) / 128;
-    return std::min(128, up16((rows + n - 1) / n));
+  if (policy == 2 || policy == 3) {
+    const int64_t cap = policy == 2 ? 128 : 64;
+    const int64_t n = (rows + cap - 1) / cap;
+    return (int)std::min<int64_t>(cap, up16((rows + n - 1) / n));
   }
   return 128;
 }

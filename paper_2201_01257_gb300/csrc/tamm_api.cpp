@@ -209,7 +209,7 @@ extern "C" tamm_status tamm_ctx_set_option(tamm_ctx* ctx, int option, int64_t va
       return;
     }
     if (option == TAMM_OPT_OZAKI_TILE_POLICY) {
-      if (value < 0 || value > 2) throw Error(TAMM_EINVAL, "tile policy must be 0, 1 or 2");
+      if (value < 0 || value > 3) throw Error(TAMM_EINVAL, "tile policy must be 0..3");
       ctx->oz_tile_policy = (int)value;
       return;
     }

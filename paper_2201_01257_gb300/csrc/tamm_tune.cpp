@@ -41,7 +41,7 @@ namespace {
 
 constexpr double kSafety = 0.5;  // margin for other data of the same contraction
 constexpr int kChunks[] = {1280, 640, 320};
-constexpr int kPolicies[] = {0, 1, 2};  // tile policies (TAMM_OPT_OZAKI_TILE_POLICY)
+constexpr int kPolicies[] = {0, 1, 2, 3};  // tile policies (TAMM_OPT_OZAKI_TILE_POLICY)
 constexpr int kTimedRuns = 3;
 
 // A view of C's block structure on another buffer (same id: the same cached plans).

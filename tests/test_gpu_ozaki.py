@@ -185,13 +185,13 @@ def test_three_slices_after_six_slices(gpu_lib):
 
 @pytest.mark.parametrize("O_,V_,to,tv", [(8, 24, 2, 4), (16, 40, 8, 10), (40, 80, 20, 40)])
 def test_tile_policies_agree(gpu_lib, O_, V_, to, tv):
-    """Output columns per work item (three tile policies) and the GEMM grid (one CTA per work item, or
+    """Output columns per work item (four tile policies) and the GEMM grid (one CTA per work item, or
     one per SM walking the items): every combination gives bitwise the same values."""
     from paper_2201_01257_gb300 import workload as gw
 
     w = wl.small_doubles(O_, V_, to, tv)
     outs = []
-    for policy in (0, 1, 2):
+    for policy in (0, 1, 2, 3):
         for persistent in (0, 1):
             ctx = gpu_lib.Context(0)
             ctx.set_option(gpu_lib.TAMM_OPT_OZAKI_TILE_POLICY, policy)
