@@ -496,7 +496,8 @@ def run_config3_case(args) -> dict:
     from paper_2201_01257_gb300 import workload as gw
     from tamm_synth import workloads as wl
 
-    w = wl.config3()
+    O_, V_ = (int(x) for x in args.irrep.split(",")) if args.irrep else (64, 384)
+    w = wl.config3(O=O_, V=V_)
     stream = torch.cuda.Stream(0)
     ctx = tg.Context(0, stream=stream)
     with torch.cuda.stream(stream):
@@ -516,7 +517,7 @@ def run_config3_case(args) -> dict:
         ctx.sync()
         return a.elapsed_time(b) / k
 
-    out = {"case": "irrep_doubles_O64_V384: vvvv ladder + ring with P(ab)P(ij), D2h irreps, tiles U{8..96}",
+    out = {"case": f"{w.name}: vvvv ladder + ring with P(ab)P(ij), D2h irreps, tiles U{{8..96}}",
            "nonzero_block_flops": flops, "blocks": {k: T[k].n_blocks for k in ("V_vvvv", "T", "R")}}
     with torch.cuda.stream(stream):
         for policy in (0, 1, 2):
@@ -554,6 +555,7 @@ def main():
     ap.add_argument("--slices", type=int, default=0,
                     help="split-precision slices per operand; 0 = autotune every contraction for 1e-10")
     ap.add_argument("--config3", action="store_true", help="time the uneven-irrep grouped ladder + ring instead")
+    ap.add_argument("--irrep", default="", help="O,V: with --config3, spin-orbital counts (default 64,384)")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -477,8 +477,11 @@ __global__ void __launch_bounds__(kThreads, 1) ozaki_gemm_kernel(const __grid_co
         const uint8_t* b_tiles = p.problems[q].b_tiles;
         const OzGroup g = p.problems[q].groups[it.group];
         const uint32_t b_bytes = (uint32_t)S * 32u * (uint32_t)g.n_tile;
+        OzTask tk_next{};
+        if (g.task_begin < g.task_end) tk_next = tasks[g.task_begin];
         for (int t = g.task_begin; t < g.task_end && !*abort_flag; ++t) {
-          const OzTask tk = tasks[t];
+          const OzTask tk = tk_next;
+          if (t + 1 < g.task_end) tk_next = tasks[t + 1];  // loaded while this task's copies issue
           const uint8_t* a = a_tiles + tk.a_off + (size_t)((int64_t)it.mt * tk.k_tiles) * half_bytes;
           const uint8_t* b = b_tiles + tk.b_off + (size_t)((int64_t)it.nt * tk.k_tiles) * b_bytes;
           for (int kt = 0; kt < tk.k_tiles; ++kt) {
@@ -534,8 +537,10 @@ __global__ void __launch_bounds__(kThreads, 1) ozaki_gemm_kernel(const __grid_co
         // a ragged tile runs unfused with N rounded up to 16 columns
         const uint32_t idesc1 = sm100::idesc_bf16_f32(128, full_tile ? H : (uint32_t)((n_valid + 15) & ~15));
         const uint32_t idesc2 = sm100::idesc_bf16_f32(128, 2u * H);
+        int kt_next = g.task_begin < g.task_end ? tasks[g.task_begin].k_tiles : 0;
         for (int t = g.task_begin; t < g.task_end && ok; ++t) {
-          const int k_tiles = tasks[t].k_tiles;
+          const int k_tiles = kt_next;
+          if (t + 1 < g.task_end) kt_next = tasks[t + 1].k_tiles;  // loaded while this task issues
           int in_chunk = 0;  // position inside the current chunk (no division on the issue path)
           for (int kt = 0; kt < k_tiles; ++kt) {
             const bool first = in_chunk == 0;
@@ -606,31 +611,58 @@ __global__ void __launch_bounds__(kThreads, 1) ozaki_gemm_kernel(const __grid_co
         buf = 0;
         cur_H = H;
       }
-      epi_barrier();  // the previous item's output writes (which read fref) are done
-      int Eref = kOzExpZero;
-      for (int t = g.task_begin; t < g.task_end; ++t)
-        Eref = max(Eref, a_exp[tasks[t].a_exp + (int64_t)it.mt * kOzTileM + row]);
-      if (etid < H) {
-        int F = kOzExpZero;
-        for (int t = g.task_begin; t < g.task_end; ++t)
-          F = max(F, b_exp[tasks[t].b_exp + (int64_t)it.nt * H + etid]);
-        fref[etid] = F;
+      const int64_t arow = (int64_t)it.mt * kOzTileM + row, bcol = (int64_t)it.nt * H + etid;
+      const bool has_col = etid < H;
+      // reference exponents: the maxima over the group's tasks (loads unrolled so that several
+      // are in flight at once)
+      int Eref = kOzExpZero, F = kOzExpZero;
+      {
+        int t = g.task_begin;
+        for (; t + 4 <= g.task_end; t += 4) {
+          int ea4[4], eb4[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            ea4[u] = a_exp[tasks[t + u].a_exp + arow];
+            eb4[u] = has_col ? b_exp[tasks[t + u].b_exp + bcol] : kOzExpZero;
+          }
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            Eref = max(Eref, ea4[u]);
+            F = max(F, eb4[u]);
+          }
+        }
+        for (; t < g.task_end; ++t) {
+          Eref = max(Eref, a_exp[tasks[t].a_exp + arow]);
+          if (has_col) F = max(F, b_exp[tasks[t].b_exp + bcol]);
+        }
       }
+      epi_barrier();  // the previous item's output writes (which read fref) are done
+      if (has_col) fref[etid] = F;
       float hi[64], lo[64];
 #pragma unroll
       for (int j = 0; j < 64; ++j) hi[j] = lo[j] = 0.0f;
+      // exponents of the next task are loaded one task ahead, while this task's chunks drain
+      int ea_next = kOzExpZero, eb_next = kOzExpZero, kt_next = 0;
+      if (g.task_begin < g.task_end) {
+        const OzTask t0 = tasks[g.task_begin];
+        ea_next = a_exp[t0.a_exp + arow];
+        if (has_col) eb_next = b_exp[t0.b_exp + bcol];
+        kt_next = t0.k_tiles;
+      }
       for (int t = g.task_begin; t < g.task_end; ++t, ++task_count) {
-        const OzTask tk = tasks[t];
+        const int ea = ea_next, eb = eb_next, k_tiles = kt_next;
+        if (t + 1 < g.task_end) {
+          const OzTask tn = tasks[t + 1];
+          ea_next = a_exp[tn.a_exp + arow];
+          if (has_col) eb_next = b_exp[tn.b_exp + bcol];
+          kt_next = tn.k_tiles;
+        }
         float* sbuf = sB + (task_count & 1u) * 128;
         epi_barrier();  // fref is set, and sbuf's previous readers (two tasks ago) are done
-        if (etid < H) {
-          const int eb = b_exp[tk.b_exp + (int64_t)it.nt * H + etid];
-          sbuf[etid] = (eb == kOzExpZero) ? 0.0f : pow2f(eb - fref[etid]);
-        }
+        if (has_col) sbuf[etid] = (eb == kOzExpZero) ? 0.0f : pow2f(eb - fref[etid]);
         epi_barrier();
-        const int ea = a_exp[tk.a_exp + (int64_t)it.mt * kOzTileM + row];
         const float sA = (ea == kOzExpZero) ? 0.0f : pow2f(ea - Eref);
-        const int n_chunks = ok ? (tk.k_tiles + p.chunk_tiles - 1) / p.chunk_tiles : 0;
+        const int n_chunks = ok ? (k_tiles + p.chunk_tiles - 1) / p.chunk_tiles : 0;
         for (int ck = 0; ck < n_chunks; ++ck) {
           if (!wait_bounded(&acc_full[buf], (acc_parity >> buf) & 1u, abort_flag, p.status)) {
             ok = false;
@@ -945,6 +977,7 @@ struct OzakiPlan : Plan {
     std::vector<OzGroup> groups;
     std::vector<OzTask> tasks;
     std::vector<OzItem> items;
+    std::vector<int64_t> group_k;  // summed extent per group
     for (const auto& g : lay.groups) {
       OzGroup gg;
       gg.c_off = O.off[(size_t)g.out_block];
@@ -969,6 +1002,17 @@ struct OzakiPlan : Plan {
       gg.task_end = (int32_t)tasks.size();
       const int32_t gi = (int32_t)groups.size();
       groups.push_back(gg);
+      group_k.push_back(Ksum);
+      (void)gi;
+    }
+    // work items, the groups with the longest summed range first (the grid then ends on short
+    // items); inside a group, the items sharing an A row tile are adjacent (L2 reuse)
+    std::vector<int32_t> order(groups.size());
+    for (size_t i = 0; i < order.size(); ++i) order[i] = (int32_t)i;
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int32_t x, int32_t y) { return group_k[(size_t)x] > group_k[(size_t)y]; });
+    for (int32_t gi : order) {
+      const OzGroup& gg = groups[(size_t)gi];
       const int32_t mts = (gg.M + kOzTileM - 1) / kOzTileM, nts = (gg.N + gg.n_tile - 1) / gg.n_tile;
       for (int32_t mt = 0; mt < mts; ++mt)
         for (int32_t nt = 0; nt < nts; ++nt) items.push_back({0, gi, mt, nt});

@@ -216,16 +216,16 @@ def irrep_space(name: str, n_spin_orbitals: int, rng, tile_lo: int = 8, tile_hi:
     return SpaceSpec(name, tuple(groups), tile=0, tile_sizes=tuple(tiles))
 
 
-def config3(seed_k: int = 3) -> Workload:
-    """Uneven D2h blocks: O=64, V=384 spin-orbitals, irrep counts and tile cuts seeded; the vvvv
-    ladder and the ring term (spin and irrep block sparsity)."""
+def config3(seed_k: int = 3, O: int = 64, V: int = 384) -> Workload:
+    """Uneven D2h blocks: O=64, V=384 spin-orbitals (other sizes for small cases), irrep counts and
+    tile cuts seeded; the vvvv ladder and the ring term (spin and irrep block sparsity)."""
     import numpy as np
 
     seed = SEED_BASE + seed_k
     rng = np.random.default_rng(seed)
-    occ = irrep_space("occ", 64, rng)
-    virt = irrep_space("virt", 384, rng)
-    w = Workload("irrep_doubles_O64_V384", seed, {"occ": occ, "virt": virt}, {})
+    occ = irrep_space("occ", O, rng)
+    virt = irrep_space("virt", V, rng)
+    w = Workload(f"irrep_doubles_O{O}_V{V}", seed, {"occ": occ, "virt": virt}, {})
     si = "spin_irrep"
     w.tensors = {
         "V_vvvv": TensorSpec("V_vvvv", ("virt",) * 4, 2, si, sigma=0.1, stream=1, anti01=True, anti23=True),
