@@ -112,6 +112,10 @@ TAMM_API const char* tamm_last_error(const tamm_ctx* ctx);
                                         128 columns, of equal width rounded up to 16 (N = 400 -> 4 x 112);
                                         3 = as 2 with at most 64 columns (N = 400 -> 7 x 64).  Tiles of at
                                         most 64 (32) columns keep two (four) accumulators in flight */
+#define TAMM_OPT_OZAKI_PANELS 3 /* split precision: 1 (default) = output blocks that have the same rows and
+                                   the same A block in every summed-tile pair run as one column panel
+                                   (their B blocks stacked into one image: wider N, A tiles read once);
+                                   0 = every output block alone */
 /* Set option `option` to `value`.  Errors: TAMM_EINVAL (unknown option or value out of range). */
 TAMM_API tamm_status tamm_ctx_set_option(tamm_ctx* ctx, int option, int64_t value);
 

@@ -3,6 +3,7 @@
 // described in ozaki.h.
 #include <algorithm>
 #include <cstring>
+#include <map>
 
 #include "ozaki.h"
 #include "sm100.cuh"
@@ -222,9 +223,10 @@ __global__ void __launch_bounds__(256) ozaki_slice_kernel(const double* __restri
     int e = kOzExpZero;
     if (m != 0ull) (void)frexp(__longlong_as_double((long long)m), &e);
     if (kFloat && m != 0ull) e = 6;  // floating pieces: unit scale
-    if (lane == 0) exps[B.exp_off + grow] = e;
-    const int32_t rr = grow % H;
-    uint8_t* rbase = tiles + B.tile_off + (size_t)(grow / H) * B.k_tiles * tile_bytes + rr * 32;
+    const int32_t vrow = B.dst_row0 + grow;  // row of the (possibly concatenated) sliced image
+    if (lane == 0) exps[B.exp_off + vrow] = e;
+    const int32_t rr = vrow % H;
+    uint8_t* rbase = tiles + B.tile_off + (size_t)(vrow / H) * B.k_tiles * tile_bytes + rr * 32;
     const int swz_row = (rr >> 2) & 1;
     const int npairs = B.k_tiles * 8;  // 32-bit words (element pairs) per row of the padded K range
     for (int pw = lane; pw < npairs; pw += 32) {
@@ -277,7 +279,7 @@ __global__ void __launch_bounds__(256) ozaki_slice_kernel(const double* __restri
     if (rmax[r] != 0ull) (void)frexp(__longlong_as_double((long long)rmax[r]), &e);
     if (kFloat && rmax[r] != 0ull) e = 6;
     rexp[r] = e;
-    exps[B.exp_off + it.r0 + r] = e;
+    exps[B.exp_off + B.dst_row0 + it.r0 + r] = e;
   }
   __syncthreads();
   const int nch2 = B.k_tiles * 2;
@@ -304,9 +306,9 @@ __global__ void __launch_bounds__(256) ozaki_slice_kernel(const double* __restri
         for (int q = 0; q < S; ++q) packed[q][j >> 1] = wd[q];
       }
     }
-    const int32_t grow = it.r0 + r;
-    const int32_t rr = grow % H;
-    const int64_t tile = (int64_t)(grow / H) * B.k_tiles + ch / 2;
+    const int32_t vrow = B.dst_row0 + it.r0 + r;
+    const int32_t rr = vrow % H;
+    const int64_t tile = (int64_t)(vrow / H) * B.k_tiles + ch / 2;
     const int swz = (ch & 1) ^ ((rr >> 2) & 1);
     uint8_t* base = tiles + B.tile_off + (size_t)tile * tile_bytes + rr * 32 + swz * 16;
 #pragma unroll
@@ -436,6 +438,8 @@ __global__ void __launch_bounds__(kThreads, 1) ozaki_gemm_kernel(const __grid_co
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_holder + 1);
   float* sB = reinterpret_cast<float*>(tmem_holder + 4);  // [2][128] per-task column scales
   int* fref = reinterpret_cast<int*>(sB + 256);            // [128] reference column exponents
+  int64_t* col_base = reinterpret_cast<int64_t*>(fref + 128);        // [128] column map of a panel item
+  int32_t* col_stride = reinterpret_cast<int32_t*>(col_base + 128);  // [128]
 
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
 
@@ -636,8 +640,12 @@ __global__ void __launch_bounds__(kThreads, 1) ozaki_gemm_kernel(const __grid_co
           if (has_col) F = max(F, b_exp[tasks[t].b_exp + bcol]);
         }
       }
-      epi_barrier();  // the previous item's output writes (which read fref) are done
+      epi_barrier();  // the previous item's output writes (which read fref and the column map) are done
       if (has_col) fref[etid] = F;
+      if (g.colmap >= 0 && has_col && bcol < g.N) {
+        col_base[etid] = p.problems[q].col_base[g.colmap + bcol];
+        col_stride[etid] = p.problems[q].col_stride[g.colmap + bcol];
+      }
       float hi[64], lo[64];
 #pragma unroll
       for (int j = 0; j < 64; ++j) hi[j] = lo[j] = 0.0f;
@@ -702,8 +710,12 @@ __global__ void __launch_bounds__(kThreads, 1) ozaki_gemm_kernel(const __grid_co
       if (ok) {
         const int grow = it.mt * kOzTileM + row;
         if (grow < g.M) {
-          double* crow = p.problems[q].c + g.c_off + (int64_t)grow * g.N + (int64_t)it.nt * H;
+          // one output block: row-major M x N at c_off; a column panel: column c of block m at
+          // col_base[c] + row * col_stride[c]
+          double* c = p.problems[q].c;
+          double* crow = c + g.c_off + (int64_t)grow * g.N + (int64_t)it.nt * H;
           const double alpha = p.problems[q].alpha, beta = p.problems[q].beta;
+          const bool panel = g.colmap >= 0;
 #pragma unroll
           for (int j = 0; j < 64; ++j) {
             const int col = c0 + j;
@@ -711,7 +723,7 @@ __global__ void __launch_bounds__(kThreads, 1) ozaki_gemm_kernel(const __grid_co
               double v = 0.0;
               if (Eref != kOzExpZero && fref[col] != kOzExpZero)
                 v = ((double)hi[j] + (double)lo[j]) * pow2d(Eref + fref[col] - 12);
-              double* cp = crow + col;
+              double* cp = panel ? c + col_base[col] + (int64_t)grow * col_stride[col] : crow + col;
               *cp = beta != 0.0 ? fma(beta, *cp, alpha * v) : alpha * v;
             }
           }
@@ -849,85 +861,80 @@ struct OzakiPlan : Plan {
   OzGroup* d_groups = nullptr;
   OzTask* d_tasks = nullptr;
   OzItem* d_items = nullptr;
+  int64_t* d_col_base = nullptr;
+  int32_t* d_col_stride = nullptr;
   int64_t n_items = 0;
   std::unique_ptr<AddPlan> perm_out;
   size_t off_ta = 0, off_tb = 0, off_ea = 0, off_eb = 0, off_x = 0, scratch_bytes = 0;
   int warps_a = 8, kbuf_a = 2, warps_b = 8, kbuf_b = 2;  // slicing launch shapes
 
-  // Slice records for the GEMM-order operand `gemm` (blocks of `native`
+  // Geometry of block b of the GEMM-order operand `gemm` (blocks of `native`
   // permuted by perm); row modes are [r0, r0+nr), summed modes [k0, k0+nk).
-  // tile_policy < 0: 128-row tiles (A operands); else oz_tile_rows(rows, tile_policy) (B operands).
-  // `bytes` accumulates the sliced image size of S slices, `exps` the exponent count; `warps` and
-  // `kbuf` are the slicing launch's warps per CTA and doubles per warp row buffer.
-  static void slice_blocks(const tamm_tensor& native, const tamm_tensor& gemm, const std::vector<int>& perm,
-                           int r0, int nr, int k0, int nk, int S, int tile_policy, std::vector<SliceBlock>& out,
-                           std::vector<SliceItem>& items, int64_t& bytes, int64_t& exps, int& warps, int& kbuf) {
-    out.resize((size_t)gemm.n_blocks);
-    for (int64_t b = 0; b < gemm.n_blocks; ++b) {
-      const int64_t* gt = &gemm.tiles[(size_t)(b * gemm.nm)];
-      int64_t nt[kMaxModes];
-      for (int m = 0; m < gemm.nm; ++m) nt[perm[m]] = gt[m];
-      const int64_t nb = native.find(nt);
-      if (nb < 0) throw Error(TAMM_EINVAL, "ozaki: operand block lookup failed");
-      int64_t stride[kMaxModes], s = 1;
-      for (int q = native.nm - 1; q >= 0; --q) {
-        stride[q] = s;
-        s *= native.sp[q]->size[(size_t)nt[q]];
-      }
-      SliceBlock& B = out[(size_t)b];
-      memset(&B, 0, sizeof(B));
-      B.src_off = native.off[(size_t)nb];
-      if (nr > 4 || nk > 4) throw Error(TAMM_EUNSUPPORTED, "ozaki: at most 4 free and 4 summed modes per operand");
-      B.nr = nr;
-      B.nk = nk;
-      int64_t rows = 1, K = 1;
-      for (int m = 0; m < nr; ++m) {
-        B.rdim[m] = (int32_t)gemm.sp[r0 + m]->size[(size_t)gt[r0 + m]];
-        B.rstride[m] = (int32_t)stride[perm[r0 + m]];
-        rows *= B.rdim[m];
-      }
-      for (int m = 0; m < nk; ++m) {
-        B.kdim[m] = (int32_t)gemm.sp[k0 + m]->size[(size_t)gt[k0 + m]];
-        B.kstride[m] = (int32_t)stride[perm[k0 + m]];
-        K *= B.kdim[m];
-      }
-      if (rows > (1 << 30) || K > (1 << 30)) throw Error(TAMM_EUNSUPPORTED, "ozaki: block too large");
-      B.rows = (int32_t)rows;
-      B.K = (int32_t)K;
-      const int H = tile_policy < 0 ? kOzTileM : oz_tile_rows(rows, tile_policy);
-      B.tile_rows = H;
-      B.row_tiles = (int32_t)((rows + H - 1) / H);
-      B.k_tiles = (int32_t)((K + kOzTileK - 1) / kOzTileK);
-      B.k_contig = (nk > 0 && B.kstride[nk - 1] == 1) ? 1 : 0;
-      if (nk == 0) B.k_contig = 1;
-      {
-        int64_t st = 1;
-        B.k_dense = 1;
-        for (int m = nk - 1; m >= 0; --m) {
-          if (B.kstride[m] != st) B.k_dense = 0;
-          st *= B.kdim[m];
-        }
-      }
-      B.tile_off = bytes;
-      B.exp_off = exps;
-      bytes += (int64_t)B.row_tiles * B.k_tiles * S * H * 32;
-      exps += (int64_t)B.row_tiles * H;
+  // The image layout fields (tile_rows, row_tiles, tile_off, exp_off,
+  // dst_row0) are filled by the caller.
+  static SliceBlock block_geometry(const tamm_tensor& native, const tamm_tensor& gemm, const std::vector<int>& perm,
+                                   int r0, int nr, int k0, int nk, int64_t b) {
+    const int64_t* gt = &gemm.tiles[(size_t)(b * gemm.nm)];
+    int64_t nt[kMaxModes];
+    for (int m = 0; m < gemm.nm; ++m) nt[perm[m]] = gt[m];
+    const int64_t nb = native.find(nt);
+    if (nb < 0) throw Error(TAMM_EINVAL, "ozaki: operand block lookup failed");
+    int64_t stride[kMaxModes], s = 1;
+    for (int q = native.nm - 1; q >= 0; --q) {
+      stride[q] = s;
+      s *= native.sp[q]->size[(size_t)nt[q]];
     }
-    // warp row buffers: K + 2 doubles (room for the aligned-down start), for the longest dense row;
-    // as many warps (<= 8) as fit the shared-memory budget.  Rows too long for one warp buffer go
-    // through the general path.
+    SliceBlock B;
+    memset(&B, 0, sizeof(B));
+    B.src_off = native.off[(size_t)nb];
+    if (nr > 4 || nk > 4) throw Error(TAMM_EUNSUPPORTED, "ozaki: at most 4 free and 4 summed modes per operand");
+    B.nr = nr;
+    B.nk = nk;
+    int64_t rows = 1, K = 1;
+    for (int m = 0; m < nr; ++m) {
+      B.rdim[m] = (int32_t)gemm.sp[r0 + m]->size[(size_t)gt[r0 + m]];
+      B.rstride[m] = (int32_t)stride[perm[r0 + m]];
+      rows *= B.rdim[m];
+    }
+    for (int m = 0; m < nk; ++m) {
+      B.kdim[m] = (int32_t)gemm.sp[k0 + m]->size[(size_t)gt[k0 + m]];
+      B.kstride[m] = (int32_t)stride[perm[k0 + m]];
+      K *= B.kdim[m];
+    }
+    if (rows > (1 << 30) || K > (1 << 30)) throw Error(TAMM_EUNSUPPORTED, "ozaki: block too large");
+    B.rows = (int32_t)rows;
+    B.K = (int32_t)K;
+    B.k_tiles = (int32_t)((K + kOzTileK - 1) / kOzTileK);
+    B.k_contig = (nk > 0 && B.kstride[nk - 1] == 1) ? 1 : 0;
+    if (nk == 0) B.k_contig = 1;
+    int64_t st = 1;
+    B.k_dense = 1;
+    for (int m = nk - 1; m >= 0; --m) {
+      if (B.kstride[m] != st) B.k_dense = 0;
+      st *= B.kdim[m];
+    }
+    return B;
+  }
+
+  // Slicing launch shape and items for an operand's records; record i covers
+  // image rows [dst_row0, dst_row0 + extent[i]) (rows past its own are zero).
+  // Warp row buffers hold K + 2 doubles (room for the aligned-down start) of
+  // the longest dense row; as many warps (<= 8) as fit the shared-memory
+  // budget.  Rows too long for one warp buffer go through the general path.
+  static void slicing_items(std::vector<SliceBlock>& recs, const std::vector<int32_t>& extent,
+                            std::vector<SliceItem>& items, int& warps, int& kbuf) {
     int64_t kmax = 0;
-    for (const SliceBlock& B : out)
+    for (const SliceBlock& B : recs)
       if (B.k_dense) kmax = std::max<int64_t>(kmax, B.K);
     kbuf = (int)((kmax + 2 + 1) & ~int64_t(1));
     warps = (int)std::min<int64_t>(8, (int64_t)kOzSliceSmemBudget / ((int64_t)kbuf * 8));
     if (warps < 1) {
-      for (SliceBlock& B : out) B.k_dense = 0;
+      for (SliceBlock& B : recs) B.k_dense = 0;
       warps = 8;
       kbuf = 2;
     }
-    for (int64_t b = 0; b < gemm.n_blocks; ++b) {
-      const SliceBlock& B = out[(size_t)b];
+    for (size_t i = 0; i < recs.size(); ++i) {
+      const SliceBlock& B = recs[i];
       // rows per slicing CTA: one per warp for a dense summed range, else enough rows for every
       // thread to have work, at least 32 for coalescing along rows
       int R;
@@ -937,13 +944,13 @@ struct OzakiPlan : Plan {
         R = 32;
         while (R < kOzSliceMaxRows && (int64_t)R * ((B.K + 7) / 8) < 32 * warps * 4) R *= 2;
       }
-      const int32_t padded = B.row_tiles * B.tile_rows;
-      for (int32_t r = 0; r < padded; r += R) items.push_back({(int32_t)b, r, std::min<int32_t>(R, padded - r), 0});
+      for (int32_t r = 0; r < extent[i]; r += R)
+        items.push_back({(int32_t)i, r, std::min<int32_t>(R, extent[i] - r), 0});
     }
   }
 
   OzakiPlan(tamm_ctx* c, const tamm_tensor* C, const char* lc, const tamm_tensor* A, const char* la,
-            const tamm_tensor* B, const char* lb, int slices, int tile_policy)
+            const tamm_tensor* B, const char* lb, int slices, int tile_policy, bool panels)
       : Plan(c), lay(c, C, lc, A, la, B, lb), S(slices) {
     const int nfl = (int)lay.free_left.size(), nfr = (int)lay.free_right.size(), nk = (int)lay.summed.size();
     auto perm_of = [](const std::string& need, const std::string& have) {
@@ -951,13 +958,141 @@ struct OzakiPlan : Plan {
       for (size_t m = 0; m < need.size(); ++m) p[m] = (int)have.find(need[m]);
       return p;
     };
-    std::vector<SliceBlock> sa, sb;
+    const tamm_tensor& Lg = lay.left_gemm();
+    const tamm_tensor& Rg = lay.right_gemm();
+    const std::vector<int> perm_l = perm_of(lay.need_left, lay.label_left);
+    const std::vector<int> perm_r = perm_of(lay.need_right, lay.label_right);
+
+    // A operand: one image per block, 128-row tiles
+    std::vector<SliceBlock> sa;
+    std::vector<int32_t> ext_a;
+    int64_t ta = 0, ea = 0;
+    for (int64_t b = 0; b < Lg.n_blocks; ++b) {
+      SliceBlock R = block_geometry(*lay.left, Lg, perm_l, 0, nfl, nfl, nk, b);
+      R.tile_rows = kOzTileM;
+      R.row_tiles = (R.rows + kOzTileM - 1) / kOzTileM;
+      R.tile_off = ta;
+      R.exp_off = ea;
+      R.dst_row0 = 0;
+      ta += (int64_t)R.row_tiles * R.k_tiles * S * kOzTileM * 32;
+      ea += (int64_t)R.row_tiles * kOzTileM;
+      sa.push_back(R);
+      ext_a.push_back(R.row_tiles * kOzTileM);
+    }
+
+    // Column panels: output blocks with the same rows and the same A block in every task (the
+    // same summed tiles) share every A tile, so their columns are concatenated into one wider
+    // output; each task's B blocks become one image with the members' rows stacked.
+    std::vector<std::vector<int>> members;
+    {
+      std::map<std::vector<int64_t>, int> panel_of;
+      for (size_t gi = 0; gi < lay.groups.size(); ++gi) {
+        const auto& g = lay.groups[gi];
+        std::vector<int64_t> key{g.M};
+        for (int64_t t = g.task_begin; t < g.task_end; ++t) key.push_back(lay.tasks[(size_t)t].left_block);
+        if (!panels) key.push_back(-1 - (int64_t)gi);  // every group alone
+        auto it = panel_of.find(key);
+        if (it == panel_of.end()) {
+          panel_of[key] = (int)members.size();
+          members.push_back({(int)gi});
+        } else {
+          members[(size_t)it->second].push_back((int)gi);
+        }
+      }
+    }
+    // B images: one per distinct (task, member B blocks) list
+    std::vector<SliceBlock> sb;
+    std::vector<int32_t> ext_b;
+    struct Image {
+      int64_t tile_off, exp_off;
+      int32_t k_tiles;
+    };
+    std::vector<Image> images;
+    std::map<std::vector<int64_t>, int> image_of;
+    int64_t tb = 0, eb = 0;
+    const tamm_tensor& O = lay.out_gemm_tensor();
+    std::vector<OzGroup> groups;
+    std::vector<OzTask> tasks;
+    std::vector<int64_t> col_base;
+    std::vector<int32_t> col_stride;
+    std::vector<int64_t> group_k;  // summed extent per output group
+    for (const auto& mem : members) {
+      const auto& g0 = lay.groups[(size_t)mem[0]];
+      int64_t Np = 0;
+      for (int gi : mem) Np += lay.groups[(size_t)gi].N;
+      if (Np > (int64_t(1) << 30)) throw Error(TAMM_EUNSUPPORTED, "ozaki: output panel too wide");
+      const int H = oz_tile_rows(Np, tile_policy);
+      const int32_t row_tiles = (int32_t)((Np + H - 1) / H);
+      OzGroup gg;
+      gg.M = (int32_t)g0.M;
+      gg.N = (int32_t)Np;
+      gg.n_tile = H;
+      gg.pad = 0;
+      if (mem.size() == 1) {
+        gg.c_off = O.off[(size_t)g0.out_block];
+        gg.colmap = -1;
+      } else {
+        gg.c_off = 0;
+        gg.colmap = (int64_t)col_base.size();
+        for (int gi : mem) {
+          const auto& g = lay.groups[(size_t)gi];
+          for (int64_t cc = 0; cc < g.N; ++cc) {
+            col_base.push_back(O.off[(size_t)g.out_block] + cc);
+            col_stride.push_back((int32_t)g.N);
+          }
+        }
+      }
+      gg.task_begin = (int32_t)tasks.size();
+      const int64_t ntask = g0.task_end - g0.task_begin;
+      int64_t Ksum = 0;
+      for (int64_t t = 0; t < ntask; ++t) {
+        const auto& tk0 = lay.tasks[(size_t)(g0.task_begin + t)];
+        std::vector<int64_t> key{(int64_t)H};
+        for (int gi : mem) key.push_back(lay.tasks[(size_t)(lay.groups[(size_t)gi].task_begin + t)].right_block);
+        auto it = image_of.find(key);
+        int img;
+        if (it != image_of.end()) {
+          img = it->second;
+        } else {
+          img = (int)images.size();
+          image_of[key] = img;
+          Image im{tb, eb, 0};
+          int32_t row0 = 0;
+          for (size_t m = 0; m < mem.size(); ++m) {
+            SliceBlock R = block_geometry(*lay.right, Rg, perm_r, nk, nfr, 0, nk, key[m + 1]);
+            if (m == 0) im.k_tiles = R.k_tiles;
+            if (R.k_tiles != im.k_tiles) throw Error(TAMM_EINVAL, "ozaki: K mismatch in a panel");
+            R.tile_rows = H;
+            R.row_tiles = row_tiles;
+            R.tile_off = im.tile_off;
+            R.exp_off = im.exp_off;
+            R.dst_row0 = row0;
+            const bool last = m + 1 == mem.size();
+            ext_b.push_back(last ? row_tiles * H - row0 : R.rows);
+            row0 += R.rows;
+            sb.push_back(R);
+          }
+          if (row0 != Np) throw Error(TAMM_EINVAL, "ozaki: B block rows differ from the output columns");
+          tb += (int64_t)row_tiles * im.k_tiles * S * H * 32;
+          eb += (int64_t)row_tiles * H;
+          images.push_back(im);
+        }
+        const SliceBlock& A_ = sa[(size_t)tk0.left_block];
+        const Image& im = images[(size_t)img];
+        if (A_.k_tiles != im.k_tiles) throw Error(TAMM_EINVAL, "ozaki: K mismatch");
+        tasks.push_back({A_.tile_off, im.tile_off, A_.exp_off, im.exp_off, A_.k_tiles, 0});
+        Ksum += (int64_t)A_.k_tiles * kOzTileK;
+      }
+      // the double-float accumulator holds sums of |G0| <= Ksum * 64 * 64 far below 2^40
+      if (Ksum > (int64_t(1) << 26)) throw Error(TAMM_EUNSUPPORTED, "ozaki: summed extent too large");
+      gg.task_end = (int32_t)tasks.size();
+      groups.push_back(gg);
+      group_k.push_back(Ksum);
+    }
     std::vector<SliceItem> ia, ib;
-    int64_t ta = 0, tb = 0, ea = 0, eb = 0;
-    slice_blocks(*lay.left, lay.left_gemm(), perm_of(lay.need_left, lay.label_left), 0, nfl, nfl, nk, S, -1, sa,
-                 ia, ta, ea, warps_a, kbuf_a);
-    slice_blocks(*lay.right, lay.right_gemm(), perm_of(lay.need_right, lay.label_right), nk, nfr, 0, nk, S,
-                 tile_policy, sb, ib, tb, eb, warps_b, kbuf_b);
+    slicing_items(sa, ext_a, ia, warps_a, kbuf_a);
+    slicing_items(sb, ext_b, ib, warps_b, kbuf_b);
+
     auto align = [](size_t x) { return (x + 1023) & ~size_t(1023); };
     off_ta = 0;
     scratch_bytes = align((size_t)ta);
@@ -973,40 +1108,9 @@ struct OzakiPlan : Plan {
       off_x = scratch_bytes;
       scratch_bytes += align((size_t)lay.out_perm->n_elems * 8);
     }
-    const tamm_tensor& O = lay.out_gemm_tensor();
-    std::vector<OzGroup> groups;
-    std::vector<OzTask> tasks;
-    std::vector<OzItem> items;
-    std::vector<int64_t> group_k;  // summed extent per group
-    for (const auto& g : lay.groups) {
-      OzGroup gg;
-      gg.c_off = O.off[(size_t)g.out_block];
-      gg.M = (int32_t)g.M;
-      gg.N = (int32_t)g.N;
-      gg.n_tile = oz_tile_rows(g.N, tile_policy);
-      gg.pad = 0;
-      gg.task_begin = (int32_t)tasks.size();
-      int64_t Ksum = 0;
-      for (int64_t t = g.task_begin; t < g.task_end; ++t) {
-        const auto& tk = lay.tasks[(size_t)t];
-        const SliceBlock& A_ = sa[(size_t)tk.left_block];
-        const SliceBlock& B_ = sb[(size_t)tk.right_block];
-        if (A_.k_tiles != B_.k_tiles) throw Error(TAMM_EINVAL, "ozaki: K mismatch");
-        if (B_.rows != gg.N || B_.tile_rows != gg.n_tile)
-          throw Error(TAMM_EINVAL, "ozaki: B block rows differ from the output columns");
-        tasks.push_back({A_.tile_off, B_.tile_off, A_.exp_off, B_.exp_off, A_.k_tiles, 0});
-        Ksum += (int64_t)A_.k_tiles * kOzTileK;
-      }
-      // the double-float accumulator holds sums of |G0| <= Ksum * 64 * 64 far below 2^40
-      if (Ksum > (int64_t(1) << 26)) throw Error(TAMM_EUNSUPPORTED, "ozaki: summed extent too large");
-      gg.task_end = (int32_t)tasks.size();
-      const int32_t gi = (int32_t)groups.size();
-      groups.push_back(gg);
-      group_k.push_back(Ksum);
-      (void)gi;
-    }
     // work items, the groups with the longest summed range first (the grid then ends on short
     // items); inside a group, the items sharing an A row tile are adjacent (L2 reuse)
+    std::vector<OzItem> items;
     std::vector<int32_t> order(groups.size());
     for (size_t i = 0; i < order.size(); ++i) order[i] = (int32_t)i;
     std::stable_sort(order.begin(), order.end(),
@@ -1027,6 +1131,10 @@ struct OzakiPlan : Plan {
     d_groups = upload(groups);
     d_tasks = upload(tasks);
     d_items = upload(items);
+    if (!col_base.empty()) {
+      d_col_base = upload(col_base);
+      d_col_stride = upload(col_stride);
+    }
   }
 };
 
@@ -1036,6 +1144,7 @@ void run_contract_ozaki(tamm_ctx* ctx, double alpha, tamm_tensor* C, const char*
   int chunk_k = ctx->oz_chunk_k;
   int tile_policy = ctx->oz_tile_policy;
   bool persistent = ctx->oz_persistent;
+  const bool panels = ctx->oz_panels;
   if (slices == 0) {
     slices = kOzDefaultSlices;
     if (!float_split) {
@@ -1050,7 +1159,8 @@ void run_contract_ozaki(tamm_ctx* ctx, double alpha, tamm_tensor* C, const char*
   }
   if (slices < kOzMinSlices || slices > kOzMaxSlices)
     throw Error(TAMM_EINVAL, "ozaki: slices must be %d..%d (0 = %d)", kOzMinSlices, kOzMaxSlices, kOzDefaultSlices);
-  const std::string key = "oz" + std::to_string(slices) + "|" + std::to_string(tile_policy) + "|" +
+  const std::string key = "oz" + std::to_string(slices) + "|" + std::to_string(tile_policy) +
+                          (panels ? "p|" : "|") +
                           std::to_string(C->id) + "|" + lc + "|" + std::to_string(A->id) + "|" + la + "|" +
                           std::to_string(B->id) + "|" + lb;
   OzakiPlan* p;
@@ -1059,7 +1169,7 @@ void run_contract_ozaki(tamm_ctx* ctx, double alpha, tamm_tensor* C, const char*
     p = static_cast<OzakiPlan*>(itp->second.get());
   } else {
     if (ctx->capturing) throw Error(TAMM_EINVAL, "a new contraction plan cannot be built during graph capture");
-    p = new OzakiPlan(ctx, C, lc, A, la, B, lb, slices, tile_policy);
+    p = new OzakiPlan(ctx, C, lc, A, la, B, lb, slices, tile_policy, panels);
     ctx->plans[key].reset(p);
   }
   OzOpRecord op;
@@ -1118,6 +1228,8 @@ void execute_ozaki(tamm_ctx* ctx, const std::vector<OzOpRecord>& ops) {
     pr.groups = p->d_groups;
     pr.tasks = p->d_tasks;
     pr.items = p->d_items;
+    pr.col_base = p->d_col_base;
+    pr.col_stride = p->d_col_stride;
     pr.c = p->perm_out ? (double*)(s + p->off_x) : ops[i].c;
     pr.alpha = ops[i].alpha;
     pr.beta = p->perm_out ? 0.0 : ops[i].beta;

@@ -53,7 +53,7 @@ struct SliceBlock {
   int32_t k_contig;  // consecutive k are adjacent in memory (else consecutive rows are)
   int32_t k_dense;   // the whole summed range is one contiguous run: offset of k is k
   int32_t tile_rows; // rows per tile H (a multiple of 16, <= 128): a tile is S slices of H x 16 bf16
-  int32_t pad;
+  int32_t dst_row0;  // image row of this block's row 0 (blocks concatenated along rows share an image)
 };
 
 constexpr int kOzSliceMaxRows = 128;  // rows per slicing CTA
@@ -67,8 +67,12 @@ struct SliceItem {
   int32_t pad;
 };
 
+// An output group: one output block (row-major M x N at c_off), or a column
+// panel -- output blocks that share M and every A block, concatenated along
+// N (colmap >= 0: column c lives at col_base[colmap + c] + row * col_stride[colmap + c]).
 struct OzGroup {
   int64_t c_off;
+  int64_t colmap;
   int32_t M, N;
   int32_t task_begin, task_end;
   int32_t n_tile;  // output columns per work item = rows per B tile (a multiple of 16, <= 128)
@@ -92,6 +96,8 @@ struct OzProblem {
   const OzGroup* groups;
   const OzTask* tasks;
   const struct OzItem* items;
+  const int64_t* col_base;    // column maps of the panels
+  const int32_t* col_stride;
   int64_t item_begin;
   double* c;
   double alpha, beta;

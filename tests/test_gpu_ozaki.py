@@ -185,21 +185,27 @@ def test_three_slices_after_six_slices(gpu_lib):
 
 @pytest.mark.parametrize("O_,V_,to,tv", [(8, 24, 2, 4), (16, 40, 8, 10), (40, 80, 20, 40)])
 def test_tile_policies_agree(gpu_lib, O_, V_, to, tv):
-    """Output columns per work item (four tile policies) and the GEMM grid (one CTA per work item, or
-    one per SM walking the items): every combination gives bitwise the same values."""
+    """Output columns per work item (four tile policies), the GEMM grid (one CTA per work item, or
+    one per SM walking the items) and column panels on or off: every combination gives bitwise
+    the same values."""
     from paper_2201_01257_gb300 import workload as gw
 
     w = wl.small_doubles(O_, V_, to, tv)
     outs = []
+    ctx = gpu_lib.Context(0)
+    gsp, gt = gw.build(ctx, w)
+    runner = gw.Runner(ctx, w, gsp, gt)
     for policy in (0, 1, 2, 3):
         for persistent in (0, 1):
-            ctx = gpu_lib.Context(0)
-            ctx.set_option(gpu_lib.TAMM_OPT_OZAKI_TILE_POLICY, policy)
-            ctx.set_option(gpu_lib.TAMM_OPT_OZAKI_PERSISTENT, persistent)
-            gsp, gt = gw.build(ctx, w)
-            gw.Runner(ctx, w, gsp, gt).run("ozaki_bf16", 0)
-            ctx.sync()
-            outs.append({k: gt[k].download() for k in ("R", "W")})
+            for panels in (0, 1):
+                ctx.set_option(gpu_lib.TAMM_OPT_OZAKI_TILE_POLICY, policy)
+                ctx.set_option(gpu_lib.TAMM_OPT_OZAKI_PERSISTENT, persistent)
+                ctx.set_option(gpu_lib.TAMM_OPT_OZAKI_PANELS, panels)
+                gt["R"].data.fill_(float("nan"))
+                gt["W"].data.fill_(float("nan"))
+                runner.run("ozaki_bf16", 0)
+                ctx.sync()
+                outs.append({k: gt[k].download() for k in ("R", "W")})
     for k in ("R", "W"):
         for p in range(1, len(outs)):
             assert np.array_equal(outs[p][k], outs[0][k]), (k, p, rel_err(outs[p][k], outs[0][k]))
