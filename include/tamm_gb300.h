@@ -116,6 +116,11 @@ TAMM_API const char* tamm_last_error(const tamm_ctx* ctx);
                                    the same A block in every summed-tile pair run as one column panel
                                    (their B blocks stacked into one image: wider N, A tiles read once);
                                    0 = every output block alone */
+#define TAMM_OPT_OZAKI_SPLIT_K 4 /* split precision: 1 (default) = when a contraction has fewer than two
+                                    128 x 128 output tiles per SM, cut every output block's summed tile
+                                    pairs into up to 8 consecutive ranges, computed in parallel into a
+                                    workspace and added in range order (deterministic; a different
+                                    rounding from the unsplit sum); 0 = never split */
 /* Set option `option` to `value`.  Errors: TAMM_EINVAL (unknown option or value out of range). */
 TAMM_API tamm_status tamm_ctx_set_option(tamm_ctx* ctx, int option, int64_t value);
 
@@ -125,7 +130,8 @@ TAMM_API tamm_status tamm_ctx_set_option(tamm_ctx* ctx, int option, int64_t valu
 #define TAMM_KERNEL_GEMM_F64 2  /* FP64 block GEMM */
 #define TAMM_KERNEL_SLICE 3     /* split-precision operand slicing */
 #define TAMM_KERNEL_GEMM_OZ 4   /* split-precision tcgen05 block GEMM */
-#define TAMM_KERNEL_CLASSES 5
+#define TAMM_KERNEL_SPLIT_REDUCE 5 /* split precision: sum of split summed ranges into C */
+#define TAMM_KERNEL_CLASSES 6
 /* Number of kernels this context has launched since creation. */
 TAMM_API tamm_status tamm_ctx_launch_count(const tamm_ctx* ctx, int64_t* launches);
 /* enable != 0: bracket every later kernel launch with CUDA events on the

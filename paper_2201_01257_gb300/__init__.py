@@ -28,8 +28,9 @@ _lib = None
 TAMM_OK, TAMM_EINVAL, TAMM_ENOMEM, TAMM_ECUDA, TAMM_EUNSUPPORTED, TAMM_ETIMEOUT, TAMM_ECHECK, TAMM_ELIMIT = range(8)
 TAMM_SYM_DENSE, TAMM_SYM_SPIN, TAMM_SYM_SPIN_IRREP = 0, 1, 2
 TAMM_PREC_F64, TAMM_PREC_OZAKI_BF16, TAMM_PREC_OZAKI_I8, TAMM_PREC_BF16X3 = 0, 1, 2, 3
-KERNEL_CLASSES = ("add", "reduce", "gemm_f64", "slice", "gemm_ozaki")
-TAMM_OPT_OZAKI_CHUNK_K, TAMM_OPT_OZAKI_PERSISTENT, TAMM_OPT_OZAKI_TILE_POLICY, TAMM_OPT_OZAKI_PANELS = 0, 1, 2, 3
+KERNEL_CLASSES = ("add", "reduce", "gemm_f64", "slice", "gemm_ozaki", "split_reduce")
+(TAMM_OPT_OZAKI_CHUNK_K, TAMM_OPT_OZAKI_PERSISTENT, TAMM_OPT_OZAKI_TILE_POLICY, TAMM_OPT_OZAKI_PANELS,
+ TAMM_OPT_OZAKI_SPLIT_K) = range(5)
 SYM = {"dense": TAMM_SYM_DENSE, "spin": TAMM_SYM_SPIN, "spin_irrep": TAMM_SYM_SPIN_IRREP}
 PREC = {"f64": TAMM_PREC_F64, "ozaki_bf16": TAMM_PREC_OZAKI_BF16, "ozaki_i8": TAMM_PREC_OZAKI_I8,
         "bf16x3": TAMM_PREC_BF16X3}

@@ -482,10 +482,10 @@ __global__ void __launch_bounds__(kThreads, 1) ozaki_gemm_kernel(const __grid_co
         const OzGroup g = p.problems[q].groups[it.group];
         const uint32_t b_bytes = (uint32_t)S * 32u * (uint32_t)g.n_tile;
         OzTask tk_next{};
-        if (g.task_begin < g.task_end) tk_next = tasks[g.task_begin];
-        for (int t = g.task_begin; t < g.task_end && !*abort_flag; ++t) {
+        if (it.t0 < it.t1) tk_next = tasks[it.t0];
+        for (int t = it.t0; t < it.t1 && !*abort_flag; ++t) {
           const OzTask tk = tk_next;
-          if (t + 1 < g.task_end) tk_next = tasks[t + 1];  // loaded while this task's copies issue
+          if (t + 1 < it.t1) tk_next = tasks[t + 1];  // loaded while this task's copies issue
           const uint8_t* a = a_tiles + tk.a_off + (size_t)((int64_t)it.mt * tk.k_tiles) * half_bytes;
           const uint8_t* b = b_tiles + tk.b_off + (size_t)((int64_t)it.nt * tk.k_tiles) * b_bytes;
           for (int kt = 0; kt < tk.k_tiles; ++kt) {
@@ -541,10 +541,10 @@ __global__ void __launch_bounds__(kThreads, 1) ozaki_gemm_kernel(const __grid_co
         // a ragged tile runs unfused with N rounded up to 16 columns
         const uint32_t idesc1 = sm100::idesc_bf16_f32(128, full_tile ? H : (uint32_t)((n_valid + 15) & ~15));
         const uint32_t idesc2 = sm100::idesc_bf16_f32(128, 2u * H);
-        int kt_next = g.task_begin < g.task_end ? tasks[g.task_begin].k_tiles : 0;
-        for (int t = g.task_begin; t < g.task_end && ok; ++t) {
+        int kt_next = it.t0 < it.t1 ? tasks[it.t0].k_tiles : 0;
+        for (int t = it.t0; t < it.t1 && ok; ++t) {
           const int k_tiles = kt_next;
-          if (t + 1 < g.task_end) kt_next = tasks[t + 1].k_tiles;  // loaded while this task issues
+          if (t + 1 < it.t1) kt_next = tasks[t + 1].k_tiles;  // loaded while this task issues
           int in_chunk = 0;  // position inside the current chunk (no division on the issue path)
           for (int kt = 0; kt < k_tiles; ++kt) {
             const bool first = in_chunk == 0;
@@ -621,8 +621,8 @@ __global__ void __launch_bounds__(kThreads, 1) ozaki_gemm_kernel(const __grid_co
       // are in flight at once)
       int Eref = kOzExpZero, F = kOzExpZero;
       {
-        int t = g.task_begin;
-        for (; t + 4 <= g.task_end; t += 4) {
+        int t = it.t0;
+        for (; t + 4 <= it.t1; t += 4) {
           int ea4[4], eb4[4];
 #pragma unroll
           for (int u = 0; u < 4; ++u) {
@@ -635,7 +635,7 @@ __global__ void __launch_bounds__(kThreads, 1) ozaki_gemm_kernel(const __grid_co
             F = max(F, eb4[u]);
           }
         }
-        for (; t < g.task_end; ++t) {
+        for (; t < it.t1; ++t) {
           Eref = max(Eref, a_exp[tasks[t].a_exp + arow]);
           if (has_col) F = max(F, b_exp[tasks[t].b_exp + bcol]);
         }
@@ -651,15 +651,15 @@ __global__ void __launch_bounds__(kThreads, 1) ozaki_gemm_kernel(const __grid_co
       for (int j = 0; j < 64; ++j) hi[j] = lo[j] = 0.0f;
       // exponents of the next task are loaded one task ahead, while this task's chunks drain
       int ea_next = kOzExpZero, eb_next = kOzExpZero, kt_next = 0;
-      if (g.task_begin < g.task_end) {
-        const OzTask t0 = tasks[g.task_begin];
+      if (it.t0 < it.t1) {
+        const OzTask t0 = tasks[it.t0];
         ea_next = a_exp[t0.a_exp + arow];
         if (has_col) eb_next = b_exp[t0.b_exp + bcol];
         kt_next = t0.k_tiles;
       }
-      for (int t = g.task_begin; t < g.task_end; ++t, ++task_count) {
+      for (int t = it.t0; t < it.t1; ++t, ++task_count) {
         const int ea = ea_next, eb = eb_next, k_tiles = kt_next;
-        if (t + 1 < g.task_end) {
+        if (t + 1 < it.t1) {
           const OzTask tn = tasks[t + 1];
           ea_next = a_exp[tn.a_exp + arow];
           if (has_col) eb_next = b_exp[tn.b_exp + bcol];
@@ -706,10 +706,23 @@ __global__ void __launch_bounds__(kThreads, 1) ozaki_gemm_kernel(const __grid_co
           buf = buf + 1 == nbuf ? 0u : buf + 1;
         }
       }
-      if (g.task_begin == g.task_end) epi_barrier();  // keep the fref barrier count uniform
+      if (it.t0 == it.t1) epi_barrier();  // keep the fref barrier count uniform
       if (ok) {
         const int grow = it.mt * kOzTileM + row;
-        if (grow < g.M) {
+        if (grow < g.M && it.split >= 0) {
+          // a partial over one summed range of a split group: its FP64 value, dense [split][M][N]
+          double* wrow = p.problems[q].ws + g.ws_off + ((int64_t)it.split * g.M + grow) * g.N + (int64_t)it.nt * H;
+#pragma unroll
+          for (int j = 0; j < 64; ++j) {
+            const int col = c0 + j;
+            if (col < n_valid) {
+              double v = 0.0;
+              if (Eref != kOzExpZero && fref[col] != kOzExpZero)
+                v = ((double)hi[j] + (double)lo[j]) * pow2d(Eref + fref[col] - 12);
+              wrow[col] = v;
+            }
+          }
+        } else if (grow < g.M) {
           // one output block: row-major M x N at c_off; a column panel: column c of block m at
           // col_base[c] + row * col_stride[c]
           double* c = p.problems[q].c;
@@ -735,6 +748,25 @@ __global__ void __launch_bounds__(kThreads, 1) ozaki_gemm_kernel(const __grid_co
   if (warp == 1) {
     sm100::tc_fence_after();
     sm100::tmem_dealloc(tmem, 512);
+  }
+}
+
+// Sum of a split group's partials in range order, then C = beta C + alpha sum.
+__global__ void __launch_bounds__(256) ozaki_reduce_kernel(const OzReduceItem* __restrict__ items,
+                                                           const OzGroup* __restrict__ groups,
+                                                           const double* __restrict__ ws, double* __restrict__ c,
+                                                           const int64_t* __restrict__ col_base,
+                                                           const int32_t* __restrict__ col_stride, double alpha,
+                                                           double beta) {
+  const OzReduceItem it = items[blockIdx.x];
+  const OzGroup g = groups[it.group];
+  const int64_t MN = (int64_t)g.M * g.N;
+  for (int64_t e = it.e0 + threadIdx.x; e < it.e1; e += blockDim.x) {
+    double v = 0.0;
+    for (int sp = 0; sp < g.nsplit; ++sp) v += ws[g.ws_off + sp * MN + e];
+    const int64_t row = e / g.N, col = e - row * g.N;
+    double* cp = g.colmap >= 0 ? c + col_base[g.colmap + col] + row * col_stride[g.colmap + col] : c + g.c_off + e;
+    *cp = beta != 0.0 ? fma(beta, *cp, alpha * v) : alpha * v;
   }
 }
 
@@ -811,6 +843,17 @@ static cudaError_t gemm_dispatch(tamm_ctx* ctx, const OzParams& p, int grid) {
   return cudaGetLastError();
 }
 
+cudaError_t launch_ozaki_reduce(tamm_ctx* ctx, const OzReduceItem* items, int64_t n_items, const OzGroup* groups,
+                                const double* ws, double* c, const int64_t* col_base, const int32_t* col_stride,
+                                double alpha, double beta) {
+  if (n_items == 0) return cudaSuccess;
+  kernel_begin(ctx, TAMM_KERNEL_SPLIT_REDUCE);
+  ozaki_reduce_kernel<<<(unsigned)n_items, 256, 0, ctx->stream>>>(items, groups, ws, c, col_base, col_stride, alpha,
+                                                                   beta);
+  kernel_end(ctx, TAMM_KERNEL_SPLIT_REDUCE);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_ozaki_gemm(tamm_ctx* ctx, OzProblem* problems, const int64_t* n_items_per_problem,
                               int n_problems, int S, int chunk_tiles, bool persistent) {
   if (chunk_tiles < 1 || chunk_tiles > kOzChunkTiles) return cudaErrorInvalidValue;
@@ -864,8 +907,10 @@ struct OzakiPlan : Plan {
   int64_t* d_col_base = nullptr;
   int32_t* d_col_stride = nullptr;
   int64_t n_items = 0;
+  OzReduceItem* d_red = nullptr;  // reduction chunks of the split groups
+  int64_t n_red = 0;
   std::unique_ptr<AddPlan> perm_out;
-  size_t off_ta = 0, off_tb = 0, off_ea = 0, off_eb = 0, off_x = 0, scratch_bytes = 0;
+  size_t off_ta = 0, off_tb = 0, off_ea = 0, off_eb = 0, off_x = 0, off_ws = 0, scratch_bytes = 0;
   int warps_a = 8, kbuf_a = 2, warps_b = 8, kbuf_b = 2;  // slicing launch shapes
 
   // Geometry of block b of the GEMM-order operand `gemm` (blocks of `native`
@@ -950,7 +995,7 @@ struct OzakiPlan : Plan {
   }
 
   OzakiPlan(tamm_ctx* c, const tamm_tensor* C, const char* lc, const tamm_tensor* A, const char* la,
-            const tamm_tensor* B, const char* lb, int slices, int tile_policy, bool panels)
+            const tamm_tensor* B, const char* lb, int slices, int tile_policy, bool panels, bool allow_split)
       : Plan(c), lay(c, C, lc, A, la, B, lb), S(slices) {
     const int nfl = (int)lay.free_left.size(), nfr = (int)lay.free_right.size(), nk = (int)lay.summed.size();
     auto perm_of = [](const std::string& need, const std::string& have) {
@@ -1027,7 +1072,8 @@ struct OzakiPlan : Plan {
       gg.M = (int32_t)g0.M;
       gg.N = (int32_t)Np;
       gg.n_tile = H;
-      gg.pad = 0;
+      gg.nsplit = 1;
+      gg.ws_off = 0;
       if (mem.size() == 1) {
         gg.c_off = O.off[(size_t)g0.out_block];
         gg.colmap = -1;
@@ -1108,18 +1154,51 @@ struct OzakiPlan : Plan {
       off_x = scratch_bytes;
       scratch_bytes += align((size_t)lay.out_perm->n_elems * 8);
     }
+    // Split summed ranges when the contraction has too few output tiles to fill the GPU (two
+    // 128 x 128 tiles per SM): every group's tasks are cut into the same number of consecutive
+    // ranges (at most 8, at most one per task).  The count depends only on the block structure,
+    // so it is the same whatever the tile policy, grid kind or panel setting.
+    int64_t base_tiles = 0;
+    for (const auto& g : lay.groups) base_tiles += ((g.M + 127) / 128) * ((g.N + 127) / 128);
+    const int64_t target = 2 * std::max(1, c->sm_count);
+    const int split = !allow_split || base_tiles >= target || base_tiles == 0
+                          ? 1
+                          : (int)std::min<int64_t>(8, (target + base_tiles - 1) / base_tiles);
+    int64_t ws_doubles = 0;
+    std::vector<OzReduceItem> red;
+    for (size_t gi = 0; gi < groups.size(); ++gi) {
+      OzGroup& gg = groups[gi];
+      const int32_t T = gg.task_end - gg.task_begin;
+      gg.nsplit = std::max(1, std::min(split, T));
+      if (gg.nsplit > 1) {
+        gg.ws_off = ws_doubles;
+        const int64_t MN = (int64_t)gg.M * gg.N;
+        ws_doubles += gg.nsplit * MN;
+        for (int64_t e = 0; e < MN; e += 4096) red.push_back({(int32_t)gi, 0, e, std::min<int64_t>(MN, e + 4096)});
+      }
+    }
     // work items, the groups with the longest summed range first (the grid then ends on short
     // items); inside a group, the items sharing an A row tile are adjacent (L2 reuse)
     std::vector<OzItem> items;
     std::vector<int32_t> order(groups.size());
     for (size_t i = 0; i < order.size(); ++i) order[i] = (int32_t)i;
-    std::stable_sort(order.begin(), order.end(),
-                     [&](int32_t x, int32_t y) { return group_k[(size_t)x] > group_k[(size_t)y]; });
+    std::stable_sort(order.begin(), order.end(), [&](int32_t x, int32_t y) {
+      return group_k[(size_t)x] / groups[(size_t)x].nsplit > group_k[(size_t)y] / groups[(size_t)y].nsplit;
+    });
     for (int32_t gi : order) {
       const OzGroup& gg = groups[(size_t)gi];
       const int32_t mts = (gg.M + kOzTileM - 1) / kOzTileM, nts = (gg.N + gg.n_tile - 1) / gg.n_tile;
-      for (int32_t mt = 0; mt < mts; ++mt)
-        for (int32_t nt = 0; nt < nts; ++nt) items.push_back({0, gi, mt, nt});
+      const int32_t T = gg.task_end - gg.task_begin;
+      for (int32_t sp = 0; sp < gg.nsplit; ++sp) {
+        const int32_t t0 = gg.task_begin + (int32_t)((int64_t)sp * T / gg.nsplit);
+        const int32_t t1 = gg.task_begin + (int32_t)((int64_t)(sp + 1) * T / gg.nsplit);
+        for (int32_t mt = 0; mt < mts; ++mt)
+          for (int32_t nt = 0; nt < nts; ++nt) items.push_back({gi, mt, nt, gg.nsplit > 1 ? sp : -1, t0, t1});
+      }
+    }
+    if (ws_doubles) {
+      off_ws = scratch_bytes;
+      scratch_bytes += align((size_t)ws_doubles * 8);
     }
     n_ia = (int64_t)ia.size();
     n_ib = (int64_t)ib.size();
@@ -1135,6 +1214,8 @@ struct OzakiPlan : Plan {
       d_col_base = upload(col_base);
       d_col_stride = upload(col_stride);
     }
+    n_red = (int64_t)red.size();
+    if (n_red) d_red = upload(red);
   }
 };
 
@@ -1145,6 +1226,7 @@ void run_contract_ozaki(tamm_ctx* ctx, double alpha, tamm_tensor* C, const char*
   int tile_policy = ctx->oz_tile_policy;
   bool persistent = ctx->oz_persistent;
   const bool panels = ctx->oz_panels;
+  const bool allow_split = ctx->oz_split;
   if (slices == 0) {
     slices = kOzDefaultSlices;
     if (!float_split) {
@@ -1160,7 +1242,7 @@ void run_contract_ozaki(tamm_ctx* ctx, double alpha, tamm_tensor* C, const char*
   if (slices < kOzMinSlices || slices > kOzMaxSlices)
     throw Error(TAMM_EINVAL, "ozaki: slices must be %d..%d (0 = %d)", kOzMinSlices, kOzMaxSlices, kOzDefaultSlices);
   const std::string key = "oz" + std::to_string(slices) + "|" + std::to_string(tile_policy) +
-                          (panels ? "p|" : "|") +
+                          (panels ? "p" : "") + (allow_split ? "s|" : "|") +
                           std::to_string(C->id) + "|" + lc + "|" + std::to_string(A->id) + "|" + la + "|" +
                           std::to_string(B->id) + "|" + lb;
   OzakiPlan* p;
@@ -1169,7 +1251,7 @@ void run_contract_ozaki(tamm_ctx* ctx, double alpha, tamm_tensor* C, const char*
     p = static_cast<OzakiPlan*>(itp->second.get());
   } else {
     if (ctx->capturing) throw Error(TAMM_EINVAL, "a new contraction plan cannot be built during graph capture");
-    p = new OzakiPlan(ctx, C, lc, A, la, B, lb, slices, tile_policy, panels);
+    p = new OzakiPlan(ctx, C, lc, A, la, B, lb, slices, tile_policy, panels, allow_split);
     ctx->plans[key].reset(p);
   }
   OzOpRecord op;
@@ -1230,6 +1312,7 @@ void execute_ozaki(tamm_ctx* ctx, const std::vector<OzOpRecord>& ops) {
     pr.items = p->d_items;
     pr.col_base = p->d_col_base;
     pr.col_stride = p->d_col_stride;
+    pr.ws = (double*)(s + p->off_ws);
     pr.c = p->perm_out ? (double*)(s + p->off_x) : ops[i].c;
     pr.alpha = ops[i].alpha;
     pr.beta = p->perm_out ? 0.0 : ops[i].beta;
@@ -1252,6 +1335,13 @@ void execute_ozaki(tamm_ctx* ctx, const std::vector<OzOpRecord>& ops) {
     cuda_check(launch_ozaki_gemm(ctx, batch.data(), n.data(), (int)batch.size(), ops[i].slices,
                                  ops[i].chunk_k / kOzTileK, ops[i].persistent),
                "ozaki gemm");
+  }
+  for (size_t i = 0; i < ops.size(); ++i) {
+    const OzakiPlan* p = static_cast<const OzakiPlan*>(ops[i].plan);
+    if (p->n_red)
+      cuda_check(launch_ozaki_reduce(ctx, p->d_red, p->n_red, p->d_groups, probs[i].ws, probs[i].c, p->d_col_base,
+                                     p->d_col_stride, probs[i].alpha, probs[i].beta),
+                 "ozaki split reduction");
   }
   const double one = 1.0;
   for (size_t i = 0; i < ops.size(); ++i) {

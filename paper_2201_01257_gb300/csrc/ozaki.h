@@ -70,13 +70,18 @@ struct SliceItem {
 // An output group: one output block (row-major M x N at c_off), or a column
 // panel -- output blocks that share M and every A block, concatenated along
 // N (colmap >= 0: column c lives at col_base[colmap + c] + row * col_stride[colmap + c]).
+// A group's tasks may be split into nsplit summed ranges (few output tiles,
+// long summed extent): each range's work items write their FP64 partials to
+// the workspace, dense [split][M][N] at ws_off, and a reduction adds them in
+// range order into C.
 struct OzGroup {
   int64_t c_off;
   int64_t colmap;
+  int64_t ws_off;
   int32_t M, N;
   int32_t task_begin, task_end;
   int32_t n_tile;  // output columns per work item = rows per B tile (a multiple of 16, <= 128)
-  int32_t pad;
+  int32_t nsplit;
 };
 
 struct OzTask {
@@ -98,6 +103,7 @@ struct OzProblem {
   const struct OzItem* items;
   const int64_t* col_base;    // column maps of the panels
   const int32_t* col_stride;
+  double* ws;                 // partials of split groups
   int64_t item_begin;
   double* c;
   double alpha, beta;
@@ -105,7 +111,16 @@ struct OzProblem {
 constexpr int kOzMaxProblems = 64;  // problems per launch (kernel-parameter table)
 
 struct OzItem {
-  int32_t problem, group, mt, nt;
+  int32_t group, mt, nt;
+  int32_t split;   // summed range of a split group (-1: the group is not split)
+  int32_t t0, t1;  // tasks [t0, t1) of this item
+};
+
+// One chunk of the reduction of a split group's partials.
+struct OzReduceItem {
+  int32_t group;
+  int32_t pad;
+  int64_t e0, e1;  // elements [e0, e1) of the group's M x N output
 };
 
 // MMA schedule for one K step: A slice, first B slice, number of adjacent B
@@ -170,6 +185,10 @@ inline int oz_tile_rows(int64_t rows, int policy) {
 cudaError_t launch_ozaki_slice(tamm_ctx* ctx, const double* src, const SliceBlock* blocks, const SliceItem* items,
                                int64_t n_items, int S, bool float_split, uint8_t* tiles, int32_t* exps, int warps,
                                int kbuf);
+// Reduction of split groups' partials into C (after the GEMM launch).
+cudaError_t launch_ozaki_reduce(tamm_ctx* ctx, const OzReduceItem* items, int64_t n_items, const OzGroup* groups,
+                                const double* ws, double* c, const int64_t* col_base, const int32_t* col_stride,
+                                double alpha, double beta);
 // One launch over the work items of up to kOzMaxProblems problems (item_begin
 // of each problem is filled in here); `n_items` is the total.
 cudaError_t launch_ozaki_gemm(tamm_ctx* ctx, OzProblem* problems, const int64_t* n_items_per_problem,

@@ -213,6 +213,11 @@ extern "C" tamm_status tamm_ctx_set_option(tamm_ctx* ctx, int option, int64_t va
       ctx->oz_tile_policy = (int)value;
       return;
     }
+    if (option == TAMM_OPT_OZAKI_SPLIT_K) {
+      if (value != 0 && value != 1) throw Error(TAMM_EINVAL, "split must be 0 or 1");
+      ctx->oz_split = value != 0;
+      return;
+    }
     if (option == TAMM_OPT_OZAKI_PANELS) {
       if (value != 0 && value != 1) throw Error(TAMM_EINVAL, "panels must be 0 or 1");
       ctx->oz_panels = value != 0;

@@ -148,6 +148,7 @@ struct tamm_ctx {
   bool oz_persistent = false;  // split precision: persistent GEMM grid (one CTA per SM)
   int oz_tile_policy = 1;      // split precision: output columns per work item (TAMM_OPT_OZAKI_TILE_POLICY)
   bool oz_panels = true;       // split precision: concatenate output blocks sharing their A blocks
+  bool oz_split = true;        // split precision: split long summed ranges of small contractions
   int64_t launches = 0;    // kernels launched by this context
   bool profiling = false;  // bracket launches with CUDA events
   struct TimedLaunch {

@@ -218,8 +218,13 @@ def test_scaled_batch_in_one_graph(cfg3):
                     T = r.tensors
                     ctx.contract(0.5, T["R"], "abij", 0.0, T["V_vvvv"], "abef", T["T"], "efij", "ozaki_bf16")
 
+        ctx.profile(True)
+        n0 = ctx.launch_count()
         step()
         ctx.sync()
+        eager_launches = ctx.launch_count() - n0
+        prof = ctx.profile_read()
+        ctx.profile(False)
         eager = [r.tensors["R"].download() for _, r in probs]
         ctx.graph_begin()
         try:
@@ -230,7 +235,10 @@ def test_scaled_batch_in_one_graph(cfg3):
             r.tensors["R"].data.fill_(np.nan)
         g.launch()
     ctx.sync()
-    assert g.kernel_launches == 2 * len(probs) + 1  # two slicing launches per problem, one grouped GEMM
+    # two slicing launches per problem, one grouped GEMM for all 32, and the summed-range reductions
+    # of the problems too small to fill the GPU alone
+    assert prof["gemm_ozaki"][1] == 1 and prof["slice"][1] == 2 * len(probs)
+    assert g.kernel_launches == eager_launches == 2 * len(probs) + 1 + prof["split_reduce"][1]
     for (w, r), e in zip(probs, eager):
         assert np.array_equal(r.tensors["R"].download(), e)
     worst = 0.0

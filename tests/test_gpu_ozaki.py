@@ -209,3 +209,30 @@ def test_tile_policies_agree(gpu_lib, O_, V_, to, tv):
     for k in ("R", "W"):
         for p in range(1, len(outs)):
             assert np.array_equal(outs[p][k], outs[0][k]), (k, p, rel_err(outs[p][k], outs[0][k]))
+
+
+def test_split_summed_ranges(gpu_lib):
+    """Few output tiles and long summed extents (O=16, V=64, tiles 8/16): the contractions are split
+    into summed ranges (the reduction kernel runs), match the unsplit sums to rounding and the oracle
+    to 1e-10."""
+    from paper_2201_01257_gb300 import workload as gw
+
+    w = wl.small_doubles(16, 64, 8, 16)
+    outs, reductions = [], []
+    for split in (0, 1):
+        ctx = gpu_lib.Context(0)
+        ctx.set_option(gpu_lib.TAMM_OPT_OZAKI_SPLIT_K, split)
+        gsp, gt = gw.build(ctx, w)
+        ctx.profile(True)
+        gw.Runner(ctx, w, gsp, gt).run("ozaki_bf16", 0)
+        ctx.sync()
+        reductions.append(ctx.profile_read()["split_reduce"][1])
+        outs.append({k: gt[k] for k in ("R", "W")})
+    assert reductions[0] == 0 and reductions[1] > 0, reductions
+    _, ot = O.build_workload(w)
+    O.run_workload(w, ot)
+    for k in ("R", "W"):
+        a = gpu_to_oracle_layout(outs[0][k], ot[k])
+        b = gpu_to_oracle_layout(outs[1][k], ot[k])
+        assert rel_err(b, a) <= 1e-12, (k, rel_err(b, a))
+        assert rel_err(b, ot[k].data) <= 1e-10, k
