@@ -126,8 +126,9 @@ struct OzReduceItem {
 // MMA schedule for one K step: A slice, first B slice, number of adjacent B
 // slices fused along N (1 or 2), accumulator region, and whether it is the
 // first write of its region(s) in a chunk.  Products (k, l) with k + l <= S + 1
-// (1-based) go to region min(k + l - 2, 3); exact-group products of adjacent B
-// slices are fused into one N = 256 MMA when `fuse` is set (full tiles).
+// (1-based) go to region min(k + l - 2, 3); products of adjacent B slices that
+// land in adjacent regions are fused into one N = 2H MMA when `fuse` is set
+// (full tiles).
 struct OzOp {
   int a, b, nb, region, first;
 };
@@ -143,7 +144,9 @@ __host__ __device__ constexpr OzSched oz_schedule(int S, bool fuse) {
     int l = 1;
     while (l <= S + 1 - k) {
       const int region = k + l - 2 < 3 ? k + l - 2 : 3;
-      const bool pair = fuse && region < 2 && l + 1 <= S + 1 - k && k + l + 1 <= 4;
+      // (k, l) and (k, l + 1) share one MMA when they land in two adjacent regions (region <= 2)
+      // that are both written for the first time in the chunk, or both accumulated
+      const bool pair = fuse && region < 3 && l + 1 <= S + 1 - k && written[region] == written[region + 1];
       OzOp& o = s.op[s.n++];
       o.a = k - 1;
       o.b = l - 1;
