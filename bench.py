@@ -35,14 +35,18 @@ if ROOT not in sys.path:
 METRIC = "block-sparse contraction TFLOP/s: split-precision vs FP64, rel err ≤1e-10"
 UNIT = "TFLOP/s"
 SLICES = 6
-# DRAM bytes per launch of the split-precision GEMM kernel from an ncu capture,
-# keyed by the hash of the kernel source it was taken on (null when it changed).
-MEASURED_TRAFFIC = {}
+# DRAM bytes (read + write) per launch of the split-precision GEMM kernel, averaged over the five GEMM
+# launches of a config-2 step, from the ncu launch list of this bench command (profiles/
+# launch_list_ccsd_doubles_O40_V240.md), keyed by the hash of the kernel sources it was taken on; a
+# changed kernel reports null until it is captured again.
+MEASURED_TRAFFIC = {"579fc31202d8e9d2": 8.011e9}
 
 
 def kernel_source_hash() -> str:
-    p = os.path.join(ROOT, "paper_2201_01257_gb300", "csrc", "ozaki.cu")
-    return hashlib.sha256(open(p, "rb").read()).hexdigest()[:16]
+    h = hashlib.sha256()
+    for f in ("ozaki.cu", "ozaki.h", "sm100.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_2201_01257_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
 
 
 def measured_peaks() -> dict:
