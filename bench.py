@@ -229,6 +229,27 @@ def run_ours(args, rank: int, world: int) -> dict | None:
     r_64, w_64, e_64 = T["R"].download(), T["W"].download(), float(energy_dev.item())
     rel = lambda a, b: float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
 
+    # --- each contraction alone (not the headline): split precision and FP64 ---
+    per_contraction = {}
+    for st in w.steps:
+        if not isinstance(st, wl.ContractSpec):
+            continue
+        res = {"nonzero_block_flops": run.flops(st)}
+        for prec, reps in (("oz", 3), ("f64", 1)):
+            go = lambda: run.run("ozaki_bf16" if prec == "oz" else "f64", oz_slices if prec == "oz" else 0,
+                                 steps=[st])
+            go()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(reps):
+                go()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            t = e0.elapsed_time(e1) / reps
+            res["split_ms" if prec == "oz" else "f64_ms"] = round(t, 3)
+            res["split_TFLOP/s" if prec == "oz" else "f64_TFLOP/s"] = round(res["nonzero_block_flops"] / t / 1e9, 3)
+        per_contraction[st.name] = res
+
     # --- end to end through the C ABI: pinned host inputs in, result out, every step ---
     # Every step copies all of its inputs from pinned host memory and reads R and the energy back.
     # Pipelined (the reported figure): the inputs of step k+1 are copied, on a second stream through
@@ -351,6 +372,7 @@ def run_ours(args, rank: int, world: int) -> dict | None:
         "f64": {"value": round(job_throughput(world, flops, ms_f64), 4), "unit": UNIT,
                 "ms_per_step": round(ms_f64, 2), "steps": f64_steps},
         "speedup_vs_f64": round(ms_f64 / ms, 2),
+        "per_contraction": per_contraction,
         "rel_err_vs_f64": {"R": rel(r_oz, r_64), "W": rel(w_oz, w_64), "energy": abs(e_oz - e_64) / abs(e_64)},
         "e2e": {"value": round(job_throughput(world, flops, ms_e2e), 3), "unit": UNIT,
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": round(ms_e2e, 3),
@@ -679,6 +701,99 @@ def run_batch_case(args) -> dict:
             "ms": round(total_ms, 3), "TFLOP/s": round(total_flops / total_ms / 1e9, 3)}
 
 
+def _device_fill(T, spec, seed):
+    import torch
+
+    gen = torch.Generator(device=T.data.device)
+    gen.manual_seed(seed)
+    T.data.normal_(0.0, spec.sigma, generator=gen)
+
+
+def run_config5_case(args) -> dict:
+    """Config 5 at full size (O=80, V=320, tiles 40/64; V_vvvv 31.5 GB): ladder, oooo and ring each
+    autotuned for 1e-10, timed alone in split precision and in FP64.  Inputs are seeded normals drawn on
+    the device (the host generator would take minutes for 4e9 elements); parity of this size is tested
+    on sampled sub-blocks with the host-generated inputs."""
+    import torch
+
+    import paper_2201_01257_gb300 as tg
+    from paper_2201_01257_gb300 import workload as gw
+    from tamm_synth import workloads as wl
+
+    w = wl.config5()
+    ctx = tg.Context(0)
+    sp, T = gw.build(ctx, w, fill=False)
+    for k, (name, spec) in enumerate(w.tensors.items()):
+        if spec.sigma:
+            _device_fill(T[name], spec, w.seed * 16 + k)
+    run = gw.Runner(ctx, w, sp, T)
+    run.run("f64")  # intermediates (W) hold the values the contractions see
+    ctx.sync()
+    out = {"case": f"{w.name}: vvvv ladder, oooo ladder, ring with P(ab)P(ij); split precision autotuned "
+                   "for rel err 1e-10, and FP64", "contractions": {}}
+    stream = torch.cuda.current_stream()
+    for st in w.steps:
+        if not isinstance(st, wl.ContractSpec):
+            continue
+        tuned = run.autotune(1e-10, steps=[st])[st.name]
+        res = {"nonzero_block_flops": run.flops(st), "autotuned": tuned}
+        for prec, reps in (("ozaki_bf16", max(1, args.steps)), ("f64", 1)):
+            run.run(prec, 0, steps=[st])
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(reps):
+                run.run(prec, 0, steps=[st])
+            e1.record(stream)
+            torch.cuda.synchronize()
+            t = e0.elapsed_time(e1) / reps
+            key = "split" if prec == "ozaki_bf16" else "f64"
+            res[f"{key}_ms"] = round(t, 3)
+            res[f"{key}_TFLOP/s"] = round(res["nonzero_block_flops"] / t / 1e9, 3)
+        out["contractions"][st.name] = res
+    return out
+
+
+def run_dense4d_case(args) -> dict:
+    """The paper's dense 4-D benchmark C(a,b,c,d) = A(a,b,m,n) B(m,n,c,d) (Sec. V), every extent N, on
+    one GPU in split precision (6 slices); FP64 as well when N <= 128.  Inputs are device-seeded normals."""
+    import torch
+
+    import paper_2201_01257_gb300 as tg
+    from paper_2201_01257_gb300 import workload as gw
+    from tamm_synth import workloads as wl
+
+    N, tile = (int(x) for x in args.dense4d.split(","))
+    w = wl.dense4d(N, tile)
+    ctx = tg.Context(0)
+    sp, T = gw.build(ctx, w, fill=False)
+    for k, name in enumerate(("A", "B")):
+        _device_fill(T[name], w.tensors[name], w.seed * 16 + k)
+    run = gw.Runner(ctx, w, sp, T)
+    st = w.steps[0]
+    flops = run.flops(st)
+    stream = torch.cuda.current_stream()
+    out = {"case": f"{w.name}: C(abcd) = A(abmn) B(mncd), all blocks stored", "nonzero_block_flops": flops}
+    precs = [("ozaki_bf16", max(1, args.steps))] + ([("f64", 1)] if N <= 128 else [])
+    results = {}
+    for prec, reps in precs:
+        run.run(prec, SLICES if prec == "ozaki_bf16" else 0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            run.run(prec, SLICES if prec == "ozaki_bf16" else 0)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t = e0.elapsed_time(e1) / reps
+        results[prec] = T["C"].download() if N <= 128 else None
+        key = "split" if prec == "ozaki_bf16" else "f64"
+        out[f"{key}_ms"] = round(t, 3)
+        out[f"{key}_TFLOP/s"] = round(flops / t / 1e9, 3)
+    if results.get("f64") is not None:
+        a, b = results["ozaki_bf16"], results["f64"]
+        out["split_rel_err_vs_f64"] = float(np.linalg.norm(a - b) / np.linalg.norm(b))
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -693,6 +808,8 @@ def main():
     ap.add_argument("--config3", action="store_true", help="time the uneven-irrep grouped ladder + ring instead")
     ap.add_argument("--irrep", default="", help="O,V: with --config3, spin-orbital counts (default 64,384)")
     ap.add_argument("--batch", action="store_true", help="time the 32 independent ladders in sub-batches instead")
+    ap.add_argument("--config5", action="store_true", help="time the O=80 V=320 contractions alone instead")
+    ap.add_argument("--dense4d", default="", help="N,tile: time the dense 4-D contraction instead")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -702,6 +819,10 @@ def main():
         out = run_config3_case(args)
     elif args.batch:
         out = run_batch_case(args)
+    elif args.config5:
+        out = run_config5_case(args)
+    elif args.dense4d:
+        out = run_dense4d_case(args)
     elif args.impl == "reference":
         out = run_reference(args, rank)
     else:

@@ -192,6 +192,20 @@ def small_doubles(O: int = 8, V: int = 24, to: int = 2, tv: int = 4, seed_k: int
 CONFIGS = {1: config1, 2: config2, 4: config4, 5: config5}
 
 
+def dense4d(N: int, tile: int, seed_k: int = 6) -> Workload:
+    """The dense 4-D contraction of the paper's performance comparison (Sec. V):
+    C(a,b,c,d) = A(a,b,m,n) B(m,n,c,d), every index of extent N in one space of fixed tiles, every
+    block stored; A, B ~ N(0, 0.1), not antisymmetrised."""
+    w = Workload(f"dense4d_N{N}_tile{tile}", SEED_BASE + seed_k, {"d": SpaceSpec("d", ((N, 1, 0),), tile=tile)}, {})
+    w.tensors = {
+        "A": TensorSpec("A", ("d",) * 4, 2, "dense", sigma=0.1, stream=1),
+        "B": TensorSpec("B", ("d",) * 4, 2, "dense", sigma=0.1, stream=2),
+        "C": TensorSpec("C", ("d",) * 4, 2, "dense"),
+    }
+    w.steps = [ContractSpec("dense4d", "C", "abcd", "A", "abmn", "B", "mncd", 1.0, beta=0.0)]
+    return w
+
+
 # ------------------------------------------------------------ D2h irreps
 
 def irrep_space(name: str, n_spin_orbitals: int, rng, tile_lo: int = 8, tile_hi: int = 96) -> SpaceSpec:

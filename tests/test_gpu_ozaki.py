@@ -236,3 +236,14 @@ def test_split_summed_ranges(gpu_lib):
         b = gpu_to_oracle_layout(outs[1][k], ot[k])
         assert rel_err(b, a) <= 1e-12, (k, rel_err(b, a))
         assert rel_err(b, ot[k].data) <= 1e-10, k
+
+
+def test_dense4d_matches_oracle(gpu_lib):
+    """The paper's dense 4-D contraction C(abcd) = A(abmn) B(mncd) (every block stored), N = 24 in tiles
+    of 8 (and a ragged 20 in tiles of 8): FP64 <= 1e-12 and split precision <= 1e-10 vs the oracle."""
+    for N, tile in ((24, 8), (20, 8)):
+        w = wl.dense4d(N, tile)
+        for prec, tol in (("f64", 1e-12), ("ozaki_bf16", 1e-10)):
+            _, gt, ot, _, _ = run_both(gpu_lib, w, prec)
+            err = rel_err(gpu_to_oracle_layout(gt["C"], ot["C"]), ot["C"].data)
+            assert err <= tol, (N, prec, err)
