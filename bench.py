@@ -36,7 +36,7 @@ METRIC = "block-sparse contraction TFLOP/s: split-precision vs FP64, rel err ≤
 UNIT = "TFLOP/s"
 SLICES = 6
 # DRAM bytes (read + write) per launch of the split-precision GEMM kernel, averaged over the five GEMM
-# launches of a config-2 step, from the ncu launch list of this bench command (profiles/
+# launches of an O=40 V=240 doubles step, from the ncu launch list of this bench command (profiles/
 # launch_list_ccsd_doubles_O40_V240.md), keyed by the hash of the kernel sources it was taken on; a
 # changed kernel reports null until it is captured again.
 MEASURED_TRAFFIC = {"579fc31202d8e9d2": 8.011e9}
@@ -156,7 +156,7 @@ def run_ours(args, rank: int, world: int) -> dict | None:
             dist.barrier()
         torch.cuda.synchronize()
 
-    w = wl.config2()
+    w = wl.ccsd_doubles_o40_v240()
     ctx = tg.Context(dev)
     spaces, T = gw.build(ctx, w, fill=False)
     host = {}
@@ -495,7 +495,7 @@ def cpu_baseline(seconds: float = 15.0) -> dict:
     """The FP64 oracle (as it stands) on a bounded sample of the same workload."""
     from tamm_synth import workloads as wl
 
-    w = wl.config2()
+    w = wl.ccsd_doubles_o40_v240()
     cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
     # calibrate on a small sample, then size the timed sample to about `seconds`
     T, plan, fl = oracle_sample(w, 1e9, seed=1)
@@ -513,7 +513,7 @@ def run_reference(args, rank: int) -> dict | None:
         return None
     from tamm_synth import workloads as wl
 
-    w = wl.config2()
+    w = wl.ccsd_doubles_o40_v240()
     cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
     T, plan, fl = oracle_sample(w, 1e9, seed=1)
     dt = time_oracle_sample(T, plan)
@@ -564,7 +564,7 @@ def run_ladder_case(args) -> dict:
             "TFLOP/s": round(fl / ms / 1e9, 3), "nonzero_block_flops": fl}
 
 
-def run_config3_case(args) -> dict:
+def run_irrep_case(args) -> dict:
     """Uneven D2h blocks (O=64, V=384): the ladder and the ring as one contraction group, eager and as a
     CUDA graph, against the same contractions launched one by one and the FP64 path."""
     import torch
@@ -574,7 +574,7 @@ def run_config3_case(args) -> dict:
     from tamm_synth import workloads as wl
 
     O_, V_ = (int(x) for x in args.irrep.split(",")) if args.irrep else (64, 384)
-    w = wl.config3(O=O_, V=V_)
+    w = wl.irrep_doubles(O=O_, V=V_)
     stream = torch.cuda.Stream(0)
     ctx = tg.Context(0, stream=stream)
     with torch.cuda.stream(stream):
@@ -626,7 +626,7 @@ def run_batch_case(args) -> dict:
     graph.  The stored V_vvvv of all 32 (162 GB in FP64 for these sizes) plus their slice images exceed
     one GPU, so sub-batches run one after another; inputs are seeded normals drawn on the device
     (torch generator, sigma 0.1 / 0.01): a throughput measurement (parity of the same path is tested on
-    the scaled batch and on the config-3 problem)."""
+    the scaled batch and on the O=64 V=384 irrep problem)."""
     import gc
 
     import torch
@@ -635,7 +635,7 @@ def run_batch_case(args) -> dict:
     from paper_2201_01257_gb300 import workload as gw
     from tamm_synth import workloads as wl
 
-    sizes = wl.config3_batch_sizes()
+    sizes = wl.ladder_batch_sizes()
     stream = torch.cuda.Stream(0)
     ctx = tg.Context(0, stream=stream)
     free, _ = torch.cuda.mem_get_info(0)
@@ -709,8 +709,8 @@ def _device_fill(T, spec, seed):
     T.data.normal_(0.0, spec.sigma, generator=gen)
 
 
-def run_config5_case(args) -> dict:
-    """Config 5 at full size (O=80, V=320, tiles 40/64; V_vvvv 31.5 GB): ladder, oooo and ring each
+def run_doubles_o80_case(args) -> dict:
+    """The O=80 V=320 doubles contractions at full size (tiles 40/64; V_vvvv 31.5 GB): ladder, oooo and ring each
     autotuned for 1e-10, timed alone in split precision and in FP64.  Inputs are seeded normals drawn on
     the device (the host generator would take minutes for 4e9 elements); parity of this size is tested
     on sampled sub-blocks with the host-generated inputs."""
@@ -720,7 +720,7 @@ def run_config5_case(args) -> dict:
     from paper_2201_01257_gb300 import workload as gw
     from tamm_synth import workloads as wl
 
-    w = wl.config5()
+    w = wl.ccsd_doubles_o80_v320()
     ctx = tg.Context(0)
     sp, T = gw.build(ctx, w, fill=False)
     for k, (name, spec) in enumerate(w.tensors.items()):
@@ -805,22 +805,22 @@ def main():
     ap.add_argument("--ladder", default="", help="O,V: time one split-precision ladder of that size instead")
     ap.add_argument("--slices", type=int, default=0,
                     help="split-precision slices per operand; 0 = autotune every contraction for 1e-10")
-    ap.add_argument("--config3", action="store_true", help="time the uneven-irrep grouped ladder + ring instead")
-    ap.add_argument("--irrep", default="", help="O,V: with --config3, spin-orbital counts (default 64,384)")
+    ap.add_argument("--irrep-doubles", action="store_true", help="time the uneven-irrep grouped ladder + ring instead")
+    ap.add_argument("--irrep", default="", help="O,V: with --irrep-doubles, spin-orbital counts (default 64,384)")
     ap.add_argument("--batch", action="store_true", help="time the 32 independent ladders in sub-batches instead")
-    ap.add_argument("--config5", action="store_true", help="time the O=80 V=320 contractions alone instead")
+    ap.add_argument("--doubles-o80", action="store_true", help="time the O=80 V=320 contractions alone instead")
     ap.add_argument("--dense4d", default="", help="N,tile: time the dense 4-D contraction instead")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     if args.ladder:
         out = run_ladder_case(args)
-    elif args.config3:
-        out = run_config3_case(args)
+    elif args.irrep_doubles:
+        out = run_irrep_case(args)
     elif args.batch:
         out = run_batch_case(args)
-    elif args.config5:
-        out = run_config5_case(args)
+    elif args.doubles_o80:
+        out = run_doubles_o80_case(args)
     elif args.dense4d:
         out = run_dense4d_case(args)
     elif args.impl == "reference":

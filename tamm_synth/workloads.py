@@ -101,7 +101,7 @@ def _vt(seed_k: int, O: int, V: int, to: int, tv: int, name: str) -> Workload:
                     {"occ": spin_space("occ", O, to), "virt": spin_space("virt", V, tv)}, {})
 
 
-def config1() -> Workload:
+def ladder_o8_v32() -> Workload:
     """Ladder R[a,b,i,j] += 0.5 sum_ef V[a,b,e,f] T[e,f,i,j]; O=8, V=32, tiles 4/8."""
     w = _vt(1, 8, 32, 4, 8, "ladder_O8_V32")
     w.tensors = {
@@ -149,14 +149,14 @@ def doubles_steps(full: bool = True) -> list:
     return s
 
 
-def config2() -> Workload:
+def ccsd_doubles_o40_v240() -> Workload:
     """Six doubles-shaped contractions; O=40, V=240, tiles 20/40."""
     w = _doubles(_vt(2, 40, 240, 20, 40, "ccsd_doubles_O40_V240"))
     w.steps = doubles_steps()
     return w
 
 
-def config4() -> Workload:
+def ladder_energy_o32_v192() -> Workload:
     """T' = T + 0.5 V_vvvv T; E = 1/4 V_oovv T'; O=32, V=192, tiles 16/32."""
     w = _vt(4, 32, 192, 16, 32, "ladder_energy_O32_V192")
     w.tensors = {
@@ -174,7 +174,7 @@ def config4() -> Workload:
     return w
 
 
-def config5() -> Workload:
+def ccsd_doubles_o80_v320() -> Workload:
     """Ladder + ring + oooo; O=80, V=320, tiles 40/64 (V_vvvv about 31 GB)."""
     w = _doubles(_vt(5, 80, 320, 40, 64, "ccsd_doubles_O80_V320"))
     s = doubles_steps(full=False)
@@ -189,7 +189,9 @@ def small_doubles(O: int = 8, V: int = 24, to: int = 2, tv: int = 4, seed_k: int
     return w
 
 
-CONFIGS = {1: config1, 2: config2, 4: config4, 5: config5}
+# the spin-block workloads by name
+WORKLOADS = {w.__name__: w for w in (ladder_o8_v32, ccsd_doubles_o40_v240, ladder_energy_o32_v192,
+                                     ccsd_doubles_o80_v320)}
 
 
 def dense4d(N: int, tile: int, seed_k: int = 6) -> Workload:
@@ -230,7 +232,7 @@ def irrep_space(name: str, n_spin_orbitals: int, rng, tile_lo: int = 8, tile_hi:
     return SpaceSpec(name, tuple(groups), tile=0, tile_sizes=tuple(tiles))
 
 
-def config3(seed_k: int = 3, O: int = 64, V: int = 384) -> Workload:
+def irrep_doubles(seed_k: int = 3, O: int = 64, V: int = 384) -> Workload:
     """Uneven D2h blocks: O=64, V=384 spin-orbitals (other sizes for small cases), irrep counts and
     tile cuts seeded; the vvvv ladder and the ring term (spin and irrep block sparsity)."""
     import numpy as np
@@ -255,7 +257,7 @@ def config3(seed_k: int = 3, O: int = 64, V: int = 384) -> Workload:
     return w
 
 
-def config3_batch_sizes(n: int = 32, seed_k: int = 3, o_range=(16, 64), v_range=(64, 320)) -> list:
+def ladder_batch_sizes(n: int = 32, seed_k: int = 3, o_range=(16, 64), v_range=(64, 320)) -> list:
     """(O, V) of the independent ladder problems: even spin-orbital counts drawn uniformly."""
     import numpy as np
 

@@ -1,4 +1,4 @@
-"""Write tests/golden/oracle_config1.json from the FP64 oracle only.
+"""Write tests/golden/oracle_ladder_o8_v32.json from the FP64 oracle only.
 
 Regression values for the 8/32 spin-orbital ladder (tiles 4/8): norm of R and
 two scalar contractions.  Run from the repository root:
@@ -16,7 +16,7 @@ from tamm_synth import workloads as wl  # noqa: E402
 
 
 def main():
-    w = wl.config1()
+    w = wl.ladder_o8_v32()
     _, T = O.build_workload(w)
     O.run_workload(w, T)
     out = {
@@ -27,7 +27,7 @@ def main():
         "n_blocks_R": int(T["R"].n_blocks),
         "n_elems_V_vvvv": int(T["V_vvvv"].n_elems),
     }
-    with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "oracle_config1.json"), "w") as f:
+    with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "oracle_ladder_o8_v32.json"), "w") as f:
         json.dump(out, f, indent=1)
 
 

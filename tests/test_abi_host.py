@@ -43,9 +43,16 @@ def spaces_for(ctx, w):
             {k: O.Space.from_spec(s) for k, s in w.spaces.items()})
 
 
-@pytest.mark.parametrize("cfg", [1, 2, 4, 5])
-def test_block_tables_match_oracle(hctx, cfg):
-    w = wl.CONFIGS[cfg]()
+@pytest.mark.parametrize("name", sorted(wl.WORKLOADS) + ["irrep_doubles", "irrep_doubles_small", "dense4d"])
+def test_block_tables_match_oracle(hctx, name):
+    if name == "irrep_doubles":
+        w = wl.irrep_doubles()
+    elif name == "irrep_doubles_small":
+        w = wl.irrep_doubles(O=32, V=96)
+    elif name == "dense4d":
+        w = wl.dense4d(40, 16)
+    else:
+        w = wl.WORKLOADS[name]()
     gs, os_ = spaces_for(hctx, w)
     for k in gs:
         assert gs[k].n == os_[k].n
@@ -91,8 +98,8 @@ def test_flop_counts_closed_forms(hctx):
     assert hctx.flops(R, "abij", T, "efij", V, "abef") == hctx.flops(R, "abij", V, "abef", T, "efij")
 
 
-def test_config2_flops(hctx):
-    w = wl.config2()
+def test_doubles_o40_v240_flops(hctx):
+    w = wl.ccsd_doubles_o40_v240()
     gs, _ = spaces_for(hctx, w)
     T = {n: hctx.tensor([gs[m] for m in t.modes], t.n_upper, t.sym) for n, t in w.tensors.items()}
     f = {s.name: hctx.flops(T[s.c], s.lc, T[s.a], s.la, T[s.b], s.lb) for s in w.steps

@@ -1,4 +1,4 @@
-"""Gradients through torch.autograd (config 4: O=32, V=192 spin-orbitals, tiles 16/32).
+"""Gradients through torch.autograd (ladder energy, O=32, V=192 spin-orbitals, tiles 16/32).
 
 E = 1/4 V_oovv(ijab) T'(abij),  T' = T + 1/2 V_vvvv(abef) T(efij).
 
@@ -22,11 +22,11 @@ pytestmark = pytest.mark.gpu
 
 
 @pytest.fixture(scope="module")
-def cfg4():
+def ladder_energy():
     import paper_2201_01257_gb300 as tg
     from paper_2201_01257_gb300 import workload as gw
 
-    w = wl.config4()
+    w = wl.ladder_energy_o32_v192()
     ctx = tg.Context(0)
     gsp, gt = gw.build(ctx, w)
     _, ot = O.build_workload(w)
@@ -82,8 +82,8 @@ def oracle_ref_boxes(ot, n_boxes=96, seed=4):
     return out
 
 
-def test_fp64_gradients_match_oracle_closed_forms(cfg4):
-    ctx, gt, ot = cfg4
+def test_fp64_gradients_match_oracle_closed_forms(ladder_energy):
+    ctx, gt, ot = ladder_energy
     E, g = grads(ctx, gt)
     refs = oracle_ref_boxes(ot)
     for name, boxes in refs.items():
@@ -112,10 +112,10 @@ def gpu_to_oracle_layout_from(G, R, values):
     return out
 
 
-def test_gradients_match_central_differences(cfg4):
+def test_gradients_match_central_differences(ladder_energy):
     import torch
 
-    ctx, gt, ot = cfg4
+    ctx, gt, ot = ladder_energy
     E0, g = grads(ctx, gt)
     rng = np.random.default_rng(64)
     h = 1e-6
@@ -155,8 +155,8 @@ def test_gradients_match_central_differences(cfg4):
 
 
 @pytest.mark.parametrize("precision,tol", [("ozaki_bf16", 1e-10), ("bf16x3", 1e-5)])
-def test_split_precision_gradients(cfg4, precision, tol):
-    ctx, gt, ot = cfg4
+def test_split_precision_gradients(ladder_energy, precision, tol):
+    ctx, gt, ot = ladder_energy
     E64, g64 = grads(ctx, gt)
     E, g = grads(ctx, gt, precision)
     for k in g:
@@ -166,8 +166,8 @@ def test_split_precision_gradients(cfg4, precision, tol):
     assert abs(E - E64) <= tol * abs(E64)
 
 
-def test_recompute_matches_stored(cfg4):
-    ctx, gt, ot = cfg4
+def test_recompute_matches_stored(ladder_energy):
+    ctx, gt, ot = ladder_energy
     E1, g1 = grads(ctx, gt, recompute=False)
     E2, g2 = grads(ctx, gt, recompute=True)
     assert E1 == E2
@@ -175,12 +175,12 @@ def test_recompute_matches_stored(cfg4):
         assert np.array_equal(g1[k], g2[k])
 
 
-def test_generic_functions_match_fused_adjoint(cfg4):
+def test_generic_functions_match_fused_adjoint(ladder_energy):
     import torch
 
     from paper_2201_01257_gb300 import autograd as ga
 
-    ctx, gt, ot = cfg4
+    ctx, gt, ot = ladder_energy
     E1, g1 = grads(ctx, gt)
     T, V, Voo = gt["T"], gt["V_vvvv"], gt["V_oovv"]
     v = V.data.clone().requires_grad_(True)

@@ -1,6 +1,6 @@
 """Autotuner of the split-precision path (slice count and exact-chunk length).
 
-On the config-4 ladder (O=32, V=192, tiles 16/32) and a small doubles ring (output permutation):
+On the O=32 V=192 ladder (tiles 16/32) and a small doubles ring (output permutation):
 * the chosen configuration meets the target against the FP64 oracle itself (not only against the
   GPU's FP64 reference the tuner used), on seeded sub-blocks;
 * a looser target never needs more slices than a tighter one;
@@ -20,11 +20,11 @@ pytestmark = pytest.mark.gpu
 
 
 @pytest.fixture(scope="module")
-def cfg4():
+def ladder_energy():
     import paper_2201_01257_gb300 as tg
     from paper_2201_01257_gb300 import workload as gw
 
-    w = wl.config4()
+    w = wl.ladder_energy_o32_v192()
     ctx = tg.Context(0)
     gsp, gt = gw.build(ctx, w, only={"V_vvvv", "T", "Tp"})
     return tg, ctx, w, gt
@@ -48,8 +48,8 @@ def sampled_error(R_gpu, ot, n=64, seed=11):
     return float(np.sqrt(num / den))
 
 
-def test_autotune_meets_target_and_is_used(cfg4):
-    tg, ctx, w, gt = cfg4
+def test_autotune_meets_target_and_is_used(ladder_energy):
+    tg, ctx, w, gt = ladder_energy
     V, T, R = gt["V_vvvv"], gt["T"], gt["Tp"]
     R.data.fill_(7.0)
     ctx.sync()
@@ -100,8 +100,8 @@ def test_autotune_ring_with_output_permutation(gpu_lib):
         assert rel_err(gpu_to_oracle_layout(gt[name], ot[name]), ot[name].data) <= 1e-10, name
 
 
-def test_autotune_unreachable_target(cfg4):
-    tg, ctx, w, gt = cfg4
+def test_autotune_unreachable_target(ladder_energy):
+    tg, ctx, w, gt = ladder_energy
     with pytest.raises(tg.TammError) as e:
         ctx.autotune(gt["Tp"], "abij", gt["V_vvvv"], "abef", gt["T"], "efij", 1e-30)
     assert e.value.status == tg.TAMM_EUNSUPPORTED
@@ -110,10 +110,10 @@ def test_autotune_unreachable_target(cfg4):
     assert e.value.status == tg.TAMM_EINVAL
 
 
-def test_autotune_refuses_a_zero_product(cfg4):
+def test_autotune_refuses_a_zero_product(ladder_energy):
     import torch
 
-    tg, ctx, w, gt = cfg4
+    tg, ctx, w, gt = ladder_energy
     zero = torch.zeros_like(gt["T"].data)
     Tz = ctx.tensor_permuted(gt["T"], [0, 1, 2, 3], allocate=False)
     Tz.bind(zero)

@@ -1,4 +1,4 @@
-"""Config 5 at full size on the GPU: ladder + ring + oooo, O=80 / V=320 spin-orbitals,
+"""Doubles contractions at full size on the GPU: ladder + ring + oooo, O=80 / V=320 spin-orbitals,
 tiles 40/64 (V_vvvv about 31.5 GB FP64).  The oracle recomputes 256 seeded
 8x8x8x8 sub-blocks of the outputs (seeded over contraction, output block and
 offset); split precision is held to 1e-10 and FP64 to 1e-12 normwise over them.
@@ -13,11 +13,11 @@ pytestmark = [pytest.mark.gpu, pytest.mark.slow]
 
 
 @pytest.fixture(scope="module")
-def cfg5():
+def doubles80():
     import paper_2201_01257_gb300 as tg
     from paper_2201_01257_gb300 import workload as gw
 
-    w = wl.config5()
+    w = wl.ccsd_doubles_o80_v320()
     names = {"V_vvvv", "T", "W0", "V_ovvo"}
     ctx = tg.Context(0)
     gsp, gt = gw.build(ctx, w, only=names | {"R", "X"})
@@ -92,8 +92,8 @@ def oracle_refs(ot, boxes, box=8):
 
 
 @pytest.mark.parametrize("prec,tol", [("ozaki_bf16", 1e-10), ("f64", 1e-12)])
-def test_config5_sampled_sub_blocks(cfg5, prec, tol):
-    ctx, gsp, gt, ot, w, boxes, refs = cfg5
+def test_doubles_o80_v320_sampled_sub_blocks(doubles80, prec, tol):
+    ctx, gsp, gt, ot, w, boxes, refs = doubles80
     R = gt["R"]
     idx = {tuple(t): k for k, t in enumerate(R.block_tiles.tolist())}
     _, ext_all = ot["R"].block_lo_ext()
@@ -112,5 +112,5 @@ def test_config5_sampled_sub_blocks(cfg5, prec, tol):
             num += float(np.sum((sub - ref) ** 2))
             den += float(np.sum(ref ** 2))
         err = np.sqrt(num / den)
-        print(f"config5 {name} {prec}: {len(sel)} boxes, rel err {err:.3e}")
+        print(f"O=80 V=320 {name} {prec}: {len(sel)} boxes, rel err {err:.3e}")
         assert err <= tol, (name, prec, err)

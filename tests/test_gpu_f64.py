@@ -24,8 +24,8 @@ def run_both(tg, w, precision="f64", slices=0):
     return ctx, gt, ot, genergy, oenergy
 
 
-def test_config1_ladder_f64(gpu_lib):
-    ctx, gt, ot, _, _ = run_both(gpu_lib, wl.config1())
+def test_ladder_o8_v32_f64(gpu_lib):
+    ctx, gt, ot, _, _ = run_both(gpu_lib, wl.ladder_o8_v32())
     got = gpu_to_oracle_layout(gt["R"], ot["R"])
     assert rel_err(got, ot["R"].data) <= TOL_F64
     assert np.abs(got - ot["R"].data).max() <= 1e-14 * np.abs(ot["R"].data).max()
@@ -89,12 +89,12 @@ def test_errors(gpu_lib):
     assert e.value.status == tg.TAMM_EINVAL
 
 
-def test_config2_sampled_blocks_f64(gpu_lib):
-    """Full config-2 sizes on the GPU; oracle recomputes sampled 4x4x4x4 boxes of the output."""
+def test_doubles_o40_v240_sampled_blocks_f64(gpu_lib):
+    """Full O=40 V=240 doubles sizes on the GPU; oracle recomputes sampled 4x4x4x4 boxes of the output."""
     tg = gpu_lib
     from paper_2201_01257_gb300 import workload as gw
 
-    w = wl.config2()
+    w = wl.ccsd_doubles_o40_v240()
     ctx = tg.Context(0)
     gsp, gt = gw.build(ctx, w, only={"V_vvvv", "T", "R"})
     step = w.steps[0]

@@ -1,4 +1,4 @@
-"""Config 3: uneven D2h blocks (O=64, V=384 spin-orbitals; irrep counts and tile cuts seeded, tiles
+"""Uneven D2h blocks (O=64, V=384 spin-orbitals; irrep counts and tile cuts seeded, tiles
 8..96 per (spin, irrep) group), spin and irrep block sparsity.
 
 * The vvvv ladder and the ring term run as one contraction group (one grouped tcgen05 launch over
@@ -24,13 +24,13 @@ BOX = 4
 
 
 @pytest.fixture(scope="module")
-def cfg3():
+def irrep():
     import torch
 
     import paper_2201_01257_gb300 as tg
     from paper_2201_01257_gb300 import workload as gw
 
-    w = wl.config3()
+    w = wl.irrep_doubles()
     stream = torch.cuda.Stream(0)
     ctx = tg.Context(0, stream=stream)
     with torch.cuda.stream(stream):
@@ -109,28 +109,28 @@ def run_step(ctx, stream, runner, prec, grouped):
 
 
 @pytest.mark.parametrize("prec,tol,grouped", [("ozaki_bf16", 1e-10, True), ("f64", 1e-12, False)])
-def test_config3_matches_oracle(cfg3, prec, tol, grouped):
-    ctx, stream, runner, ot, boxes, refs = cfg3
+def test_irrep_doubles_match_oracle(irrep, prec, tol, grouped):
+    ctx, stream, runner, ot, boxes, refs = irrep
     R, R2 = run_step(ctx, stream, runner, prec, grouped)
     G = runner.tensors["R"]
     for name, got in (("ladder", R), ("ring", R2)):
         err = box_error(G, ot["R"], got, boxes, refs, name)
-        print(f"config3 {name} {prec}: rel err {err:.3e}")
+        print(f"irrep {name} {prec}: rel err {err:.3e}")
         assert err <= tol, (name, prec, err)
 
 
-def test_grouped_equals_separate_bitwise(cfg3):
-    ctx, stream, runner, ot, boxes, refs = cfg3
+def test_grouped_equals_separate_bitwise(irrep):
+    ctx, stream, runner, ot, boxes, refs = irrep
     a = run_step(ctx, stream, runner, "ozaki_bf16", False)
     b = run_step(ctx, stream, runner, "ozaki_bf16", True)
     for x, y in zip(a, b):
         assert np.array_equal(x, y)
 
 
-def test_graph_replay_equals_eager(cfg3):
+def test_graph_replay_equals_eager(irrep):
     import torch
 
-    ctx, stream, runner, ot, boxes, refs = cfg3
+    ctx, stream, runner, ot, boxes, refs = irrep
     T = runner.tensors
     eager = run_step(ctx, stream, runner, "ozaki_bf16", True)  # also creates every plan and the scratch
     n0 = ctx.launch_count()
@@ -163,12 +163,12 @@ def test_graph_replay_equals_eager(cfg3):
     g.destroy()
 
 
-def test_group_and_capture_refusals(cfg3):
+def test_group_and_capture_refusals(irrep):
     import torch
 
     import paper_2201_01257_gb300 as tg
 
-    ctx, stream, runner, ot, boxes, refs = cfg3
+    ctx, stream, runner, ot, boxes, refs = irrep
     T = runner.tensors
     # an add inside a group, an FP64 contraction inside a group
     ctx.group_begin()
@@ -199,13 +199,13 @@ def test_group_and_capture_refusals(cfg3):
     ctx.sync()
 
 
-def test_scaled_batch_in_one_graph(cfg3):
+def test_scaled_batch_in_one_graph(irrep):
     import torch
 
     import paper_2201_01257_gb300 as tg
     from paper_2201_01257_gb300 import workload as gw
 
-    sizes = [(max(4, o // 2), max(8, v // 4)) for o, v in wl.config3_batch_sizes()]
+    sizes = [(max(4, o // 2), max(8, v // 4)) for o, v in wl.ladder_batch_sizes()]
     sizes = [(o + o % 2, v + v % 2) for o, v in sizes]
     stream = torch.cuda.Stream(0)
     ctx = tg.Context(0, stream=stream)

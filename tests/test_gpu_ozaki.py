@@ -29,8 +29,8 @@ def run_both(tg, w, precision="ozaki_bf16", slices=0):
     return ctx, gt, ot, ge, oe
 
 
-def test_config1_ladder_ozaki(gpu_lib):
-    _, gt, ot, _, _ = run_both(gpu_lib, wl.config1())
+def test_ladder_o8_v32_ozaki(gpu_lib):
+    _, gt, ot, _, _ = run_both(gpu_lib, wl.ladder_o8_v32())
     err = rel_err(gpu_to_oracle_layout(gt["R"], ot["R"]), ot["R"].data)
     assert err <= TOL, err
 
@@ -125,11 +125,11 @@ def test_error_decreases_with_slices(gpu_lib):
     assert errs[3] <= TOL and max(errs[3:]) <= 1e-11, errs
 
 
-def test_config2_sampled_ladder_ozaki(gpu_lib):
+def test_doubles_o40_v240_sampled_ladder_ozaki(gpu_lib):
     tg = gpu_lib
     from paper_2201_01257_gb300 import workload as gw
 
-    w = wl.config2()
+    w = wl.ccsd_doubles_o40_v240()
     ctx = tg.Context(0)
     _, gt = gw.build(ctx, w, only={"V_vvvv", "T", "R"})
     ctx.contract(0.5, gt["R"], "abij", 0.0, gt["V_vvvv"], "abef", gt["T"], "efij", "ozaki_bf16", 0)
@@ -157,7 +157,7 @@ def test_bad_slice_count(gpu_lib):
     from paper_2201_01257_gb300 import workload as gw
 
     ctx = tg.Context(0)
-    _, t = gw.build(ctx, wl.config1())
+    _, t = gw.build(ctx, wl.ladder_o8_v32())
     with pytest.raises(tg.TammError) as e:
         ctx.contract(0.5, t["R"], "abij", 0.0, t["V_vvvv"], "abef", t["T"], "efij", "ozaki_bf16", 12)
     assert e.value.status == tg.TAMM_EINVAL

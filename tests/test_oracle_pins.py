@@ -56,7 +56,7 @@ def test_spin_storage_fraction_three_eighths(n, tile):
     assert V.n_elems * 8 == 3 * n ** 4
 
 
-def test_config5_vvvv_storage_31gb():
+def test_vvvv_storage_o80_v320_31gb():
     # O=80 / V=320 spin-orbitals, virtual tile 64: the stored V_vvvv is about 31 GB.
     v = spin_space(320, 64)
     V = O.Tensor([v] * 4, 2, "spin", alloc=False)
@@ -107,8 +107,8 @@ def small():
     return w, T
 
 
-def test_ladder_matches_dense_einsum_config1():
-    w = wl.config1()
+def test_ladder_o8_v32_matches_dense_einsum():
+    w = wl.ladder_o8_v32()
     _, T = O.build_workload(w)
     O.run_workload(w, T)
     ref = 0.5 * np.einsum("abef,efij->abij", T["V_vvvv"].to_dense(), T["T"].to_dense())
@@ -393,8 +393,8 @@ def test_paper_printed_tiling_example():
 def test_oracle_regression_values():
     import json
 
-    g = json.load(open(os.path.join(HERE, "golden", "oracle_config1.json")))
-    w = wl.config1()
+    g = json.load(open(os.path.join(HERE, "golden", "oracle_ladder_o8_v32.json")))
+    w = wl.ladder_o8_v32()
     _, T = O.build_workload(w)
     O.run_workload(w, T)
     assert abs(O.norm(T["R"]) - g["norm_R"]) <= 1e-13 * g["norm_R"]
