@@ -794,6 +794,37 @@ def run_dense4d_case(args) -> dict:
     return out
 
 
+def run_doubles_term_case(args) -> dict:
+    """One contraction of the doubles recipe at a chosen size (tiles 20/40), split precision (6 slices):
+    small cases for profiling a single term."""
+    import torch
+
+    import paper_2201_01257_gb300 as tg
+    from paper_2201_01257_gb300 import workload as gw
+    from tamm_synth import workloads as wl
+
+    O_, V_, name = args.term.split(",")
+    w = wl._doubles(wl._vt(2, int(O_), int(V_), 20, 40, f"ccsd_doubles_O{O_}_V{V_}"))
+    w.steps = wl.doubles_steps()
+    ctx = tg.Context(0)
+    sp, T = gw.build(ctx, w)
+    run = gw.Runner(ctx, w, sp, T)
+    run.run("f64")
+    st = next(x for x in w.steps if x.name == name)
+    for _ in range(max(1, args.warmup)):
+        run.run("ozaki_bf16", SLICES, steps=[st])
+    ctx.sync()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        run.run("ozaki_bf16", SLICES, steps=[st])
+    e1.record()
+    ctx.sync()
+    ms = e0.elapsed_time(e1) / args.steps
+    return {"case": f"{w.name} {name}, split precision", "ms": round(ms, 3),
+            "TFLOP/s": round(run.flops(st) / ms / 1e9, 3), "nonzero_block_flops": run.flops(st)}
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -810,6 +841,7 @@ def main():
     ap.add_argument("--batch", action="store_true", help="time the 32 independent ladders in sub-batches instead")
     ap.add_argument("--doubles-o80", action="store_true", help="time the O=80 V=320 contractions alone instead")
     ap.add_argument("--dense4d", default="", help="N,tile: time the dense 4-D contraction instead")
+    ap.add_argument("--term", default="", help="O,V,name: time one doubles contraction of that size instead")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -823,6 +855,8 @@ def main():
         out = run_doubles_o80_case(args)
     elif args.dense4d:
         out = run_dense4d_case(args)
+    elif args.term:
+        out = run_doubles_term_case(args)
     elif args.impl == "reference":
         out = run_reference(args, rank)
     else:

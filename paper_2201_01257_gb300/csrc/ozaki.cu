@@ -2,6 +2,7 @@
 // kernel and the host plan that drives them.  The arithmetic scheme is
 // described in ozaki.h.
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 #include <map>
 
@@ -372,6 +373,26 @@ __device__ __forceinline__ float pow2f(int d) {
   return d < -126 ? 0.0f : __int_as_float((127 + d) << 23);
 }
 
+// x * 2^s as a double, exactly, built from the bits of the float x with integer operations (GB300's
+// FP64 pipe is narrow, and the output stage would otherwise spend most of its time there); `neg`
+// flips the sign.  False when x is subnormal, infinite or NaN, or the result leaves the normal
+// range: the caller then takes the FP64 route.
+__device__ __forceinline__ bool f2d_scaled(float x, int s, bool neg, double& out) {
+  const uint32_t u = __float_as_uint(x);
+  const unsigned long long sign = ((unsigned long long)(u >> 31) ^ (neg ? 1ull : 0ull)) << 63;
+  const uint32_t a = u & 0x7FFFFFFFu;
+  if (a == 0u) {
+    out = __longlong_as_double((long long)sign);
+    return true;
+  }
+  const int e = (int)(a >> 23);
+  const int de = e - 127 + 1023 + s;
+  if (e == 0 || e == 255 || de <= 0 || de >= 2047) return false;
+  out = __longlong_as_double(
+      (long long)(sign | ((unsigned long long)de << 52) | ((unsigned long long)(a & 0x7FFFFFu) << 29)));
+  return true;
+}
+
 __device__ __forceinline__ double pow2d(int d) {
   if (d < -1022) return 0.0;
   if (d > 1023) return __longlong_as_double(0x7FF0000000000000ll);
@@ -717,8 +738,12 @@ __global__ void __launch_bounds__(kThreads, 1) ozaki_gemm_kernel(const __grid_co
             const int col = c0 + j;
             if (col < n_valid) {
               double v = 0.0;
-              if (Eref != kOzExpZero && fref[col] != kOzExpZero)
-                v = ((double)hi[j] + (double)lo[j]) * pow2d(Eref + fref[col] - 12);
+              if (Eref != kOzExpZero && fref[col] != kOzExpZero) {
+                const int sc = Eref + fref[col] - 12;
+                double dh, dl;
+                if (f2d_scaled(hi[j], sc, false, dh) && f2d_scaled(lo[j], sc, false, dl)) v = dh + dl;
+                else v = ((double)hi[j] + (double)lo[j]) * pow2d(sc);
+              }
               wrow[col] = v;
             }
           }
@@ -729,15 +754,27 @@ __global__ void __launch_bounds__(kThreads, 1) ozaki_gemm_kernel(const __grid_co
           double* crow = c + g.c_off + (int64_t)grow * g.N + (int64_t)it.nt * H;
           const double alpha = p.problems[q].alpha, beta = p.problems[q].beta;
           const bool panel = g.colmap >= 0;
+          // alpha = +-2^ae folds into the exponent: alpha 2^sc (hi + lo) costs one FP64 add, and
+          // C + that one more; the result is the same rounding as the FP64 route below
+          const int ae = p.problems[q].alpha_exp;
+          const bool a_p2 = p.problems[q].alpha_pow2 != 0, a_neg = alpha < 0.0;
 #pragma unroll
           for (int j = 0; j < 64; ++j) {
             const int col = c0 + j;
             if (col < n_valid) {
-              double v = 0.0;
-              if (Eref != kOzExpZero && fref[col] != kOzExpZero)
-                v = ((double)hi[j] + (double)lo[j]) * pow2d(Eref + fref[col] - 12);
+              double av = 0.0;  // alpha * (product)
+              if (Eref != kOzExpZero && fref[col] != kOzExpZero) {
+                const int sc = Eref + fref[col] - 12;
+                double dh, dl;
+                if (a_p2 && f2d_scaled(hi[j], sc + ae, a_neg, dh) && f2d_scaled(lo[j], sc + ae, a_neg, dl))
+                  av = dh + dl;
+                else
+                  av = alpha * (((double)hi[j] + (double)lo[j]) * pow2d(sc));
+              } else {
+                av = alpha * 0.0;
+              }
               double* cp = panel ? c + col_base[col] + (int64_t)grow * col_stride[col] : crow + col;
-              *cp = beta != 0.0 ? fma(beta, *cp, alpha * v) : alpha * v;
+              *cp = beta != 0.0 ? fma(beta, *cp, av) : av;
             }
           }
         }
@@ -1315,6 +1352,12 @@ void execute_ozaki(tamm_ctx* ctx, const std::vector<OzOpRecord>& ops) {
     pr.ws = (double*)(s + p->off_ws);
     pr.c = p->perm_out ? (double*)(s + p->off_x) : ops[i].c;
     pr.alpha = ops[i].alpha;
+    {
+      int e = 0;
+      const double m = std::frexp(ops[i].alpha, &e);
+      pr.alpha_pow2 = (m == 0.5 || m == -0.5) ? 1 : 0;  // alpha = +-2^(e-1)
+      pr.alpha_exp = pr.alpha_pow2 ? e - 1 : 0;
+    }
     pr.beta = p->perm_out ? 0.0 : ops[i].beta;
     counts[i] = p->n_items;
   }

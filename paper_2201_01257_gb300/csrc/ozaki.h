@@ -107,6 +107,8 @@ struct OzProblem {
   int64_t item_begin;
   double* c;
   double alpha, beta;
+  int32_t alpha_pow2;  // alpha = +-2^alpha_exp (then folded into the output scaling)
+  int32_t alpha_exp;
 };
 constexpr int kOzMaxProblems = 64;  // problems per launch (kernel-parameter table)
 
