@@ -15,6 +15,31 @@ struct Alpha4 {
   double v[kMaxAddTerms];
 };
 
+// Mixed-radix digits (row-major over dim[0..nm)) of the element index x and
+// of the thread stride q; the loops below then step the digits by q with one
+// carry pass per element instead of dividing.  Blocks hold < 2^31 elements.
+struct Digits {
+  int32_t idx[kMaxKernelModes], stp[kMaxKernelModes];
+};
+
+__device__ __forceinline__ void digits_init(const AddBlock& B, int32_t x, int32_t q, Digits& d) {
+  for (int m = B.nm - 1; m >= 0; --m) {
+    d.idx[m] = x % B.dim[m];
+    x /= B.dim[m];
+    d.stp[m] = q % B.dim[m];
+    q /= B.dim[m];
+  }
+}
+
+__device__ __forceinline__ void digits_step(const AddBlock& B, Digits& d) {
+  int32_t carry = 0;
+  for (int m = B.nm - 1; m >= 0; --m) {
+    int32_t v = d.idx[m] + d.stp[m] + carry;
+    carry = v >= B.dim[m] ? 1 : 0;
+    d.idx[m] = carry ? v - B.dim[m] : v;
+  }
+}
+
 // dst = beta*dst + sum_t alpha_t * src(perm_t), one chunk of one block per CTA.
 __global__ void __launch_bounds__(256) add_kernel(double* __restrict__ dst, const double* __restrict__ src,
                                                   const AddBlock* __restrict__ blocks,
@@ -24,13 +49,10 @@ __global__ void __launch_bounds__(256) add_kernel(double* __restrict__ dst, cons
   const AddBlock& B = blocks[it.block];
   const int64_t end = min(B.n, it.start + (int64_t)kChunk);
   const int nm = B.nm;
-  for (int64_t e = it.start + threadIdx.x; e < end; e += blockDim.x) {
-    int32_t idx[kMaxKernelModes];
-    int64_t r = e;
-    for (int m = nm - 1; m >= 0; --m) {
-      idx[m] = (int32_t)(r % B.dim[m]);
-      r /= B.dim[m];
-    }
+  Digits dg;
+  digits_init(B, (int32_t)(it.start + threadIdx.x), (int32_t)blockDim.x, dg);
+  for (int64_t e = it.start + threadIdx.x; e < end; e += blockDim.x, digits_step(B, dg)) {
+    const int32_t* idx = dg.idx;
     double acc = 0.0;
     for (int t = 0; t < n_terms; ++t) {
       if (B.src_off[t] < 0) continue;
@@ -70,12 +92,11 @@ __global__ void __launch_bounds__(256) energy_partials_kernel(const double* __re
   const int nm = B.nm;
   double acc = 0.0;
   if (B.src_off[0] >= 0) {
-    for (int64_t e = it.start + threadIdx.x; e < end; e += blockDim.x) {
-      int64_t r = e, s = B.src_off[0];
-      for (int m = nm - 1; m >= 0; --m) {
-        s += (r % B.dim[m]) * (int64_t)B.sstride[0][m];
-        r /= B.dim[m];
-      }
+    Digits dg;
+    digits_init(B, (int32_t)(it.start + threadIdx.x), (int32_t)blockDim.x, dg);
+    for (int64_t e = it.start + threadIdx.x; e < end; e += blockDim.x, digits_step(B, dg)) {
+      int64_t s = B.src_off[0];
+      for (int m = 0; m < nm; ++m) s += (int64_t)dg.idx[m] * B.sstride[0][m];
       acc = fma(a[B.dst_off + e], b[s], acc);
     }
   }

@@ -66,6 +66,7 @@ std::vector<AddBlock> build_add_blocks(const tamm_tensor& D, const char* ld, con
     const int64_t* dt = &D.tiles[(size_t)(b * D.nm)];
     ab.dst_off = D.off[(size_t)b];
     ab.n = D.block_size(b);
+    if (ab.n >= (int64_t(1) << 31)) throw Error(TAMM_EUNSUPPORTED, "add: a block of 2^31 or more elements");
     ab.nm = D.nm;
     for (int m = 0; m < D.nm; ++m) ab.dim[m] = (int32_t)D.sp[m]->size[(size_t)dt[m]];
     for (int t = 0; t < kMaxAddTerms; ++t) ab.src_off[t] = -1;
