@@ -22,57 +22,57 @@ __host__ __device__ constexpr unsigned long long digit_bias(int S) {
   return b;
 }
 
-__host__ __device__ constexpr float pow2_neg7(int k) {
-  float f = 1.0f;
+// 2^(23-7k) + (k > 0 ? 64 : 0) 2^(-7k), exact in FP32
+__host__ __device__ constexpr float slice_offset(int k) {
+  float f = k == 0 ? 8388608.0f : 8388672.0f;
   for (int i = 0; i < 7 * k; ++i) f *= 0.5f;
   return f;
 }
 
-// Slice values of x for row exponent e: v_k = d_k 2^(-7k), k = 0..S-1, where
-// d_0 (6 bits) and the balanced base-2^7 digits d_1..d_{S-1} (|d| <= 64)
-// represent round(|x| 2^(7S-1-e)) with the sign of x.  F = round(|x|
-// 2^(7S-1-e)) comes from the FP64 bit pattern; adding 64 to every lower
-// digit position, G = F + 64 (1 + 2^7 + ... + 2^(7(S-2))), turns the
-// balanced digits into plain 7-bit fields, d_k = field_k(G) - 64 (k >= 1),
-// d_0 = G >> 7(S-1).  A field becomes an exact float through the 2^23
-// bit-pattern trick, and the scaling by +-2^(-7k) is exact (at most 7
-// significant bits), so every value is also an exact BF16.
+// Slice values of |x| for row exponent e, as float bit patterns: |x| carries
+// v_k = d_k 2^(-7k), k = 0..S-1, where d_0 (6 bits) and the balanced base-2^7
+// digits d_1..d_{S-1} (|d| <= 64) represent F = round(|x| 2^(7S-1-e)).  F
+// comes from the FP64 bit pattern; adding 64 to every lower digit position,
+// G = F + 64 (1 + 2^7 + ... + 2^(7(S-2))), turns the balanced digits into
+// plain 7-bit fields, d_k = field_k(G) - 64 (k >= 1), d_0 = G >> 7(S-1).  A
+// field placed in the mantissa of 2^(23-7k) gives 2^(23-7k) + field 2^(-7k)
+// exactly; one float subtraction of 2^(23-7k) + 64 2^(-7k) leaves v_k, an
+// exact BF16 (at most 7 significant bits).  The sign of x is applied by the
+// caller to the packed BF16 pairs.
 template <int S>
-__device__ __forceinline__ void slice_values(double x, int e, float (&v)[S]) {
+__device__ __forceinline__ void slice_magnitudes(double x, int e, uint32_t (&v)[S]) {
   const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
-  int E = (int)((bits >> 52) & 0x7FF);
-  unsigned long long M = bits & ((1ull << 52) - 1);
-  if (E == 0) E = 1; else M |= 1ull << 52;
-  const int shift = E - 1075 + 7 * S - 1 - e;
+  const int Eb = (int)((bits >> 52) & 0x7FF);
+  const unsigned long long M = (bits & ((1ull << 52) - 1)) | ((unsigned long long)(Eb != 0) << 52);
+  const int shift = max(Eb, 1) - 1075 + 7 * S - 1 - e;
   unsigned long long F = 0;
-  if (M != 0 && shift > -63) {
-    if (shift >= 0) {
-      F = M << shift;
-    } else {
-      const int rs = -shift;
-      F = (M >> rs) + ((M >> (rs - 1)) & 1ull);
-    }
+  // a left shift only for S = 8 or subnormal x (a normal |x| <= 2^e gives shift <= 7S - 54)
+  if (shift >= 0) F = M << shift;
+  if (shift < 0 && shift > -63) {
+    const int rs = -shift;
+    F = (M + (1ull << (rs - 1))) >> rs;  // round half up
   }
   constexpr unsigned long long kBias = digit_bias(S);
   const unsigned long long G = F + kBias;
-  const float sgn = (bits >> 63) ? -1.0f : 1.0f;
 #pragma unroll
   for (int k = 0; k < S; ++k) {
     const int sh = 7 * (S - 1 - k);
     const uint32_t field = k == 0 ? (uint32_t)(G >> sh) : (uint32_t)(G >> sh) & 127u;
-    const float d = __fsub_rn(__uint_as_float(0x4B000000u | field), k == 0 ? 8388608.0f : 8388672.0f);
-    v[k] = __fmul_rn(d, sgn * pow2_neg7(k));
+    const float top = __uint_as_float((uint32_t)(150 - 7 * k) << 23 | field);
+    v[k] = __float_as_uint(__fsub_rn(top, slice_offset(k)));
   }
 }
 
 // BF16 pairs of the slice values of two adjacent elements: x0 in the low half of each word.
 template <int S>
 __device__ __forceinline__ void pack_digits(const double x0, const double x1, int e, uint32_t (&w)[S]) {
-  float v0[S], v1[S];
-  slice_values<S>(x0, e, v0);
-  slice_values<S>(x1, e, v1);
+  uint32_t v0[S], v1[S];
+  slice_magnitudes<S>(x0, e, v0);
+  slice_magnitudes<S>(x1, e, v1);
+  const uint32_t sign = (uint32_t)((unsigned long long)__double_as_longlong(x0) >> 63) << 15 |
+                        (uint32_t)((unsigned long long)__double_as_longlong(x1) >> 63) << 31;
 #pragma unroll
-  for (int k = 0; k < S; ++k) w[k] = __byte_perm(__float_as_uint(v0[k]), __float_as_uint(v1[k]), 0x7632);
+  for (int k = 0; k < S; ++k) w[k] = __byte_perm(v0[k], v1[k], 0x7632) ^ sign;
 }
 
 __device__ __forceinline__ int64_t mixed_offset(int32_t idx, int n, const int32_t* dim, const int32_t* stride) {
