@@ -5,6 +5,7 @@
 #include <cmath>
 #include <cstring>
 #include <map>
+#include <mutex>
 
 #include "ozaki.h"
 #include "sm100.cuh"
@@ -813,16 +814,24 @@ __global__ void __launch_bounds__(256) ozaki_reduce_kernel(const OzReduceItem* _
 // Launchers
 // ======================================================================
 
+// Kernel attributes are per device: the one-time setup is tracked per device ordinal.
+constexpr int kMaxDevices = 64;
+static std::mutex g_attr_mutex;
+
 template <int S, bool kFloat = false>
 static cudaError_t slice_dispatch(tamm_ctx* ctx, const double* src, const SliceBlock* blocks, const SliceItem* items,
                                   int64_t n_items, uint8_t* tiles, int32_t* exps, int warps, int kbuf) {
-  static size_t attr_bytes = 0;  // dynamic shared memory opted in so far (per instantiation)
+  static size_t attr_bytes[kMaxDevices] = {};  // dynamic shared memory opted in so far, per device
   const size_t smem = (size_t)warps * kbuf * sizeof(double);
-  if (smem > attr_bytes) {
-    cudaError_t e = cudaFuncSetAttribute(ozaki_slice_kernel<S, kFloat>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
-    if (e != cudaSuccess) return e;
-    attr_bytes = smem;
+  if (ctx->device < 0 || ctx->device >= kMaxDevices) return cudaErrorInvalidDevice;
+  {
+    std::lock_guard<std::mutex> lock(g_attr_mutex);
+    if (smem > attr_bytes[ctx->device]) {
+      cudaError_t e = cudaFuncSetAttribute(ozaki_slice_kernel<S, kFloat>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+      attr_bytes[ctx->device] = smem;
+    }
   }
   const int bulk = (reinterpret_cast<uintptr_t>(src) & 15) == 0 ? 1 : 0;
   ozaki_slice_kernel<S, kFloat><<<(unsigned)n_items, 32 * warps, smem, ctx->stream>>>(src, blocks, items, tiles,
@@ -864,17 +873,21 @@ static size_t oz_smem_bytes(int S) {
 
 template <int S>
 static cudaError_t gemm_dispatch(tamm_ctx* ctx, const OzParams& p, int grid) {
-  static int ready = 0;
+  static bool ready[kMaxDevices] = {};
   const size_t smem = oz_smem_bytes(S);
-  if (!ready) {
-    cudaFuncAttributes fa;
-    cudaError_t e = cudaFuncGetAttributes(&fa, ozaki_gemm_kernel<S>);
-    if (e != cudaSuccess) return e;
-    // setmaxnreg.inc would wait forever if the launch pool were too small
-    if (fa.numRegs < kRegsLaunchNeeded) return cudaErrorLaunchOutOfResources;
-    e = cudaFuncSetAttribute(ozaki_gemm_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    ready = 1;
+  if (ctx->device < 0 || ctx->device >= kMaxDevices) return cudaErrorInvalidDevice;
+  {
+    std::lock_guard<std::mutex> lock(g_attr_mutex);
+    if (!ready[ctx->device]) {
+      cudaFuncAttributes fa;
+      cudaError_t e = cudaFuncGetAttributes(&fa, ozaki_gemm_kernel<S>);
+      if (e != cudaSuccess) return e;
+      // setmaxnreg.inc would wait forever if the launch pool were too small
+      if (fa.numRegs < kRegsLaunchNeeded) return cudaErrorLaunchOutOfResources;
+      e = cudaFuncSetAttribute(ozaki_gemm_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+      ready[ctx->device] = true;
+    }
   }
   ozaki_gemm_kernel<S><<<(unsigned)grid, kThreads, smem, ctx->stream>>>(p);
   return cudaGetLastError();
@@ -901,7 +914,7 @@ cudaError_t launch_ozaki_gemm(tamm_ctx* ctx, OzProblem* problems, const int64_t*
     n_items += n_items_per_problem[i];
   }
   if (n_items == 0) return cudaSuccess;
-  static OzParams p;  // large parameter block; copied into the launch
+  OzParams p{};  // the whole problem table travels as the kernel's parameter block
   p.n_items = n_items;
   p.status = ctx->d_status;
   p.stages = oz_stages(S);
