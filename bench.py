@@ -34,6 +34,8 @@ if ROOT not in sys.path:
 
 METRIC = "block-sparse contraction TFLOP/s: split-precision vs FP64, rel err ≤1e-10"
 UNIT = "TFLOP/s"
+WORKLOAD = ("ccsd_doubles_O40_V240: vvvv ladder + W copy + intermediate + oooo ladder + ring with P(ab)P(ij) + "
+            "T1 term + energy")
 SLICES = 6
 # DRAM bytes (read + write) per launch of the split-precision GEMM kernel, averaged over the five GEMM
 # launches of an O=40 V=240 doubles step, from the ncu launch list of this bench command (profiles/
@@ -355,8 +357,7 @@ def run_ours(args, rank: int, world: int) -> dict | None:
         "dtype": "bf16 slices (f32 accumulate, f64 reconstruct)",
         "data": "synthetic (seeded Philox normals, antisymmetrised; V~N(0,0.1), T~N(0,0.01))",
         "config": {
-            "workload": "ccsd_doubles_O40_V240: vvvv ladder + W copy + intermediate + oooo ladder + ring with "
-                        "P(ab)P(ij) + T1 term + energy",
+            "workload": WORKLOAD,
             "O": 40, "V": 240, "tiles": [20, 40], "symmetry": "spin",
             "precision": "ozaki_bf16",
             "slices": ({k: v["slices"] for k, v in tuned.items()} if tuned else oz_slices),
@@ -526,11 +527,11 @@ def run_reference(args, rank: int) -> dict | None:
     value = fl / (ms * 1e-3) / 1e12
     sample = (f"FP64 oracle on seeded 4x4x4x4 sub-boxes of output blocks of the five contractions of "
               f"ccsd_doubles_O40_V240 ({fl:.3e} nonzero-block flops per step)")
-    return {"impl": "reference", "metric": METRIC, "value": round(value, 6), "unit": UNIT, "n_gpus": 0,
+    return {"impl": "reference", "metric": METRIC, "value": round(value, 6), "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 2), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "ccsd_doubles_O40_V240 (bounded sample per step)", "O": 40, "V": 240,
-                       "tiles": [20, 40], "precision": "f64 (CPU oracle)"},
+            "config": {"workload": WORKLOAD, "O": 40, "V": 240, "tiles": [20, 40], "symmetry": "spin",
+                       "precision": "f64 (CPU oracle; each step a bounded sample of the workload, see cpu_baseline)"},
             "cpu_baseline": {"value": round(value, 6), "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": round(value, 6), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
