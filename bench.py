@@ -169,7 +169,7 @@ def run_ours(args, rank: int, world: int) -> dict | None:
         h = torch.empty(t.n_elems, dtype=torch.float64, pin_memory=True)
         lo, ext = t.block_lo_ext()
         tamm_synth.fill_boxes(w.seed, spec.stream, spec.sigma, [m.n for m in t.modes], spec.anti01, spec.anti23,
-                              lo, ext, t.block_offsets, h.numpy())
+                              lo, ext, t.block_offsets, h.numpy(), sym01=spec.sym01)
         host[name] = h
         ctx.copy_from_host(t, h.numpy())
     ctx.sync()
@@ -479,7 +479,7 @@ def oracle_sample(w, target_flops: float, seed: int = 0, box: int = 4):
         lo, ext = X.block_lo_ext()
         idx = np.array(sorted(blocks))
         tamm_synth.fill_boxes(w.seed, spec.stream, spec.sigma, X.dense_shape(), spec.anti01, spec.anti23,
-                              lo[idx], ext[idx], X.block_off[idx], X.data)
+                              lo[idx], ext[idx], X.block_off[idx], X.data, sym01=spec.sym01)
     return T, plan, total
 
 

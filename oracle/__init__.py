@@ -34,7 +34,9 @@ def build(force: bool = False) -> str:
     """Compile the oracle (gcc, OpenMP) next to its source."""
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", _SRC, "-o", tmp, "-lm"])
+        # no fused multiply-add contraction: every product and sum is rounded as written, on any host
+        subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fopenmp", "-fPIC", "-shared", _SRC, "-o", tmp,
+                               "-lm"])
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -72,6 +74,7 @@ def _load(path: str | None = None):
             L.oracle_energy.argtypes = [d, vp, cp, vp, cp, dp, dp, dp]
             L.oracle_norm.argtypes = [vp, dp]
             L.oracle_norm.restype = d
+            L.oracle_cholesky_v.argtypes = [vp, vp, dp, dp, i64p, i64]
             if path is not None:
                 return L
             _lib = L
@@ -219,7 +222,7 @@ class Tensor:
             return
         lo, ext = self.block_lo_ext()
         tamm_synth.fill_boxes(seed, spec.stream, spec.sigma, self.dense_shape(), spec.anti01, spec.anti23,
-                              lo, ext, self.block_off, self.data)
+                              lo, ext, self.block_off, self.data, sym01=spec.sym01)
 
 
 def _chk(rc: int, what: str) -> None:
@@ -285,6 +288,16 @@ def norm(T: Tensor) -> float:
     return _load().oracle_norm(T._h, _pd(T.data))
 
 
+def cholesky_v(V: Tensor, X: Tensor, blocks=None) -> None:
+    """V[p,q,r,s] = sum_L X[p,r,L] X[q,s,L] - X[p,s,L] X[q,r,L] (Eq. cc12) into the listed stored blocks of V
+    (every block by default), in place on V.data; X has modes (P, R, aux), V modes (P, P, R, R)."""
+    if blocks is None:
+        _chk(_load().oracle_cholesky_v(V._h, X._h, _pd(X.data), _pd(V.data), None, 0), "cholesky_v")
+    else:
+        bl = _i64(blocks)
+        _chk(_load().oracle_cholesky_v(V._h, X._h, _pd(X.data), _pd(V.data), _p(bl), len(bl)), "cholesky_v")
+
+
 def antisymmetrize_add(R: Tensor, lr: str, X: Tensor, alpha: float = 1.0) -> None:
     """R(abij) += alpha * P(ab)P(ij) X = alpha*(X(abij) - X(baij) - X(abji) + X(baji))."""
     a, b, i, j = lr
@@ -297,13 +310,17 @@ def antisymmetrize_add(R: Tensor, lr: str, X: Tensor, alpha: float = 1.0) -> Non
 # ---------------------------------------------------------------- workloads
 
 def build_workload(w: wl.Workload, fill: bool = True):
+    """Spaces and tensors of a recipe; a tensor formed from Cholesky vectors is stored here in full."""
     spaces = {k: Space.from_spec(s) for k, s in w.spaces.items()}
     tensors = {}
     for name, t in w.tensors.items():
         T = Tensor([spaces[m] for m in t.modes], t.n_upper, t.sym)
-        if fill:
+        if fill and not t.cholesky:
             T.fill_synthetic(w.seed, t)
         tensors[name] = T
+    for name, t in w.tensors.items():
+        if fill and t.cholesky:
+            cholesky_v(tensors[name], tensors[t.cholesky])
     return spaces, tensors
 
 

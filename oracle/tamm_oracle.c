@@ -24,6 +24,8 @@
  *       C(lc) = beta*C + alpha * A(la)           (AddOp with label permutation)
  *       E     = alpha * sum A(la) * B(lb)        (full contraction to a scalar)
  *       ||T||  Frobenius norm over stored entries (utility norm)
+ *   - Cholesky-built two-electron tensor (Eq. cc12): V[p,q,r,s] from the
+ *     Cholesky vectors X[p,r,L], for the on-the-fly ("lambda") tensor.
  *     beta is 0 for "=" and 1 for "+=" ("-=" is a negative alpha).
  *
  * Summation order is fixed: contracted tile tuples in lexicographic order
@@ -572,4 +574,59 @@ double oracle_norm(const otensor* T, const double* x) {
   double s = 0.0;
   for (int64_t e = 0; e < T->n_elems; ++e) s += x[e] * x[e];
   return sqrt(s);
+}
+
+/* ---------------------------------------------------- Cholesky-built tensor */
+
+/*
+ * Two-electron tensor from Cholesky vectors (Eq. cc12; the "lambda tensor" of
+ * Sec. III.A is a tensor whose blocks are computed on demand like this):
+ *
+ *   V[p,q,r,s] = sum_L ( X[p,r,L] * X[q,s,L] - X[p,s,L] * X[q,r,L] )
+ *
+ * X has modes (P, R, aux) and V modes (P, P, R, R).  An entry of X in a block
+ * that X does not store is zero.  Fills the listed stored blocks of V (every
+ * block when `blocks` is NULL).  Summation order: aux tiles in order, then L
+ * inside the tile; each L contributes one product difference.
+ */
+int oracle_cholesky_v(const otensor* V, const otensor* X, const double* x, double* v, const int64_t* blocks,
+                      int64_t n_list) {
+  if (!V || !X || V->nm != 4 || X->nm != 3) return OR_EINVAL;
+  if (V->sp[0] != X->sp[0] || V->sp[1] != X->sp[0] || V->sp[2] != X->sp[1] || V->sp[3] != X->sp[1])
+    return OR_EINVAL;
+  const ospace* aux = X->sp[2];
+  const int64_t n = blocks ? n_list : V->n_blocks;
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int64_t i = 0; i < n; ++i) {
+    const int64_t b = blocks ? blocks[i] : i;
+    if (b < 0 || b >= V->n_blocks) continue;
+    const int64_t* t = V->tiles + b * 4;
+    const int64_t tp = t[0], tq = t[1], tr = t[2], ts = t[3];
+    const int64_t np = V->sp[0]->size[tp], nq = V->sp[1]->size[tq];
+    const int64_t nr = V->sp[2]->size[tr], ns = V->sp[3]->size[ts];
+    double* out = v + V->off[b];
+    for (int64_t ip = 0; ip < np; ++ip)
+      for (int64_t iq = 0; iq < nq; ++iq)
+        for (int64_t ir = 0; ir < nr; ++ir)
+          for (int64_t is = 0; is < ns; ++is) {
+            double acc = 0.0;
+            for (int tl = 0; tl < aux->n_tiles; ++tl) {
+              const int64_t nl = aux->size[tl];
+              int64_t k_pr[3] = {tp, tr, tl}, k_qs[3] = {tq, ts, tl};
+              int64_t k_ps[3] = {tp, ts, tl}, k_qr[3] = {tq, tr, tl};
+              const int64_t b_pr = find_block(X, k_pr), b_qs = find_block(X, k_qs);
+              const int64_t b_ps = find_block(X, k_ps), b_qr = find_block(X, k_qr);
+              for (int64_t l = 0; l < nl; ++l) {
+                /* X block (tile a, tile c, tl) is row-major: element (ia, ic, l) at (ia*nc + ic)*nl + l */
+                const double x_pr = b_pr >= 0 ? x[X->off[b_pr] + (ip * nr + ir) * nl + l] : 0.0;
+                const double x_qs = b_qs >= 0 ? x[X->off[b_qs] + (iq * ns + is) * nl + l] : 0.0;
+                const double x_ps = b_ps >= 0 ? x[X->off[b_ps] + (ip * ns + is) * nl + l] : 0.0;
+                const double x_qr = b_qr >= 0 ? x[X->off[b_qr] + (iq * nr + ir) * nl + l] : 0.0;
+                acc += x_pr * x_qs - x_ps * x_qr;
+              }
+            }
+            out[((ip * nq + iq) * nr + ir) * ns + is] = acc;
+          }
+  }
+  return OR_OK;
 }

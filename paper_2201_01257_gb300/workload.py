@@ -35,7 +35,7 @@ def fill_tensor(T: Tensor, seed: int, spec: wl.TensorSpec) -> None:
     lo, ext = T.block_lo_ext()
     dims = [m.n for m in T.modes]
     tamm_synth.fill_boxes(seed, spec.stream, spec.sigma, dims, spec.anti01, spec.anti23, lo, ext,
-                          T.block_offsets, host)
+                          T.block_offsets, host, sym01=spec.sym01)
     T.upload(host)
 
 

@@ -75,8 +75,10 @@ def value(seed: int, stream: int, sigma: float, dims, anti01: bool, anti23: bool
 
 
 def fill_boxes(seed: int, stream: int, sigma: float, dims, anti01: bool, anti23: bool,
-               lo, ext, off, out: np.ndarray) -> None:
-    """Fill boxes ``[lo[b], lo[b]+ext[b])`` of a dense tensor, row-major, at ``out[off[b]:]``."""
+               lo, ext, off, out: np.ndarray, sym01: bool = False) -> None:
+    """Fill boxes ``[lo[b], lo[b]+ext[b])`` of a dense tensor, row-major, at ``out[off[b]:]``.
+
+    ``sym01`` symmetrises modes 0 and 1 of a 3-mode tensor instead (Cholesky vectors)."""
     lo = _i64(lo).reshape(-1, len(dims))
     ext = _i64(ext).reshape(-1, len(dims))
     off = _i64(off).reshape(-1)
@@ -87,6 +89,10 @@ def fill_boxes(seed: int, stream: int, sigma: float, dims, anti01: bool, anti23:
         need = int((off + ext.prod(axis=1)).max())
         assert need <= out.size, (need, out.size)
     d = _i64(dims)
-    _load().tamm_synth_fill_boxes(seed, stream, sigma, len(d), _p64(d), int(anti01), int(anti23), nbox,
+    pair01 = int(anti01)
+    if sym01:
+        assert len(d) == 3 and d[0] == d[1] and not anti01, "sym01: 3-mode tensors with equal first two extents"
+        pair01 = 2
+    _load().tamm_synth_fill_boxes(seed, stream, sigma, len(d), _p64(d), pair01, int(anti23), nbox,
                                   _p64(lo), _p64(ext), _p64(off),
                                   out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))

@@ -16,6 +16,12 @@
  *       one pair:    (X[pq..] - X[qp..]) / sqrt(2)
  *     which keeps the off-diagonal standard deviation at sigma and makes the
  *     diagonal (p == q) exactly zero.
+ *   - Symmetrisation of the first two modes of a 3-mode tensor (pair code 2,
+ *     for Cholesky vectors X[p,r,L] = X[r,p,L]):
+ *       (X[prL] + X[rpL]) / sqrt(2)
+ *     (off-diagonal standard deviation sigma, diagonal sqrt(2) sigma).
+ *
+ * Pair codes for modes (0,1): 0 plain, 1 antisymmetrised, 2 symmetrised.
  */
 #include <math.h>
 #include <stdint.h>
@@ -96,6 +102,9 @@ double tamm_synth_value(uint64_t seed, uint32_t stream, double sigma, int ndim, 
   } else if (ndim == 4 && anti23) {
     v = (tamm_synth_normal(seed, stream, lin4(d, p, q, r, s)) -
          tamm_synth_normal(seed, stream, lin4(d, p, q, s, r))) * 0.70710678118654752440;
+  } else if (ndim == 3 && anti01 == 2) {
+    v = (tamm_synth_normal(seed, stream, lin4(d, 0, q, r, s)) +
+         tamm_synth_normal(seed, stream, lin4(d, 0, r, q, s))) * 0.70710678118654752440;
   } else if (ndim == 2 && anti01) {
     v = (tamm_synth_normal(seed, stream, lin4(d, 0, 0, r, s)) -
          tamm_synth_normal(seed, stream, lin4(d, 0, 0, s, r))) * 0.70710678118654752440;

@@ -43,6 +43,8 @@ class TensorSpec:
     stream: int = 0
     anti01: bool = False
     anti23: bool = False
+    sym01: bool = False  # 3-mode tensors: symmetric in modes 0 and 1 (Cholesky vectors X[p,r,L] = X[r,p,L])
+    cholesky: str = ""  # formed on the fly from these Cholesky vectors (Eq. cc12); no stored values
 
 
 @dataclass(frozen=True)
@@ -187,6 +189,43 @@ def small_doubles(O: int = 8, V: int = 24, to: int = 2, tv: int = 4, seed_k: int
     w = _doubles(_vt(seed_k, O, V, to, tv, f"ccsd_doubles_O{O}_V{V}"))
     w.steps = doubles_steps()
     return w
+
+
+def aux_space(name: str, n_aux: int, tile: int) -> SpaceSpec:
+    """Auxiliary (Cholesky-vector) index: one spinless group (spin 0, irrep 0) of n_aux vectors."""
+    return SpaceSpec(name, ((n_aux, 0, 0),), tile=tile)
+
+
+def cholesky_sigma(sigma_v: float, n_aux: int) -> float:
+    """Standard deviation of the Cholesky vectors that gives the formed V entries (a sum of 2 n_aux products
+    of independent draws) the standard deviation sigma_v."""
+    return (sigma_v * sigma_v / (2.0 * n_aux)) ** 0.25
+
+
+def cholesky_ladder(O: int, V: int, to: int, tv: int, n_aux: int, t_aux: int, seed_k: int) -> Workload:
+    """Ladder R[a,b,i,j] = 0.5 sum_ef V[a,b,e,f] T[e,f,i,j] with V_vvvv never stored: it is formed on the fly
+    from Cholesky vectors X[p,r,L] (symmetric in p, r; spin-diagonal; L spinless) as
+    V[a,b,e,f] = sum_L X[a,e,L] X[b,f,L] - X[a,f,L] X[b,e,L]."""
+    w = _vt(seed_k, O, V, to, tv, f"cholesky_ladder_O{O}_V{V}_L{n_aux}")
+    w.spaces["aux"] = aux_space("aux", n_aux, t_aux)
+    w.tensors = {
+        "X": TensorSpec("X", ("virt", "virt", "aux"), 1, sigma=cholesky_sigma(0.1, n_aux), stream=8, sym01=True),
+        "V_chol": TensorSpec("V_chol", ("virt",) * 4, 2, cholesky="X"),
+        "T": TensorSpec("T", ("virt", "virt", "occ", "occ"), 2, sigma=0.01, stream=2, anti01=True, anti23=True),
+        "R": TensorSpec("R", ("virt", "virt", "occ", "occ"), 2),
+    }
+    w.steps = [ContractSpec("ladder", "R", "abij", "V_chol", "abef", "T", "efij", 0.5, beta=0.0)]
+    return w
+
+
+def cholesky_ladder_o40_v240() -> Workload:
+    """Cholesky-vector ladder at O=40, V=240 (tiles 20/40) with 2(O+V) = 560 vectors in tiles of 112."""
+    return cholesky_ladder(40, 240, 20, 40, 560, 112, 7)
+
+
+def cholesky_ladder_o8_v32() -> Workload:
+    """Small Cholesky-vector ladder for tests: O=8, V=32 (tiles 4/8), 80 vectors in tiles of 24 (ragged)."""
+    return cholesky_ladder(8, 32, 4, 8, 80, 24, 8)
 
 
 # the spin-block workloads by name
