@@ -795,6 +795,52 @@ def run_dense4d_case(args) -> dict:
     return out
 
 
+def run_cholesky_case(args) -> dict:
+    """The ladder R = 1/2 V T with V_vvvv never stored: a lambda tensor formed slab by slab from 560
+    Cholesky vectors (Eq. cc12) inside the contraction, O=40 V=240 (tiles 20/40).  Split precision
+    (6 slices, formation included) and FP64; flops count forming V once plus the ladder."""
+    import torch
+
+    import paper_2201_01257_gb300 as tg
+    from paper_2201_01257_gb300 import workload as gw
+    from tamm_synth import workloads as wl
+
+    w = wl.cholesky_ladder_o40_v240()
+    ctx = tg.Context(0)
+    sp, T = gw.build(ctx, w, slab_bytes=int(args.slab_gb * (1 << 30)))
+    run = gw.Runner(ctx, w, sp, T)
+    st = w.steps[0]
+    V = T["V_chol"]
+    flops = run.flops(st)
+    out = {"case": f"{w.name}: R = 1/2 V_vvvv T, V_vvvv formed on the fly from Cholesky vectors",
+           "V_vvvv_bytes_not_stored": V.n_elems * 8, "slab_buffer_bytes": V.buffer_bytes, "slabs": V.n_slabs,
+           "form_flops": V.form_flops, "ladder_flops": flops - V.form_flops, "nonzero_block_flops": flops}
+    stream = torch.cuda.current_stream()
+    results = {}
+    for prec, reps in (("ozaki_bf16", max(1, args.steps)), ("f64", 1)):
+        run.run(prec, SLICES if prec == "ozaki_bf16" else 0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            run.run(prec, SLICES if prec == "ozaki_bf16" else 0)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t = e0.elapsed_time(e1) / reps
+        results[prec] = T["R"].download()
+        key = "split" if prec == "ozaki_bf16" else "f64"
+        out[f"{key}_ms"] = round(t, 3)
+        out[f"{key}_TFLOP/s"] = round(flops / t / 1e9, 3)
+    a, b = results["ozaki_bf16"], results["f64"]
+    out["split_rel_err_vs_f64"] = float(np.linalg.norm(a - b) / np.linalg.norm(b))
+    ctx.profile(True)
+    run.run("ozaki_bf16", SLICES)
+    prof = ctx.profile_read()
+    ctx.profile(False)
+    out["split_kernel_ms"] = {k: round(v[0], 3) for k, v in prof.items() if v[1]}
+    out["split_kernel_launches"] = {k: v[1] for k, v in prof.items() if v[1]}
+    return out
+
+
 def run_doubles_term_case(args) -> dict:
     """One contraction of the doubles recipe at a chosen size (tiles 20/40), split precision (6 slices):
     small cases for profiling a single term."""
@@ -843,6 +889,9 @@ def main():
     ap.add_argument("--doubles-o80", action="store_true", help="time the O=80 V=320 contractions alone instead")
     ap.add_argument("--dense4d", default="", help="N,tile: time the dense 4-D contraction instead")
     ap.add_argument("--term", default="", help="O,V,name: time one doubles contraction of that size instead")
+    ap.add_argument("--cholesky", action="store_true",
+                    help="time the ladder with V_vvvv formed on the fly from Cholesky vectors instead")
+    ap.add_argument("--slab-gb", type=float, default=0.0, help="with --cholesky: slab buffer bound (0 = default)")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -858,6 +907,8 @@ def main():
         out = run_dense4d_case(args)
     elif args.term:
         out = run_doubles_term_case(args)
+    elif args.cholesky:
+        out = run_cholesky_case(args)
     elif args.impl == "reference":
         out = run_reference(args, rank)
     else:

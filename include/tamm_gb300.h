@@ -152,7 +152,8 @@ TAMM_API tamm_status tamm_sync(tamm_ctx* ctx);
  * sub-ranges, TiledIndexSpace with fixed or explicit tile sizes; spin sub-spaces
  * as in Sec. IV.A eq. "tamm_cc-Spin").  The space is `n_groups` contiguous
  * groups of orbitals; group g has `group_size[g]` orbitals, spin
- * `group_spin[g]` (+1 alpha, -1 beta) and irrep `group_irrep[g]` in 0..7 (NULL
+ * `group_spin[g]` (+1 alpha, -1 beta, 0 spinless: an auxiliary index such as
+ * the Cholesky vectors' of Eq. cc12) and irrep `group_irrep[g]` in 0..7 (NULL
  * = all 0).  Tiling: if `fixed_tile` > 0 each group is cut into tiles of that
  * size, the last tile of a group taking the remainder; otherwise the
  * `n_tiles` sizes in `tile_sizes` are laid over the groups in order and must
@@ -207,6 +208,40 @@ TAMM_API double* tamm_tensor_data(const tamm_tensor* t);
 /* NULL is ignored.  Storage obtained by tamm_tensor_allocate is released
  * stream-ordered on the context's stream. */
 TAMM_API void tamm_tensor_destroy(tamm_tensor* t);
+
+/* Cholesky lambda tensor (Sec. III.A "lambda tensor": blocks computed on
+ * demand, never stored; Sec. IV.A Eq. cc12 Cholesky decomposition of the
+ * two-electron tensor):
+ *     V[p,q,r,s] = sum_L X[p,r,L] X[q,s,L] - X[p,s,L] X[q,r,L]
+ * `X` is a stored 3-mode tensor of Cholesky vectors with modes (P, R, aux);
+ * V has modes (P, P, R, R) with two upper modes and X's symmetry kind, and
+ * stores a block exactly when some aux tile links the X blocks of one of the
+ * two products.  V is read-only and only feeds tamm_contract (as A or B):
+ * the contraction forms V in slabs of consecutive first-mode tiles (one
+ * X-by-X product into an internal buffer, then the two-term permuted add into
+ * a slab buffer, both in the contraction's precision) and runs the contraction
+ * on each slab, the first with the caller's beta and the rest with beta = 1.
+ * `slab_bytes` bounds the two slab buffers together (0 = 8 GiB; a tile that
+ * alone needs more gets a slab of its own); they are allocated here through
+ * the context allocator and freed by tamm_tensor_destroy.  X must stay alive
+ * and bound while V is used.  tamm_tensor_info/blocks describe V's block
+ * table as if it were stored; bind, allocate, copies, tamm_add, tamm_energy,
+ * tamm_norm, tamm_autotune and contraction groups refuse V
+ * (TAMM_EUNSUPPORTED), and V can never be an output.
+ * Errors: TAMM_EINVAL (X not a stored 3-mode tensor), TAMM_ENOMEM. */
+TAMM_API tamm_status tamm_tensor_create_cholesky(tamm_ctx* ctx, const tamm_tensor* X, int64_t slab_bytes,
+                                                 tamm_tensor** out);
+/* Slab count, FP64-equivalent flops that forming all of V once costs (the
+ * X-by-X products; 2*M*N*K per block pair), and the bytes of the two slab
+ * buffers (any pointer may be NULL).  Errors: TAMM_EINVAL (not a lambda tensor). */
+TAMM_API tamm_status tamm_cholesky_info(const tamm_tensor* V, int* n_slabs, double* form_flops,
+                                        int64_t* buffer_bytes);
+/* Form all of V into `out`, a stored tensor with V's spaces and block table
+ * (e.g. from tamm_tensor_create on V's spaces with n_upper 2 and X's
+ * symmetry), slab by slab in `precision` / `slices` as tamm_contract takes them.
+ * Errors: TAMM_EINVAL (block tables differ), as tamm_contract otherwise. */
+TAMM_API tamm_status tamm_cholesky_form(tamm_ctx* ctx, const tamm_tensor* V, tamm_tensor* out, int precision,
+                                        int slices);
 
 /* ------------------------------------------------------------- operations */
 

@@ -68,6 +68,9 @@ PROTOTYPES = [
     ("tamm_tensor_copy_to_host", _i, [_vp, _vp, _vp]),
     ("tamm_tensor_data", _vp, [_vp]),
     ("tamm_tensor_destroy", None, [_vp]),
+    ("tamm_tensor_create_cholesky", _i, [_vp, _vp, _i64, ctypes.POINTER(_vp)]),
+    ("tamm_cholesky_info", _i, [_vp, _ip, _dp, _i64p]),
+    ("tamm_cholesky_form", _i, [_vp, _vp, _vp, _i, _i]),
     ("tamm_contract", _i, [_vp, _d, _vp, _cp, _d, _vp, _cp, _vp, _cp, _i, _i]),
     ("tamm_contract_flops", _i, [_vp, _vp, _cp, _vp, _cp, _vp, _cp, _dp]),
     ("tamm_add", _i, [_vp, _vp, _cp, _d, _vp, _i, ctypes.POINTER(_cp), _dp]),
@@ -200,6 +203,16 @@ class Context:
 
     def tensor(self, modes, n_upper: int, sym: str = "spin", allocate: bool = True) -> "Tensor":
         return Tensor(self, modes, n_upper, sym, allocate and self.device >= 0)
+
+    def tensor_cholesky(self, X: "Tensor", slab_bytes: int = 0) -> "CholeskyTensor":
+        """Lambda tensor V[p,q,r,s] = sum_L X[p,r,L] X[q,s,L] - X[p,s,L] X[q,r,L] (Eq. cc12) over X's
+        (P, R, aux) modes, formed slab by slab inside the contractions that read it."""
+        return CholeskyTensor(self, X, slab_bytes)
+
+    def cholesky_form(self, V: "CholeskyTensor", out: "Tensor", precision="f64", slices: int = 0) -> None:
+        """Form all of V into the stored tensor ``out`` (same spaces and block table)."""
+        prec = PREC[precision] if isinstance(precision, str) else int(precision)
+        self.check(self.lib.tamm_cholesky_form(self.handle, V.handle, out.handle, prec, slices), "tamm_cholesky_form")
 
     def tensor_permuted(self, like: "Tensor", perm, allocate: bool = True) -> "Tensor":
         """Tensor whose mode m is like's mode perm[m], storing the images of like's blocks."""
@@ -435,3 +448,39 @@ class Tensor:
         if getattr(self, "handle", None) and getattr(self.ctx, "handle", None):
             self.ctx.lib.tamm_tensor_destroy(self.handle)
             self.handle = None
+
+
+class CholeskyTensor(Tensor):
+    """Read-only lambda tensor formed from Cholesky vectors X (tamm_tensor_create_cholesky); it has a block
+    table but no storage, and keeps X alive."""
+
+    def __init__(self, ctx: Context, X: Tensor, slab_bytes: int = 0):
+        self.ctx = ctx
+        self.factor = X
+        self.modes = [X.modes[0], X.modes[0], X.modes[1], X.modes[1]]
+        self.nm = 4
+        h = ctypes.c_void_p()
+        ctx.check(ctx.lib.tamm_tensor_create_cholesky(ctx.handle, X.handle, int(slab_bytes), ctypes.byref(h)),
+                  "tamm_tensor_create_cholesky")
+        self.handle = h
+        nb, ne = ctypes.c_int64(), ctypes.c_int64()
+        ctx.lib.tamm_tensor_info(h, ctypes.byref(nb), ctypes.byref(ne))
+        self.n_blocks, self.n_elems = nb.value, ne.value
+        self.block_tiles = np.zeros((self.n_blocks, self.nm), np.int64)
+        self.block_offsets = np.zeros(self.n_blocks, np.int64)
+        if self.n_blocks:
+            ctx.lib.tamm_tensor_blocks(h, _ptr(self.block_tiles), _ptr(self.block_offsets))
+        self.data = None
+        n, f, b = ctypes.c_int(), ctypes.c_double(), ctypes.c_int64()
+        ctx.check(ctx.lib.tamm_cholesky_info(h, ctypes.byref(n), ctypes.byref(f), ctypes.byref(b)),
+                  "tamm_cholesky_info")
+        self.n_slabs, self.form_flops, self.buffer_bytes = n.value, f.value, b.value
+
+    def bind(self, t) -> None:
+        raise TammError(TAMM_EUNSUPPORTED, "a lambda tensor has no storage")
+
+    def upload(self, host: np.ndarray) -> None:
+        raise TammError(TAMM_EUNSUPPORTED, "a lambda tensor has no storage")
+
+    def download(self) -> np.ndarray:
+        raise TammError(TAMM_EUNSUPPORTED, "a lambda tensor has no storage")

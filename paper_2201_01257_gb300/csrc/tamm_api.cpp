@@ -11,6 +11,7 @@
 
 #include "tamm_internal.h"
 #include "tamm_contract.h"
+#include "tamm_lambda.h"
 #include "tamm_plan.h"
 
 using namespace tamm;
@@ -275,7 +276,7 @@ extern "C" tamm_status tamm_space_create(tamm_ctx* ctx, int n_groups, const int6
     int64_t pos = 0;
     for (int g = 0; g < n_groups; ++g) {
       if (group_size[g] < 0) throw Error(TAMM_EINVAL, "space: negative group size");
-      if (group_spin[g] != 1 && group_spin[g] != -1) throw Error(TAMM_EINVAL, "space: spin must be +1 or -1");
+      if (group_spin[g] < -1 || group_spin[g] > 1) throw Error(TAMM_EINVAL, "space: spin must be +1, -1 or 0");
       const int irr = group_irrep ? group_irrep[g] : 0;
       if (irr < 0 || irr > 7) throw Error(TAMM_EINVAL, "space: irrep must be in 0..7");
       int64_t left = group_size[g];
@@ -376,6 +377,12 @@ static void build_blocks(tamm_tensor& T, Pred keep) {
   T.n_elems = pos;
 }
 
+void build_blocks_where(tamm_tensor& T, const std::function<bool(const int64_t*)>& keep) { build_blocks(T, keep); }
+
+static void not_lambda(const tamm_tensor* t, const char* what) {
+  if (t->lambda) throw Error(TAMM_EUNSUPPORTED, "%s: a lambda tensor has no storage", what);
+}
+
 std::unique_ptr<tamm_tensor> make_permuted_tensor(const tamm_tensor& S, const int* perm) {
   // New tensor whose mode m is S's mode perm[m]; stores exactly the images of S's blocks.
   std::unique_ptr<tamm_tensor> T(new tamm_tensor());
@@ -451,6 +458,7 @@ extern "C" tamm_status tamm_tensor_bind(tamm_tensor* t, double* device_data) {
   if (!t) return TAMM_EINVAL;
   return guarded(t->ctx, [&] {
     require_device(t->ctx);
+    not_lambda(t, "bind");
     if (!device_data && t->n_elems) throw Error(TAMM_EINVAL, "bind: null device pointer");
     if (((uintptr_t)device_data) % 8) throw Error(TAMM_EINVAL, "bind: pointer not 8-byte aligned");
     if (t->owned) ctx_free(t->ctx, t->data, t->owned_bytes);
@@ -463,6 +471,7 @@ extern "C" tamm_status tamm_tensor_bind(tamm_tensor* t, double* device_data) {
 extern "C" tamm_status tamm_tensor_allocate(tamm_tensor* t) {
   if (!t) return TAMM_EINVAL;
   return guarded(t->ctx, [&] {
+    not_lambda(t, "allocate");
     if (t->owned) ctx_free(t->ctx, t->data, t->owned_bytes);
     t->owned = false;
     const size_t bytes = (size_t)std::max<int64_t>(t->n_elems, 1) * sizeof(double);
@@ -476,6 +485,7 @@ extern "C" tamm_status tamm_tensor_copy_from_host(tamm_ctx* ctx, tamm_tensor* t,
   if (!ctx || !t) return TAMM_EINVAL;
   return guarded(ctx, [&] {
     require_device(ctx);
+    not_lambda(t, "copy");
     if (!host || (t->n_elems && !t->data)) throw Error(TAMM_EINVAL, "copy: null buffer or unbound tensor");
     cuda_check(cudaMemcpyAsync(t->data, host, (size_t)t->n_elems * sizeof(double), cudaMemcpyHostToDevice,
                                ctx->stream),
@@ -487,6 +497,7 @@ extern "C" tamm_status tamm_tensor_copy_to_host(tamm_ctx* ctx, const tamm_tensor
   if (!ctx || !t) return TAMM_EINVAL;
   return guarded(ctx, [&] {
     require_device(ctx);
+    not_lambda(t, "copy");
     if (!host || (t->n_elems && !t->data)) throw Error(TAMM_EINVAL, "copy: null buffer or unbound tensor");
     cuda_check(cudaMemcpyAsync(host, t->data, (size_t)t->n_elems * sizeof(double), cudaMemcpyDeviceToHost,
                                ctx->stream),
@@ -495,6 +506,31 @@ extern "C" tamm_status tamm_tensor_copy_to_host(tamm_ctx* ctx, const tamm_tensor
 }
 
 extern "C" double* tamm_tensor_data(const tamm_tensor* t) { return t ? t->data : nullptr; }
+
+extern "C" tamm_status tamm_tensor_create_cholesky(tamm_ctx* ctx, const tamm_tensor* X, int64_t slab_bytes,
+                                                   tamm_tensor** out) {
+  if (!ctx || !out) return TAMM_EINVAL;
+  *out = nullptr;
+  return guarded(ctx, [&] { *out = make_cholesky_tensor(ctx, X, slab_bytes).release(); });
+}
+
+extern "C" tamm_status tamm_cholesky_info(const tamm_tensor* V, int* n_slabs, double* form_flops,
+                                          int64_t* buffer_bytes) {
+  if (!V || !V->lambda) return TAMM_EINVAL;
+  if (n_slabs) *n_slabs = (int)V->lambda->slabs.size();
+  if (form_flops) *form_flops = V->lambda->form_flops;
+  if (buffer_bytes) *buffer_bytes = (int64_t)(V->lambda->v_bytes + V->lambda->x1_bytes);
+  return TAMM_OK;
+}
+
+extern "C" tamm_status tamm_cholesky_form(tamm_ctx* ctx, const tamm_tensor* V, tamm_tensor* out, int precision,
+                                          int slices) {
+  if (!ctx) return TAMM_EINVAL;
+  return guarded(ctx, [&] {
+    require_device(ctx);
+    cholesky_form(ctx, V, out, precision, slices);
+  });
+}
 
 extern "C" void tamm_tensor_destroy(tamm_tensor* t) {
   if (!t) return;

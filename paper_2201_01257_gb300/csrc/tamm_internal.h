@@ -5,6 +5,7 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <functional>
 #include <map>
 #include <memory>
 #include <string>
@@ -100,6 +101,10 @@ struct TunedConfig {
 
 }  // namespace tamm
 
+namespace tamm {
+struct CholeskyLambda;  // tamm_lambda.h
+}  // namespace tamm
+
 struct tamm_space {
   tamm_ctx* ctx = nullptr;
   uint64_t id = 0;
@@ -121,6 +126,7 @@ struct tamm_tensor {
   double* data = nullptr;
   bool owned = false;
   size_t owned_bytes = 0;
+  std::shared_ptr<tamm::CholeskyLambda> lambda;  // set for a Cholesky lambda tensor (never stored)
 
   int64_t find(const int64_t* tt) const {
     int64_t lin = 0;
@@ -170,6 +176,11 @@ namespace tamm {
 // Launch bookkeeping: call around every kernel launch (counts, optional event timing).
 void kernel_begin(tamm_ctx* ctx, int kind);
 void kernel_end(tamm_ctx* ctx, int kind);
+
+// Fill a tensor's block table (lookup, tiles, offsets) with the tile tuples `keep` accepts, in
+// lexicographic order; the spaces (nm, sp) must be set.
+void build_blocks_where(tamm_tensor& T, const std::function<bool(const int64_t*)>& keep);
+void require_device(tamm_ctx* ctx);
 
 // allocation through the context allocator (stream-ordered)
 void* ctx_alloc(tamm_ctx* ctx, size_t bytes);

@@ -9,6 +9,7 @@
 
 #include "tamm_plan.h"
 #include "tamm_contract.h"
+#include "tamm_lambda.h"
 
 namespace tamm {
 
@@ -43,6 +44,7 @@ int Labels::find(char c) const {
 }
 
 static void require_data(const tamm_tensor* T, const char* what) {
+  if (T->lambda) throw Error(TAMM_EUNSUPPORTED, "%s: a lambda tensor only feeds contractions as an input", what);
   if (T->n_elems && !T->data) throw Error(TAMM_EINVAL, "%s: tensor has no device storage (bind or allocate)", what);
 }
 
@@ -365,6 +367,10 @@ static void check_contract_args(const tamm_tensor* C, const tamm_tensor* A, cons
 
 void run_contract(tamm_ctx* ctx, double alpha, tamm_tensor* C, const char* lc, double beta, const tamm_tensor* A,
                   const char* la, const tamm_tensor* B, const char* lb, int precision, int slices) {
+  if (A && B && (A->lambda || B->lambda)) {
+    run_contract_lambda(ctx, alpha, C, lc, beta, A, la, B, lb, precision, slices);
+    return;
+  }
   check_contract_args(C, A, B, beta);
   if (precision == TAMM_PREC_OZAKI_I8)
     throw Error(TAMM_EUNSUPPORTED, "INT8 slices: sm_103a has no tcgen05 kind::i8 tensor-core product");

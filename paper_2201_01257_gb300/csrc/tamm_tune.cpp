@@ -90,6 +90,7 @@ extern "C" tamm_status tamm_autotune(tamm_ctx* ctx, const tamm_tensor* C, const 
     if (!C || !A || !B || !lc || !la || !lb) throw Error(TAMM_EINVAL, "autotune: null argument");
     if (!(target_rel_err > 0.0)) throw Error(TAMM_EINVAL, "autotune: target error must be positive");
     if (ctx->group_active || ctx->capturing) throw Error(TAMM_EINVAL, "autotune inside a group or capture");
+    if (A->lambda || B->lambda || C->lambda) throw Error(TAMM_EUNSUPPORTED, "autotune: lambda tensor operand");
     if (!A->data || !B->data) throw Error(TAMM_EINVAL, "autotune: operand without data");
     bytes = (size_t)std::max<int64_t>(C->n_elems, 1) * sizeof(double);
     ref = ctx_alloc(ctx, bytes);

@@ -14,19 +14,24 @@ import numpy as np
 import tamm_synth
 from tamm_synth import workloads as wl
 
-from . import Context, Tensor
+from . import CholeskyTensor, Context, Tensor
 
 
-def build(ctx: Context, w: wl.Workload, fill: bool = True, only=None):
+def build(ctx: Context, w: wl.Workload, fill: bool = True, only=None, slab_bytes: int = 0):
+    """Spaces and tensors of a recipe; a tensor formed from Cholesky vectors becomes a lambda tensor over
+    them (slab buffers of at most ``slab_bytes``, 0 = the library's default)."""
     spaces = {k: ctx.space(s.groups, s.tile, s.tile_sizes) for k, s in w.spaces.items()}
     tensors = {}
     for name, t in w.tensors.items():
-        if only is not None and name not in only:
+        if (only is not None and name not in only) or t.cholesky:
             continue
         T = ctx.tensor([spaces[m] for m in t.modes], t.n_upper, t.sym)
         if fill and t.sigma != 0.0:
             fill_tensor(T, w.seed, t)
         tensors[name] = T
+    for name, t in w.tensors.items():
+        if t.cholesky and (only is None or name in only):
+            tensors[name] = ctx.tensor_cholesky(tensors[t.cholesky], slab_bytes)
     return spaces, tensors
 
 
@@ -70,13 +75,15 @@ class Runner:
         return self._scratch[step.name]
 
     def flops(self, step) -> float:
+        """Nonzero-block flops of a contraction step, with forming a lambda operand once counted in."""
         if not isinstance(step, wl.ContractSpec):
             return 0.0
         T = self.tensors
+        form = sum(T[n].form_flops for n in (step.a, step.b) if isinstance(T[n], CholeskyTensor))
         if step.antisym:
             X, lx = self.scratch_for(step)
-            return self.ctx.flops(X, lx, T[step.a], step.la, T[step.b], step.lb)
-        return self.ctx.flops(T[step.c], step.lc, T[step.a], step.la, T[step.b], step.lb)
+            return form + self.ctx.flops(X, lx, T[step.a], step.la, T[step.b], step.lb)
+        return form + self.ctx.flops(T[step.c], step.lc, T[step.a], step.la, T[step.b], step.lb)
 
     def run_step(self, step, precision="f64", slices: int = 0, energy_out=None):
         T, ctx = self.tensors, self.ctx

@@ -162,3 +162,65 @@ def test_group_and_graph_calls_need_a_device(hctx):
     assert hctx.lib.tamm_graph_end(hctx.handle, ct.byref(g)) == tg.TAMM_ECUDA and not g.value
     assert hctx.lib.tamm_graph_launch(None) == tg.TAMM_EINVAL
     hctx.lib.tamm_graph_destroy(None)
+
+
+# ------------------------------------------------ Cholesky lambda tensor (Eq. cc12)
+
+@pytest.mark.parametrize("recipe", [wl.cholesky_ladder_o8_v32, wl.cholesky_ladder_o40_v240])
+def test_cholesky_lambda_block_table_matches_oracle(hctx, recipe):
+    w = recipe()
+    gs, os_ = spaces_for(hctx, w)
+    assert list(gs["aux"].tile_spin) == [0] * gs["aux"].n_tiles  # spinless auxiliary index
+    xs, vs = w.tensors["X"], w.tensors["V_chol"]
+    X = hctx.tensor([gs[m] for m in xs.modes], xs.n_upper, xs.sym)
+    RX = O.Tensor([os_[m] for m in xs.modes], xs.n_upper, xs.sym, alloc=False)
+    assert (X.n_blocks, X.n_elems) == (RX.n_blocks, RX.n_elems)
+    V = hctx.tensor_cholesky(X)
+    R = O.Tensor([os_[m] for m in vs.modes], vs.n_upper, vs.sym, alloc=False)
+    # the blocks some aux tile links are exactly the spin-rule blocks of a 2|2 tensor
+    assert (V.n_blocks, V.n_elems) == (R.n_blocks, R.n_elems)
+    assert np.array_equal(V.block_tiles, R.block_tiles)
+    assert np.array_equal(V.block_offsets, R.block_off)
+    # forming V once costs 2 * (sum of |p||r| over same-spin tile pairs)^2 * n_aux
+    half = gs["virt"].n // 2
+    assert V.form_flops == 2.0 * (2 * half * half) ** 2 * gs["aux"].n
+    # the ladder's own flops are those of the stored-V ladder
+    T = hctx.tensor([gs["virt"], gs["virt"], gs["occ"], gs["occ"]], 2)
+    Vs = hctx.tensor([gs["virt"]] * 4, 2)
+    assert hctx.flops(T, "abij", V, "abef", T, "efij") == hctx.flops(T, "abij", Vs, "abef", T, "efij")
+
+
+def test_cholesky_lambda_slab_partition(hctx):
+    w = wl.cholesky_ladder_o8_v32()
+    gs, _ = spaces_for(hctx, w)
+    xs = w.tensors["X"]
+    X = hctx.tensor([gs[m] for m in xs.modes], xs.n_upper, xs.sym)
+    n_tiles = gs["virt"].n_tiles
+    one = hctx.tensor_cholesky(X, 1)  # every tile alone
+    whole = hctx.tensor_cholesky(X, 1 << 40)
+    assert one.n_slabs == n_tiles and whole.n_slabs == 1
+    assert one.form_flops == whole.form_flops
+    assert whole.buffer_bytes == 8 * (whole.n_elems + whole.n_elems * 2 // 3)  # V (3/8 dense) + X1 (1/4 dense)
+    mid = hctx.tensor_cholesky(X, whole.buffer_bytes // 2)
+    assert 2 <= mid.n_slabs < n_tiles and mid.buffer_bytes <= whole.buffer_bytes // 2
+    for V in (one, mid, whole):
+        assert np.array_equal(V.block_tiles, whole.block_tiles)
+
+
+def test_cholesky_lambda_refusals(hctx):
+    v = hctx.space([(8, 1, 0), (8, -1, 0)], tile=4)
+    a = hctx.space([(6, 0, 0)], tile=3)
+    X = hctx.tensor([v, v, a], 1)
+    V = hctx.tensor_cholesky(X)
+    h = ctypes.c_void_p()
+    assert hctx.lib.tamm_tensor_create_cholesky(hctx.handle, V.handle, 0, ctypes.byref(h)) == tg.TAMM_EINVAL
+    Y = hctx.tensor([v, v, a, a], 2)
+    assert hctx.lib.tamm_tensor_create_cholesky(hctx.handle, Y.handle, 0, ctypes.byref(h)) == tg.TAMM_EINVAL
+    assert hctx.lib.tamm_tensor_create_cholesky(hctx.handle, X.handle, -1, ctypes.byref(h)) == tg.TAMM_EINVAL
+    assert not h.value
+    assert hctx.lib.tamm_tensor_allocate(V.handle) == tg.TAMM_EUNSUPPORTED
+    assert hctx.lib.tamm_cholesky_info(X.handle, None, None, None) == tg.TAMM_EINVAL
+    with pytest.raises(tg.TammError):
+        V.bind(None)
+    with pytest.raises(tg.TammError):
+        hctx.space([(6, 2, 0)], tile=3)
