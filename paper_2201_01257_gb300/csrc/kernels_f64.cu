@@ -65,6 +65,36 @@ __global__ void __launch_bounds__(256) add_kernel(double* __restrict__ dst, cons
   }
 }
 
+// Cholesky pair difference for row p of one V block: for each q, the second product's (s, r) plane
+// X1[p, :, q, :] of block (tp,ts,tq,tr) is staged in shared memory (row pitch nr + 1 against bank
+// conflicts), so that the reads of both X1 blocks and the write of V all run along the contiguous last
+// index; then V[p,q,r,s] = X1[p,r,q,s] - plane[s][r].
+__global__ void __launch_bounds__(256) cholesky_pair_kernel(double* __restrict__ v, const double* __restrict__ x1,
+                                                            const PairBlock* __restrict__ blocks,
+                                                            const PairItem* __restrict__ items) {
+  extern __shared__ double plane[];
+  const PairItem it = items[blockIdx.x];
+  const PairBlock B = blocks[it.block];
+  const int p = it.p, nq = B.nq, nr = B.nr, ns = B.ns;
+  const int n = nr * ns;
+  for (int q = 0; q < nq; ++q) {
+    if (B.b_off >= 0) {
+      for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const int s = i / nr, r = i - s * nr;
+        plane[s * (nr + 1) + r] = x1[B.b_off + ((int64_t)(p * ns + s) * nq + q) * nr + r];
+      }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      const int r = i / ns, s = i - r * ns;
+      double val = B.a_off >= 0 ? x1[B.a_off + ((int64_t)(p * nr + r) * nq + q) * ns + s] : 0.0;
+      if (B.b_off >= 0) val -= plane[s * (nr + 1) + r];
+      v[B.v_off + ((int64_t)(p * nq + q) * nr + r) * ns + s] = val;
+    }
+    __syncthreads();
+  }
+}
+
 template <int NT>
 __device__ double block_sum(double v) {
   __shared__ double red[NT / 32];
@@ -228,6 +258,16 @@ cudaError_t launch_add(tamm_ctx* ctx, double* dst, const double* src, const AddB
   for (int t = 0; t < n_terms; ++t) al.v[t] = alpha_host[t];
   kernel_begin(ctx, TAMM_KERNEL_ADD);
   add_kernel<<<(unsigned)n_items, 256, 0, ctx->stream>>>(dst, src, blocks, items, n_terms, beta, al);
+  kernel_end(ctx, TAMM_KERNEL_ADD);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cholesky_pair(tamm_ctx* ctx, double* v, const double* x1, const PairBlock* blocks,
+                                 const PairItem* items, int64_t n_items, size_t smem_bytes) {
+  if (n_items == 0) return cudaSuccess;
+  if (smem_bytes > kPairSmemMax) return cudaErrorInvalidValue;  // the caller uses the permuted add instead
+  kernel_begin(ctx, TAMM_KERNEL_ADD);
+  cholesky_pair_kernel<<<(unsigned)n_items, 256, smem_bytes, ctx->stream>>>(v, x1, blocks, items);
   kernel_end(ctx, TAMM_KERNEL_ADD);
   return cudaGetLastError();
 }

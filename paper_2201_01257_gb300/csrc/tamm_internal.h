@@ -35,6 +35,19 @@ struct AddBlock {
   int32_t sstride[kMaxAddTerms][kMaxKernelModes];
 };
 
+// One block of the Cholesky pair difference V[p,q,r,s] = X1[p,r,q,s] - X1[p,s,q,r]: V's block (tiles
+// tp,tq,tr,ts; extents np,nq,nr,ns) and the X1 blocks (tp,tr,tq,ts) and (tp,ts,tq,tr), -1 when not stored.
+struct PairBlock {
+  int64_t v_off, a_off, b_off;
+  int32_t np, nq, nr, ns;
+};
+
+// Row p of one PairBlock processed by one CTA.
+struct PairItem {
+  int32_t block;
+  int32_t p;
+};
+
 // A chunk of one AddBlock processed by one CTA.
 struct ChunkItem {
   int32_t block;
@@ -191,6 +204,11 @@ void* ctx_scratch(tamm_ctx* ctx, size_t bytes);  // valid until the next ctx_scr
 // Implemented in kernels_f64.cu.  All launch on ctx->stream; return cudaError_t.
 cudaError_t launch_add(tamm_ctx* ctx, double* dst, const double* src, const AddBlock* blocks,
                        const ChunkItem* items, int64_t n_items, int n_terms, double beta, const double* alpha_host);
+// V = X1(p,r,q,s) - X1(p,s,q,r) over the listed blocks; `smem_bytes` = 8 * max ns * (nr + 1), at most
+// kPairSmemMax (the default dynamic shared memory limit, so no attribute call is needed).
+constexpr size_t kPairSmemMax = 48 * 1024;
+cudaError_t launch_cholesky_pair(tamm_ctx* ctx, double* v, const double* x1, const PairBlock* blocks,
+                                 const PairItem* items, int64_t n_items, size_t smem_bytes);
 cudaError_t launch_energy_partials(tamm_ctx* ctx, const double* a, const double* b, const AddBlock* blocks,
                                    const ChunkItem* items, int64_t n_items, double* partials);
 cudaError_t launch_sumsq_partials(tamm_ctx* ctx, const double* x, int64_t n, double* partials, int64_t n_parts);

@@ -9,6 +9,7 @@
 #include <vector>
 
 #include "tamm_internal.h"
+#include "tamm_plan.h"
 
 namespace tamm {
 
@@ -19,6 +20,12 @@ struct CholeskySlab {
   std::unique_ptr<tamm_tensor> v;    // V's blocks of the slab
   std::unique_ptr<tamm_tensor> x1;   // X1[p,r,q,s] = sum_L X[p,r,L] X[q,s,L] for p in the slab
   std::unique_ptr<tamm_tensor> xs;   // X's blocks with p in the slab (a view of X's storage)
+  // device lists of the pair-difference kernel (pair_smem = 0: the two-term permuted add serves the slab)
+  std::unique_ptr<Plan> pair_plan;
+  const PairBlock* d_pair_blocks = nullptr;
+  const PairItem* d_pair_items = nullptr;
+  int64_t n_pair_items = 0;
+  size_t pair_smem = 0;
 };
 
 struct CholeskyLambda {

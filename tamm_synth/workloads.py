@@ -219,8 +219,8 @@ def cholesky_ladder(O: int, V: int, to: int, tv: int, n_aux: int, t_aux: int, se
 
 
 def cholesky_ladder_o40_v240() -> Workload:
-    """Cholesky-vector ladder at O=40, V=240 (tiles 20/40) with 2(O+V) = 560 vectors in tiles of 112."""
-    return cholesky_ladder(40, 240, 20, 40, 560, 112, 7)
+    """Cholesky-vector ladder at O=40, V=240 (tiles 20/40) with 2(O+V) = 560 vectors in one aux tile."""
+    return cholesky_ladder(40, 240, 20, 40, 560, 560, 7)
 
 
 def cholesky_ladder_o8_v32() -> Workload:

@@ -124,20 +124,27 @@ def test_lambda_equals_stored_formed_v(gpu_lib, small, prec, tol):
 
 
 def test_graph_replays_lambda_ladder(gpu_lib, small):
+    import torch
+
+    from paper_2201_01257_gb300 import workload as gw
+
     w, _ = small
-    ctx, _, gt = build_gpu(gpu_lib, w, 1)
-    V, T, R = gt["V_chol"], gt["T"], gt["R"]
-    go = lambda: ctx.contract(0.5, R, "abij", 0.0, V, "abef", T, "efij", "ozaki_bf16", 0)
-    go()  # builds every plan
-    ctx.sync()
-    eager = R.download()
-    R.data.zero_()
-    with ctx.capture() as cap:
-        go()
-    assert cap.graph.kernel_launches() > 0
-    cap.graph.launch()
-    ctx.sync()
-    assert np.array_equal(R.download(), eager)
+    stream = torch.cuda.Stream(0)  # capture needs a created stream
+    ctx = gpu_lib.Context(0, stream=stream)
+    with torch.cuda.stream(stream):
+        _, gt = gw.build(ctx, w, slab_bytes=1)
+        V, T, R = gt["V_chol"], gt["T"], gt["R"]
+        go = lambda: ctx.contract(0.5, R, "abij", 0.0, V, "abef", T, "efij", "ozaki_bf16", 0)
+        go()  # builds every plan
+        ctx.sync()
+        eager = R.download()
+        R.data.zero_()
+        with ctx.capture() as cap:
+            go()
+        assert cap.graph.kernel_launches > 0
+        cap.graph.launch()
+        ctx.sync()
+        assert np.array_equal(R.download(), eager)
 
 
 def test_lambda_refusals_on_device(gpu_lib, small):
