@@ -218,9 +218,10 @@ TAMM_API void tamm_tensor_destroy(tamm_tensor* t);
  * stores a block exactly when some aux tile links the X blocks of one of the
  * two products.  V is read-only and only feeds tamm_contract (as A or B):
  * the contraction forms V in slabs of consecutive first-mode tiles (one
- * X-by-X product into an internal buffer, then the two-term permuted add into
- * a slab buffer, both in the contraction's precision) and runs the contraction
- * on each slab, the first with the caller's beta and the rest with beta = 1.
+ * X-by-X product into an internal buffer in the contraction's precision, then
+ * the FP64 difference of its two permuted images into a slab buffer) and runs
+ * the contraction on each slab, the first with the caller's beta and the rest
+ * with beta = 1.
  * `slab_bytes` bounds the two slab buffers together (0 = 8 GiB; a tile that
  * alone needs more gets a slab of its own); they are allocated here through
  * the context allocator and freed by tamm_tensor_destroy.  X must stay alive

@@ -176,6 +176,38 @@ def test_lambda_refusals_on_device(gpu_lib, small):
     ctx.sync()
 
 
+@pytest.mark.parametrize("r_tile", [72, 80])  # 42 KB planes: pair kernel; 52 KB planes: two-term permuted add
+def test_cholesky_oovv_shaped(gpu_lib, r_tile):
+    """V[m,n,e,f] from X[m,e,L] over (occ, virt, aux) — P and R spaces differ — formed and read by the
+    intermediate W(mnij) = V(mnef) T(efij), in FP64 and split precision."""
+    from paper_2201_01257_gb300 import workload as gw
+
+    w = wl.Workload(f"cholesky_oovv_R{r_tile}", wl.SEED_BASE + 11,
+                    {"occ": wl.spin_space("occ", 8, 4), "virt": wl.spin_space("virt", 2 * r_tile, r_tile),
+                     "aux": wl.aux_space("aux", 24, 12)}, {})
+    w.tensors = {
+        "X": wl.TensorSpec("X", ("occ", "virt", "aux"), 1, sigma=0.05, stream=8),
+        "V": wl.TensorSpec("V", ("occ", "occ", "virt", "virt"), 2, cholesky="X"),
+        "T": wl.TensorSpec("T", ("virt", "virt", "occ", "occ"), 2, sigma=0.01, stream=2, anti01=True,
+                           anti23=True),
+        "W": wl.TensorSpec("W", ("occ",) * 4, 2),
+    }
+    w.steps = [wl.ContractSpec("intermediate", "W", "mnij", "V", "mnef", "T", "efij", 1.0, beta=0.0)]
+    _, ot = O.build_workload(w)
+    O.run_workload(w, ot)
+    ctx, gsp, gt = build_gpu(gpu_lib, w, 1)
+    assert gt["V"].n_slabs == 2
+    for prec, tol in (("f64", 1e-12), ("ozaki_bf16", 1e-10)):
+        out = ctx.tensor(gt["V"].modes, 2, "spin")
+        ctx.cholesky_form(gt["V"], out, prec)
+        gw.Runner(ctx, w, gsp, gt).run(prec, 0)
+        ctx.sync()
+        ev = rel_err(gpu_to_oracle_layout(out, ot["V"]), ot["V"].data)
+        ew = rel_err(gpu_to_oracle_layout(gt["W"], ot["W"]), ot["W"].data)
+        print(f"oovv-shaped R tile {r_tile} {prec}: V {ev:.3e} W {ew:.3e}")
+        assert ev <= tol and ew <= tol
+
+
 # ------------------------------------------------------------ full size, sampled
 
 @pytest.mark.slow
