@@ -1,7 +1,8 @@
-"""Write tests/golden/oracle_ladder_o8_v32.json from the FP64 oracle only.
+"""Write tests/golden/oracle_ladder_o8_v32.json and oracle_cholesky_ladder_o8_v32.json from the FP64
+oracle only.
 
-Regression values for the 8/32 spin-orbital ladder (tiles 4/8): norm of R and
-two scalar contractions.  Run from the repository root:
+Regression values for the 8/32 spin-orbital ladder (tiles 4/8), with V_vvvv stored and with V_vvvv formed
+from 80 Cholesky vectors (Eq. cc12): norms and scalar contractions.  Run from the repository root:
     python tests/golden/make_golden.py
 """
 import json
@@ -28,6 +29,22 @@ def main():
         "n_elems_V_vvvv": int(T["V_vvvv"].n_elems),
     }
     with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "oracle_ladder_o8_v32.json"), "w") as f:
+        json.dump(out, f, indent=1)
+
+    w = wl.cholesky_ladder_o8_v32()
+    _, T = O.build_workload(w)
+    O.run_workload(w, T)
+    out = {
+        "workload": "Cholesky ladder O=8 V=32 tiles 4/8, 80 vectors in tiles of 24, seed %d" % w.seed,
+        "norm_X": O.norm(T["X"]),
+        "norm_V": O.norm(T["V_chol"]),
+        "norm_R": O.norm(T["R"]),
+        "R_dot_T": O.energy(1.0, T["R"], "abij", T["T"], "abij"),
+        "n_elems_X": int(T["X"].n_elems),
+        "n_elems_V": int(T["V_chol"].n_elems),
+    }
+    with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "oracle_cholesky_ladder_o8_v32.json"),
+              "w") as f:
         json.dump(out, f, indent=1)
 
 

@@ -197,3 +197,16 @@ def test_pins_catch_planted_cholesky_mistakes(mutant, tmp_path):
     with O.using_library(str(lib)):
         caught = not _pins_hold()
     assert caught, f"planted mistake {mutant!r} was not caught"
+
+
+def test_oracle_cholesky_regression_values():
+    import json
+
+    g = json.load(open(os.path.join(HERE, "golden", "oracle_cholesky_ladder_o8_v32.json")))
+    w = wl.cholesky_ladder_o8_v32()
+    _, t = O.build_workload(w)
+    O.run_workload(w, t)
+    assert t["X"].n_elems == g["n_elems_X"] and t["V_chol"].n_elems == g["n_elems_V"]
+    for key, val in (("norm_X", O.norm(t["X"])), ("norm_V", O.norm(t["V_chol"])), ("norm_R", O.norm(t["R"])),
+                     ("R_dot_T", O.energy(1.0, t["R"], "abij", t["T"], "abij"))):
+        assert abs(val - g[key]) <= 1e-13 * abs(g[key]), key
