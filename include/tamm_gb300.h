@@ -357,6 +357,42 @@ TAMM_API tamm_status tamm_group_end(tamm_ctx* ctx);
 /* Close the open group without running what it recorded.  Errors: TAMM_EINVAL (no open group). */
 TAMM_API tamm_status tamm_group_cancel(tamm_ctx* ctx);
 
+/* Scheduler (Sec. III.A deferred execution: operations are added to a
+ * scheduler and run by execute(); its dependency analysis batches the
+ * independent operations of one level).  tamm_sched_contract / _add / _energy
+ * record an operation with the arguments of tamm_contract / tamm_add /
+ * tamm_energy_async (strings are copied; tensors must stay alive until the
+ * scheduler is destroyed).  Two operations conflict when one writes storage
+ * the other reads or writes (device byte ranges; a tensor without storage
+ * counts as itself; a contraction with beta = 1 or an add with beta = 1 reads
+ * its output; a contraction reading a Cholesky lambda tensor reads the
+ * Cholesky vectors; an energy writes its 8-byte result).  An operation's level
+ * is one more than the highest level of an earlier operation it conflicts
+ * with, else 0.  tamm_sched_execute enqueues the levels in order; inside a
+ * level, first the split-precision contractions that do not read a lambda
+ * tensor as one contraction group (tamm_group_begin/end), then the other
+ * contractions, the adds and the energies in recorded order.  Results equal
+ * running the operations in recorded order (bitwise: groups reproduce single
+ * contractions).  It may run inside a graph capture and any number of times.
+ * tamm_sched_levels reports the number of operations and levels and, if
+ * `op_level` is not NULL, each operation's level (n_ops entries); it needs no
+ * device.  Errors: TAMM_EINVAL (arguments, or a group open at execution);
+ * at execution, the status of the first operation that fails (its message in
+ * tamm_last_error; the operations after it do not run). */
+typedef struct tamm_sched tamm_sched;
+TAMM_API tamm_status tamm_sched_create(tamm_ctx* ctx, tamm_sched** out);
+TAMM_API tamm_status tamm_sched_contract(tamm_sched* s, double alpha, tamm_tensor* C, const char* lc, double beta,
+                                         const tamm_tensor* A, const char* la, const tamm_tensor* B, const char* lb,
+                                         int precision, int slices);
+TAMM_API tamm_status tamm_sched_add(tamm_sched* s, tamm_tensor* C, const char* lc, double beta,
+                                    const tamm_tensor* A, int n_terms, const char* const* la, const double* alpha);
+TAMM_API tamm_status tamm_sched_energy(tamm_sched* s, double alpha, const tamm_tensor* A, const char* la,
+                                       const tamm_tensor* B, const char* lb, double* result_device);
+TAMM_API tamm_status tamm_sched_levels(tamm_sched* s, int* n_ops, int* n_levels, int* op_level);
+TAMM_API tamm_status tamm_sched_execute(tamm_sched* s);
+/* NULL is ignored. */
+TAMM_API void tamm_sched_destroy(tamm_sched* s);
+
 /* CUDA-graph capture of a sequence of library calls on the context's stream,
  * replayed with one launch (Sec. III.A: the deferred operation list executed
  * as a unit).  The context must be on a created stream (not the legacy or

@@ -88,6 +88,13 @@ PROTOTYPES = [
     ("tamm_graph_launch", _i, [_vp]),
     ("tamm_graph_info", _i, [_vp, _i64p]),
     ("tamm_graph_destroy", None, [_vp]),
+    ("tamm_sched_create", _i, [_vp, ctypes.POINTER(_vp)]),
+    ("tamm_sched_contract", _i, [_vp, _d, _vp, _cp, _d, _vp, _cp, _vp, _cp, _i, _i]),
+    ("tamm_sched_add", _i, [_vp, _vp, _cp, _d, _vp, _i, ctypes.POINTER(_cp), _dp]),
+    ("tamm_sched_energy", _i, [_vp, _d, _vp, _cp, _vp, _cp, _vp]),
+    ("tamm_sched_levels", _i, [_vp, _ip, _ip, _ip]),
+    ("tamm_sched_execute", _i, [_vp]),
+    ("tamm_sched_destroy", None, [_vp]),
 ]
 
 
@@ -321,6 +328,10 @@ class Context:
         finally:
             holder.graph = self.graph_end()
 
+    def scheduler(self) -> "Scheduler":
+        """Deferred execution by dependency level (tamm_sched_*)."""
+        return Scheduler(self)
+
     def copy_from_host(self, T, host: np.ndarray) -> None:
         assert host.dtype == np.float64 and host.flags.c_contiguous and host.size >= T.n_elems
         self.check(self.lib.tamm_tensor_copy_from_host(self.handle, T.handle, ctypes.c_void_p(host.ctypes.data)),
@@ -330,6 +341,57 @@ class Context:
         assert host.dtype == np.float64 and host.flags.c_contiguous and host.size >= T.n_elems
         self.check(self.lib.tamm_tensor_copy_to_host(self.handle, T.handle, ctypes.c_void_p(host.ctypes.data)),
                    "tamm_tensor_copy_to_host")
+
+
+class Scheduler:
+    """Recorded operations run level by level (tamm_sched); the recording methods return self."""
+
+    def __init__(self, ctx: Context):
+        self.ctx = ctx
+        self._keep = []  # tensors recorded here stay alive as long as the scheduler
+        h = ctypes.c_void_p()
+        ctx.check(ctx.lib.tamm_sched_create(ctx.handle, ctypes.byref(h)), "tamm_sched_create")
+        self.handle = h
+
+    def contract(self, alpha, C, lc, beta, A, la, B, lb, precision="f64", slices: int = 0) -> "Scheduler":
+        prec = PREC[precision] if isinstance(precision, str) else int(precision)
+        self._keep += [C, A, B]
+        self.ctx.check(self.ctx.lib.tamm_sched_contract(self.handle, alpha, C.handle, lc.encode(), beta, A.handle,
+                                                        la.encode(), B.handle, lb.encode(), prec, slices),
+                       "tamm_sched_contract")
+        return self
+
+    def add(self, C, lc, beta, A, terms) -> "Scheduler":
+        n = len(terms)
+        las = (ctypes.c_char_p * n)(*[t[1].encode() for t in terms])
+        al = (ctypes.c_double * n)(*[float(t[0]) for t in terms])
+        self._keep += [C, A]
+        self.ctx.check(self.ctx.lib.tamm_sched_add(self.handle, C.handle, lc.encode(), beta, A.handle, n, las, al),
+                       "tamm_sched_add")
+        return self
+
+    def energy_async(self, alpha, A, la, B, lb, out_device_ptr: int) -> "Scheduler":
+        self._keep += [A, B]
+        self.ctx.check(self.ctx.lib.tamm_sched_energy(self.handle, alpha, A.handle, la.encode(), B.handle,
+                                                      lb.encode(), ctypes.c_void_p(out_device_ptr)),
+                       "tamm_sched_energy")
+        return self
+
+    def levels(self) -> list:
+        n, nl = ctypes.c_int(), ctypes.c_int()
+        self.ctx.check(self.ctx.lib.tamm_sched_levels(self.handle, ctypes.byref(n), ctypes.byref(nl), None),
+                       "tamm_sched_levels")
+        lev = (ctypes.c_int * max(n.value, 1))()
+        self.ctx.check(self.ctx.lib.tamm_sched_levels(self.handle, None, None, lev), "tamm_sched_levels")
+        return [lev[i] for i in range(n.value)]
+
+    def execute(self) -> None:
+        self.ctx.check(self.ctx.lib.tamm_sched_execute(self.handle), "tamm_sched_execute")
+
+    def __del__(self):
+        if getattr(self, "handle", None) and getattr(self.ctx, "handle", None):
+            self.ctx.lib.tamm_sched_destroy(self.handle)
+            self.handle = None
 
 
 class Graph:

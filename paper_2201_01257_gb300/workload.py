@@ -113,6 +113,27 @@ class Runner:
                 out[s.name] = r
         return out
 
+    def scheduled(self, precision="f64", slices: int = 0, steps=None, energy_out=None):
+        """The recipe's steps (default: all) recorded on a scheduler, which runs them by dependency level:
+        the split-precision contractions of a level as one grouped launch.  Energies need ``energy_out``
+        (a device double pointer)."""
+        T, sch = self.tensors, self.ctx.scheduler()
+        for step in steps if steps is not None else self.w.steps:
+            if isinstance(step, wl.EnergySpec):
+                if energy_out is None:
+                    raise ValueError(f"{step.name}: a scheduled energy needs a device result pointer")
+                sch.energy_async(step.alpha, T[step.a], step.la, T[step.b], step.lb, energy_out)
+            elif isinstance(step, wl.AddSpec):
+                sch.add(T[step.c], step.lc, step.beta, T[step.a], [(step.alpha, step.la)])
+            elif step.antisym:
+                X, lx = self.scratch_for(step)
+                sch.contract(step.alpha, X, lx, 0.0, T[step.a], step.la, T[step.b], step.lb, precision, slices)
+                sch.add(T[step.c], step.lc, step.beta, X, antisym_terms(step.lc, lx))
+            else:
+                sch.contract(step.alpha, T[step.c], step.lc, step.beta, T[step.a], step.la, T[step.b], step.lb,
+                             precision, slices)
+        return sch
+
     def autotune(self, target: float = 1e-10, steps=None) -> dict:
         """Autotune every contraction step (split precision); later runs with slices = 0 use the choices.
 

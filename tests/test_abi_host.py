@@ -224,3 +224,59 @@ def test_cholesky_lambda_refusals(hctx):
         V.bind(None)
     with pytest.raises(tg.TammError):
         hctx.space([(6, 2, 0)], tile=3)
+
+
+# ------------------------------------------------------------- scheduler levels
+
+def test_scheduler_levels_of_the_doubles_step(hctx):
+    from paper_2201_01257_gb300 import workload as gw
+
+    w = wl.ccsd_doubles_o40_v240()
+    gs, _ = spaces_for(hctx, w)
+    T = {name: hctx.tensor([gs[m] for m in t.modes], t.n_upper, t.sym) for name, t in w.tensors.items()}
+    sch = gw.Runner(hctx, w, gs, T).scheduled("ozaki_bf16", 0, energy_out=0x1000)
+    # recorded: ladder (R =), W = W0, W += V_oovv T, R += 1/4 T W, X = T V_ovvo, R += P(ab)P(ij) X,
+    # R += V_vvvo t1, E = 1/4 V_oovv T
+    assert sch.levels() == [0, 0, 1, 2, 0, 3, 4, 0]
+    # no device: execution fails at its first operation and reports it
+    with pytest.raises(tg.TammError) as e:
+        sch.execute()
+    assert e.value.status == tg.TAMM_ECUDA
+
+
+def test_scheduler_conflict_kinds(hctx):
+    o = hctx.space([(4, 1, 0), (4, -1, 0)], tile=2)
+    a = hctx.space([(6, 0, 0)], tile=3)
+    A, B, C, D = (hctx.tensor([o, o], 1) for _ in range(4))
+    sch = hctx.scheduler()
+    sch.contract(1.0, C, "ij", 0.0, A, "ik", B, "kj")   # 0: reads A B, writes C
+    sch.contract(1.0, D, "ij", 0.0, A, "ik", B, "kj")   # 0: independent (reads only shared)
+    sch.add(A, "ij", 0.0, D, [(1.0, "ji")])             # 1: writes A that op 0 reads (WAR), reads D (RAW)
+    sch.add(C, "ij", 1.0, B, [(2.0, "ij")])             # 1: beta = 1 reads and writes C (after op 0)
+    sch.energy_async(1.0, C, "ij", A, "ij", 0x1000)     # 2: reads C and A written at level 1
+    sch.energy_async(1.0, B, "ij", B, "ij", 0x1000)     # 3: same result slot as op 4 (WAW)
+    assert sch.levels() == [0, 0, 1, 1, 2, 3]
+    # a contraction reading a Cholesky lambda tensor reads its vectors
+    X = hctx.tensor([o, o, a], 1)
+    V = hctx.tensor_cholesky(X)
+    R = hctx.tensor([o, o, o, o], 2)
+    sch3 = hctx.scheduler()
+    R2 = hctx.tensor([o, o, o, o], 2)
+    sch3.contract(1.0, R2, "pqrs", 0.0, V, "pqtu", R, "turs")
+    sch3.add(X, "pqL", 0.0, X, [(1.0, "pqL")])  # writes X, which op 0 reads through V
+    sch3.contract(1.0, R, "pqrs", 0.0, V, "pqtu", R2, "turs")
+    assert sch3.levels() == [0, 1, 2]
+
+
+def test_scheduler_argument_errors(hctx):
+    o = hctx.space([(4, 1, 0), (4, -1, 0)], tile=2)
+    A = hctx.tensor([o, o], 1)
+    sch = hctx.scheduler()
+    with pytest.raises(tg.TammError):
+        sch.contract(1.0, A, "ijk", 0.0, A, "ik", A, "kj")
+    with pytest.raises(tg.TammError):
+        sch.add(A, "ij", 0.0, A, [])
+    with pytest.raises(tg.TammError):
+        sch.energy_async(1.0, A, "ij", A, "ij", 0)
+    assert sch.levels() == []
+    sch.execute()  # nothing recorded: nothing to do
