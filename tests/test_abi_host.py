@@ -280,3 +280,24 @@ def test_scheduler_argument_errors(hctx):
         sch.energy_async(1.0, A, "ij", A, "ij", 0)
     assert sch.levels() == []
     sch.execute()  # nothing recorded: nothing to do
+
+
+def test_cholesky_lambda_irrep_block_table(hctx):
+    # X with the spin + irrep rule over an aux index carrying all eight D2h irreps: the blocks some aux
+    # tile links are exactly the spin + irrep blocks of a 2|2 tensor (the oracle's rule)
+    import numpy as np_
+
+    rng = np_.random.default_rng(3)
+    vs = wl.irrep_space("virt", 64, rng, 4, 12)
+    aux = wl.SpaceSpec("aux", tuple((10, 0, g) for g in range(8)), tile=5)
+    w = wl.Workload("irrep_cholesky", 1, {"virt": vs, "aux": aux}, {})
+    gs, os_ = spaces_for(hctx, w)
+    X = hctx.tensor([gs["virt"], gs["virt"], gs["aux"]], 1, "spin_irrep")
+    V = hctx.tensor_cholesky(X)
+    R = O.Tensor([os_["virt"]] * 4, 2, "spin_irrep", alloc=False)
+    assert (V.n_blocks, V.n_elems) == (R.n_blocks, R.n_elems)
+    assert np.array_equal(V.block_tiles, R.block_tiles)
+    # with the aux index in irrep 0 only, X links only same-irrep pairs: fewer blocks than the rule allows
+    aux0 = hctx.space([(80, 0, 0)], 5)
+    X0 = hctx.tensor([gs["virt"], gs["virt"], aux0], 1, "spin_irrep")
+    assert 0 < hctx.tensor_cholesky(X0).n_blocks < R.n_blocks
