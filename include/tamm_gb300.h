@@ -357,9 +357,10 @@ TAMM_API tamm_status tamm_group_end(tamm_ctx* ctx);
 /* Close the open group without running what it recorded.  Errors: TAMM_EINVAL (no open group). */
 TAMM_API tamm_status tamm_group_cancel(tamm_ctx* ctx);
 
-/* Scheduler (Sec. III.A deferred execution: operations are added to a
- * scheduler and run by execute(); its dependency analysis batches the
- * independent operations of one level).  tamm_sched_contract / _add / _energy
+/* Scheduler (Sec. III.A: operations are declared and executed through a
+ * scheduler; Sec. III.B: its data-flow analysis marks operations that share a
+ * tensor one of them updates as conflicting, and a levelized execution runs
+ * each batch of independent operations together).  tamm_sched_contract / _add / _energy
  * record an operation with the arguments of tamm_contract / tamm_add /
  * tamm_energy_async (strings are copied; tensors must stay alive until the
  * scheduler is destroyed).  Two operations conflict when one writes storage

@@ -1,9 +1,10 @@
 // Scheduler: deferred execution of recorded operations by dependency level
-// (Sec. III.A: operations are added to a scheduler and run by execute(); the
-// runtime analyses their dependencies and batches the independent operations
-// of one level).  Host logic only: every operation runs through the same
-// entry points as a direct call, and the split-precision contractions of a
-// level run as one contraction group.
+// (Sec. III.A: operations are declared and run through a scheduler; Sec.
+// III.B: a data-flow analysis marks two operations as conflicting when they
+// share a tensor and one of them updates it, and a levelized execution runs
+// each batch of mutually independent operations together).  Host logic only:
+// every operation runs through the same entry points as a direct call, and
+// the split-precision contractions of a level run as one contraction group.
 #include <algorithm>
 #include <cstring>
 #include <new>
