@@ -301,3 +301,17 @@ def test_cholesky_lambda_irrep_block_table(hctx):
     aux0 = hctx.space([(80, 0, 0)], 5)
     X0 = hctx.tensor([gs["virt"], gs["virt"], aux0], 1, "spin_irrep")
     assert 0 < hctx.tensor_cholesky(X0).n_blocks < R.n_blocks
+
+
+def test_scheduler_puts_independent_ladders_in_one_level(hctx):
+    # the 32 ladder problems of the batch share no tensor: one level, i.e. one contraction group
+    sch = hctx.scheduler()
+    for k, (o, v) in enumerate(wl.ladder_batch_sizes()[:32]):
+        w = wl.ladder_problem(2 * max(o // 8, 2), 2 * max(v // 16, 4), 1 + k, 2, 4)  # small shapes: planning only
+        gs, _ = spaces_for(hctx, w)
+        T = {n: hctx.tensor([gs[m] for m in t.modes], t.n_upper, t.sym) for n, t in w.tensors.items()}
+        st = w.steps[0]
+        sch.contract(st.alpha, T[st.c], st.lc, st.beta, T[st.a], st.la, T[st.b], st.lb, "ozaki_bf16")
+        # the same problem's energy-style read of its output comes one level later
+        sch.energy_async(1.0, T["R"], "abij", T["T"], "abij", 0x1000 + 8 * k)
+    assert sch.levels() == [0, 1] * 32
