@@ -315,3 +315,21 @@ def test_scheduler_puts_independent_ladders_in_one_level(hctx):
         # the same problem's energy-style read of its output comes one level later
         sch.energy_async(1.0, T["R"], "abij", T["T"], "abij", 0x1000 + 8 * k)
     assert sch.levels() == [0, 1] * 32
+
+
+def test_header_is_plain_c(tmp_path):
+    # the boundary is a C ABI: the header compiles as strict C99 with no C++ or torch types
+    import shutil
+    import subprocess
+
+    if shutil.which("gcc") is None:
+        pytest.skip("no C compiler")
+    src = tmp_path / "use.c"
+    src.write_text('#include "tamm_gb300.h"\n'
+                   "int main(void) {\n"
+                   "  tamm_ctx* ctx = 0; tamm_tensor* t = 0; tamm_sched* s = 0; tamm_graph* g = 0;\n"
+                   "  (void)ctx; (void)t; (void)s; (void)g;\n"
+                   "  return TAMM_OK;\n"
+                   "}\n")
+    subprocess.check_call(["gcc", "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror",
+                           "-I", os.path.join(ROOT, "include"), "-c", str(src), "-o", str(tmp_path / "use.o")])
