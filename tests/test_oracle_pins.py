@@ -299,6 +299,137 @@ def test_label_bound_to_two_spaces_rejected(small):
         O.contract(1.0, R, "abij", 0.0, T["V_oovv"], "abef", T["T"], "efij")
 
 
+# -------------------------------------------------- spin + irrep (D2h) rule
+
+# Sec. III.A (user-defined non-zero check), read as D2h: the point group is abelian and
+# isomorphic to Z2^3, so its eight irreps are labelled 0..7 and the totally symmetric
+# irrep is 0.  The pins below never write the XOR rule: they use the eight characters
+# chi_s(g) = (-1)^popcount(s & g) of Z2^3 (Fourier analysis on the group) and the
+# group-averaging (Reynolds) projection onto invariant tensors.
+
+def _chi(s, g):
+    return -1.0 if bin(s & g).count("1") % 2 else 1.0
+
+
+def _irrep_groups(mult):
+    """alpha then beta groups, irrep g holding mult[g] orbitals in each spin."""
+    return [(m, sp, g) for sp in (1, -1) for g, m in enumerate(mult) if m]
+
+
+def _count_invariant(per_mode_mult):
+    """Orbital tuples (one orbital per mode) whose irreps multiply to the totally symmetric
+    irrep: (1/8) sum_s prod_modes (sum_g m_g chi_s(g)), the orthogonality of Z2^3's characters."""
+    total = 0.0
+    for s in range(8):
+        prod = 1.0
+        for mult in per_mode_mult:
+            prod *= sum(m * _chi(s, g) for g, m in enumerate(mult))
+        total += prod
+    return total / 8
+
+
+@pytest.mark.parametrize("mult_v,mult_o", [((2,) * 8, (1,) * 8), ((3, 1, 0, 2, 5, 1, 4, 2), (1, 2, 0, 1, 1, 0, 2, 1))])
+def test_irrep_storage_closed_form(mult_v, mult_o):
+    # Spin rule (3/8 of the spin patterns of a 2|2 tensor: aa|aa, bb|bb and the four mixed ones)
+    # times the character-sum count of totally symmetric irrep tuples; with every group split
+    # evenly over the eight irreps this is 1/8 of the spin-allowed entries, 3/64 of dense.
+    v = O.Space(_irrep_groups(mult_v), tile=1)
+    o = O.Space(_irrep_groups(mult_o), tile=1)
+    for modes, mults in (([v] * 4, [mult_v] * 4), ([v, v, o, o], [mult_v, mult_v, mult_o, mult_o])):
+        T = O.Tensor(modes, 2, "spin_irrep", alloc=False)
+        assert T.n_elems == 6 * _count_invariant(mults)
+    if len(set(mult_v)) == 1:
+        n = 2 * sum(mult_v)
+        T = O.Tensor([v] * 4, 2, "spin_irrep", alloc=False)
+        assert T.n_elems * 64 == 3 * n ** 4
+    # one index pair: an (upper, lower) matrix is nonzero only inside same-spin, same-irrep blocks
+    T2 = O.Tensor([v, o], 1, "spin_irrep", alloc=False)
+    assert T2.n_elems == 2 * sum(a * b for a, b in zip(mult_v, mult_o))
+
+
+def test_irrep_hand_listed_blocks():
+    # four alpha tiles in irreps 0, 3, 5, 6 (a closed subgroup): a 1|1 matrix keeps the diagonal
+    s4 = O.Space([(1, 1, 0), (1, 1, 3), (1, 1, 5), (1, 1, 6)], tile=1)
+    M = O.Tensor([s4, s4], 1, "spin_irrep", alloc=False)
+    assert M.block_tiles.tolist() == [[0, 0], [1, 1], [2, 2], [3, 3]]
+    # two alpha tiles in irreps 1 and 2: 1*1*2*2 etc. -- a 4-tuple is totally symmetric exactly
+    # when each irrep occurs an even number of times
+    s2 = O.Space([(2, 1, 1), (3, 1, 2)], tile_sizes=(2, 3))
+    F = O.Tensor([s2] * 4, 2, "spin_irrep", alloc=False)
+    want = [[0, 0, 0, 0], [0, 0, 1, 1], [0, 1, 0, 1], [0, 1, 1, 0],
+            [1, 0, 0, 1], [1, 0, 1, 0], [1, 1, 0, 0], [1, 1, 1, 1]]
+    assert F.block_tiles.tolist() == want
+    assert F.n_elems == 2 ** 4 + 6 * 2 * 2 * 3 * 3 + 3 ** 4
+    # irreps 1, 2, 3 in one alpha space: the product of 1, 2 and 3 is symmetric, so a 4-tuple holding
+    # all three would need a fourth tile in irrep 0, which the space lacks; what remains are
+    # (g, g, g, g) and the six arrangements of each pair {g, g, h, h}
+    s3 = O.Space([(1, 1, 1), (1, 1, 2), (1, 1, 3)], tile=1)
+    G = O.Tensor([s3] * 4, 2, "spin_irrep", alloc=False)
+    assert G.n_blocks == 3 + 3 * 6  # (g,g,g,g) and the six arrangements of each pair {g,g,h,h}
+
+
+def _reynolds(x, phases):
+    """Average of x over a finite group acting by per-mode diagonal phases: phases[k][m] is the
+    vector by which mode m's orbitals are multiplied under group element k."""
+    out = np.zeros(x.shape, dtype=complex)
+    for ph in phases:
+        y = x.astype(complex)
+        for m, p in enumerate(ph):
+            shape = [1] * x.ndim
+            shape[m] = -1
+            y = y * p.reshape(shape)
+        out += y
+    return out / len(phases)
+
+
+def _invariant_dense(spaces, n_upper, rng):
+    """Dense random tensor projected onto the tensors invariant under D2h (= Z2^3 characters of the
+    orbitals' irreps) and under spin rotation about z (U(1): upper modes carry exp(i t s), lower
+    exp(-i t s); t over nine angles, which resolves net spin |d| <= 4)."""
+    x = rng.standard_normal(tuple(s.n for s in spaces))
+    irr = [np.concatenate([[t[3]] * t[1] for t in s.tiles]).astype(int) for s in spaces]
+    spn = [np.concatenate([[t[2]] * t[1] for t in s.tiles]).astype(float) for s in spaces]
+    d2h = [[np.array([_chi(g, int(q)) for q in irr[m]]) for m in range(len(spaces))] for g in range(8)]
+    x = _reynolds(x, d2h).real
+    angles = 2 * np.pi * np.arange(9) / 9
+    u1 = [[np.exp(1j * t * spn[m] * (1 if m < n_upper else -1)) for m in range(len(spaces))] for t in angles]
+    return _reynolds(x, u1).real
+
+
+def _irrep_einsum_pin_holds(rng_seed=7) -> bool:
+    rng = np.random.default_rng(rng_seed)
+    v = O.Space(_irrep_groups((2, 1, 0, 1, 2, 1, 1, 0)), tile=1)
+    o = O.Space(_irrep_groups((1, 0, 1, 0, 0, 1, 0, 0)), tile=1)
+    Vd = _invariant_dense([v] * 4, 2, rng)
+    Td = _invariant_dense([v, v, o, o], 2, rng)
+    Vd[np.abs(Vd) < 1e-13] = 0.0
+    Td[np.abs(Td) < 1e-13] = 0.0
+    V = O.Tensor([v] * 4, 2, "spin_irrep")
+    T = O.Tensor([v, v, o, o], 2, "spin_irrep")
+    V.from_dense(Vd)
+    T.from_dense(Td)
+    # the stored blocks hold every entry an invariant tensor can have
+    if not (np.array_equal(V.to_dense(), Vd) and np.array_equal(T.to_dense(), Td)):
+        return False
+    R = O.Tensor([v, v, o, o], 2, "spin_irrep")
+    O.contract(0.5, R, "abij", 0.0, V, "abef", T, "efij")
+    ref = 0.5 * np.einsum("abef,efij->abij", Vd, Td)
+    # the product of invariant tensors is invariant: it vanishes outside R's stored blocks and
+    # equals the oracle inside them
+    mask = np.zeros(R.dense_shape(), bool)
+    lo, ext = R.block_lo_ext()
+    for b in range(R.n_blocks):
+        mask[tuple(slice(lo[b, m], lo[b, m] + ext[b, m]) for m in range(4))] = True
+    scale = np.abs(ref).max()
+    if not scale > 0 or np.abs(ref[~mask]).max(initial=0.0) > 1e-13 * scale:
+        return False
+    return bool(np.allclose(R.to_dense()[mask], ref[mask], rtol=0, atol=1e-14 * scale))
+
+
+def test_irrep_invariant_dense_einsum():
+    assert _irrep_einsum_pin_holds()
+
+
 # --------------------------------------------------------- mutation tests
 
 MUTANTS = {
@@ -308,6 +439,9 @@ MUTANTS = {
     "alpha_sign": ("out[e] = prev + alpha * acc[e];", "out[e] = prev - alpha * acc[e];"),
     "skip_second_tile_tuple": ("if (ab < 0 || bb < 0) continue;", "if (ab < 0 || bb < 0 || kt == 1) continue;"),
     "beta_ignored": ("double prev = (beta != 0.0 && c_in) ? beta * c_in[e] : 0.0;", "double prev = 0.0;"),
+    "irrep_ignored": ("if (T->sym == OR_SYM_SPIN_IRREP && x != 0) return 0;", ""),
+    "irrep_or_not_xor": ("x ^= T->sp[m]->irrep[tt[m]];", "x |= T->sp[m]->irrep[tt[m]];"),
+    "irrep_sum_not_xor": ("x ^= T->sp[m]->irrep[tt[m]];", "x += T->sp[m]->irrep[tt[m]];"),
 }
 
 
@@ -324,7 +458,12 @@ def _pins_hold() -> bool:
         ref = r0 + 0.5 * np.einsum("abef,efij->abij", V.to_dense(), T.to_dense())
         if V.n_elems * 8 != 3 * 12 ** 4:
             return False
-        return bool(np.allclose(R.to_dense(), ref, rtol=0, atol=1e-14))
+        if not np.allclose(R.to_dense(), ref, rtol=0, atol=1e-14):
+            return False
+        vi = O.Space(_irrep_groups((2,) * 8), tile=1)
+        if O.Tensor([vi] * 4, 2, "spin_irrep", alloc=False).n_elems * 64 != 3 * 32 ** 4:
+            return False
+        return _irrep_einsum_pin_holds()
     except O.OracleError:
         return False
 
