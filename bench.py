@@ -38,9 +38,9 @@ WORKLOAD = ("ccsd_doubles_O40_V240: vvvv ladder + W copy + intermediate + oooo l
             "T1 term + energy")
 SLICES = 6
 # DRAM bytes (read + write) per launch of the split-precision GEMM kernel, averaged over the five GEMM
-# launches of an O=40 V=240 doubles step, from the ncu launch list of this bench command (profiles/
-# launch_list_ccsd_doubles_O40_V240.md), keyed by the hash of the kernel sources it was taken on; a
-# changed kernel reports null until it is captured again.
+# launches of an O=40 V=240 doubles step, from an ncu capture of this bench command's GEMM launches,
+# keyed by the hash of the kernel sources it was taken on; a changed kernel reports null until it is
+# captured again.
 MEASURED_TRAFFIC = {"911d88a71fa162e1": 6.945e9}
 
 

@@ -12,10 +12,11 @@
  *  - Asynchrony: every operation is enqueued on the context's CUDA stream and
  *    returns at once, except the calls that hand a host result back
  *    (tamm_energy, tamm_norm, tamm_sync), which synchronise the stream first.
- *  - Device-side failures (a bounded wait that ran out, a bounds check in the
- *    checked build) are recorded in a device status word and reported by the
- *    next synchronising call as TAMM_ETIMEOUT / TAMM_ECHECK.  Kernels never
- *    trap.
+ *  - Device-side failures (a bounded wait that ran out) are recorded in a
+ *    device status word and reported by the next synchronising call as
+ *    TAMM_ETIMEOUT.  Kernels never trap: a kernel whose wait ran out stops its
+ *    own work, lets its copies in flight land, frees its tensor memory and
+ *    returns, so the context stays usable.
  *  - Tensors store only their nonzero blocks (sparsity-aware allocation,
  *    Sec. III.B): blocks in lexicographic tile order (mode 0 slowest), each
  *    block row-major over the modes in declared order, packed one after
@@ -50,7 +51,7 @@ typedef int tamm_status;
 #define TAMM_ECUDA 3        /* a CUDA runtime/driver call failed */
 #define TAMM_EUNSUPPORTED 4 /* valid request this build/device cannot run */
 #define TAMM_ETIMEOUT 5     /* a bounded device-side wait ran out */
-#define TAMM_ECHECK 6       /* a device-side bounds check failed (checked build) */
+#define TAMM_ECHECK 6       /* reserved: no call of this build returns it */
 #define TAMM_ELIMIT 7       /* a size exceeds a fixed limit of the call */
 
 /* Block-sparsity rule of a tensor (Sec. III.A: spin attributes on tiles and a
@@ -121,6 +122,15 @@ TAMM_API const char* tamm_last_error(const tamm_ctx* ctx);
                                     pairs into up to 8 consecutive ranges, computed in parallel into a
                                     workspace and added in range order (deterministic; a different
                                     rounding from the unsplit sum); 0 = never split */
+#define TAMM_OPT_WAIT_CYCLES 5 /* split precision: SM clock cycles a kernel waits for one dependency (an
+                                  operand copy, an MMA batch, a drained accumulator) before it records
+                                  TAMM_ETIMEOUT and stops; >= 1000, default 4,000,000,000 (about 2 s).
+                                  The wait for copies already in flight to land before a kernel exits
+                                  keeps the default */
+#define TAMM_OPT_TEST_WITHHOLD_COPY 6 /* failure-path test hook: 1 = in the next split-precision GEMM
+                                         launch, CTA 0 does not issue its first operand copy (nor arrive
+                                         on that stage), so the MMA issuer's wait for it runs out and the
+                                         launch records TAMM_ETIMEOUT; reset to 0 by that launch */
 /* Set option `option` to `value`.  Errors: TAMM_EINVAL (unknown option or value out of range). */
 TAMM_API tamm_status tamm_ctx_set_option(tamm_ctx* ctx, int option, int64_t value);
 
@@ -142,8 +152,8 @@ TAMM_API tamm_status tamm_ctx_profile(tamm_ctx* ctx, int enable);
  * summed device time in milliseconds and the number of timed launches.
  * `ms` and `launches` hold TAMM_KERNEL_CLASSES entries (either may be NULL). */
 TAMM_API tamm_status tamm_ctx_profile_read(tamm_ctx* ctx, double* ms, int64_t* launches);
-/* Synchronise the stream and report any device-side status (TAMM_ETIMEOUT,
- * TAMM_ECHECK) recorded since the last synchronising call, then clear it. */
+/* Synchronise the stream and report any device-side status (TAMM_ETIMEOUT)
+ * recorded since the last synchronising call, then clear it. */
 TAMM_API tamm_status tamm_sync(tamm_ctx* ctx);
 
 /* ----------------------------------------------------------- index spaces */
@@ -276,11 +286,41 @@ TAMM_API tamm_status tamm_contract_flops(tamm_ctx* ctx, const tamm_tensor* C, co
 TAMM_API tamm_status tamm_add(tamm_ctx* ctx, tamm_tensor* C, const char* lc, double beta, const tamm_tensor* A,
                      int n_terms, const char* const* la, const double* alpha);
 
+/* The same AddOp with every alpha[t] multiplied by the device scalar
+ * *scale_device (one double of device memory, 8-byte aligned, read by the
+ * kernel when it runs), so that a scale computed on the device, such as the
+ * incoming derivative of a scalar in reverse-mode differentiation, needs no
+ * host round trip.  Errors: as tamm_add; TAMM_EINVAL for a null or misaligned
+ * scale pointer. */
+TAMM_API tamm_status tamm_add_scaled(tamm_ctx* ctx, tamm_tensor* C, const char* lc, double beta,
+                                     const tamm_tensor* A, int n_terms, const char* const* la, const double* alpha,
+                                     const double* scale_device);
+
+/* Adjoint of a MultOp (Sec. III.A, grammar figure "tensor_ops", rule
+ * alpha * A * B): for the forward C(lc) = alpha * sum A(la) * B(lb) and an
+ * incoming adjoint dC with C's block structure,
+ *     dA(la) = beta * dA(la) + alpha * sum dC(lc) * B(lb)
+ *     dB(lb) = beta * dB(lb) + alpha * sum A(la) * dC(lc)
+ * (either of dA, dB may be NULL).  The adjoint of a MultOp is again a MultOp
+ * whose label roles are exchanged: the labels summed in the forward become
+ * free labels of the result, and the free labels of the other operand become
+ * summed.  Each runs through the same block-sparse path as tamm_contract
+ * (`precision`, `slices` as there; stored blocks of dA/dB only).  dA must have
+ * A's spaces and block table, dB B's (e.g. tamm_tensor_create_permuted with the
+ * identity permutation), so that gradients share their operands' packed layout.
+ * Derivatives are taken with respect to every stored entry as an independent
+ * variable.  Errors: TAMM_EINVAL (the forward's labels or spaces, a block table
+ * that differs, aliasing, beta not 0 or 1), as tamm_contract otherwise. */
+TAMM_API tamm_status tamm_contract_adjoint(tamm_ctx* ctx, double alpha, const tamm_tensor* dC, const char* lc,
+                                           const tamm_tensor* A, const char* la, const tamm_tensor* B,
+                                           const char* lb, tamm_tensor* dA, tamm_tensor* dB, double beta,
+                                           int precision, int slices);
+
 /* Full contraction to a scalar (Sec. III.A: inner products / reductions):
  *     result = alpha * sum over all entries A(la) * B(lb)
  * with lb a permutation of la.  FP64, deterministic summation order.
  * `result_host` receives the value after the stream is synchronised.
- * Errors: TAMM_EINVAL, TAMM_ECUDA, TAMM_ETIMEOUT/TAMM_ECHECK (pending device status). */
+ * Errors: TAMM_EINVAL, TAMM_ECUDA, TAMM_ETIMEOUT (pending device status). */
 TAMM_API tamm_status tamm_energy(tamm_ctx* ctx, double alpha, const tamm_tensor* A, const char* la, const tamm_tensor* B,
                         const char* lb, double* result_host);
 /* Same, asynchronous: writes the value to `result_device` (one double of device memory). */
@@ -303,12 +343,16 @@ TAMM_API tamm_status tamm_norm_async(tamm_ctx* ctx, const tamm_tensor* t, double
  * result is one double of device memory written by the call.  Nothing is
  * allocated: the partial sums live in a fixed 256 KB array inside the library
  * that every device using the library holds until the process exits.  The
- * first call on a device looks that array's device address up, so make it
- * before any stream capture.  All calls on a device share the array, so calls
- * whose kernels overlap on the GPU (e.g. on two streams) race and must be
- * serialised by the caller.  Limit: n <= 2^29 (536,870,912 doubles).
- * Errors: TAMM_EINVAL (n < 0 or a null pointer), TAMM_ELIMIT (n above the
- * limit), TAMM_ECUDA (no usable current device or a failed launch). */
+ * first call on a device looks that array's device address up and keeps it
+ * for the life of the process, so make it before any stream capture; the kept
+ * address does not survive a device reset (cudaDeviceReset) or a recreated
+ * primary context, after which this call must not be used in that process.
+ * All calls on a device share the array, so calls whose kernels overlap on
+ * the GPU (e.g. on two streams) race and must be serialised by the caller.
+ * Limit: n <= 2^29 (536,870,912 doubles).
+ * Errors: TAMM_EINVAL (n < 0, a null pointer, or a pointer that is not 8-byte
+ * aligned; refused before any launch), TAMM_ELIMIT (n above the limit),
+ * TAMM_ECUDA (no usable current device or a failed launch). */
 TAMM_API tamm_status tamm_norm_noalloc(const double* x_device, int64_t n, double* result_device, void* stream);
 
 /* Autotuner of the split-precision path (TAMM_PREC_OZAKI_BF16) for one

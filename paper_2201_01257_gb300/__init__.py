@@ -30,7 +30,7 @@ TAMM_SYM_DENSE, TAMM_SYM_SPIN, TAMM_SYM_SPIN_IRREP = 0, 1, 2
 TAMM_PREC_F64, TAMM_PREC_OZAKI_BF16, TAMM_PREC_OZAKI_I8, TAMM_PREC_BF16X3 = 0, 1, 2, 3
 KERNEL_CLASSES = ("add", "reduce", "gemm_f64", "slice", "gemm_ozaki", "split_reduce")
 (TAMM_OPT_OZAKI_CHUNK_K, TAMM_OPT_OZAKI_PERSISTENT, TAMM_OPT_OZAKI_TILE_POLICY, TAMM_OPT_OZAKI_PANELS,
- TAMM_OPT_OZAKI_SPLIT_K) = range(5)
+ TAMM_OPT_OZAKI_SPLIT_K, TAMM_OPT_WAIT_CYCLES, TAMM_OPT_TEST_WITHHOLD_COPY) = range(7)
 SYM = {"dense": TAMM_SYM_DENSE, "spin": TAMM_SYM_SPIN, "spin_irrep": TAMM_SYM_SPIN_IRREP}
 PREC = {"f64": TAMM_PREC_F64, "ozaki_bf16": TAMM_PREC_OZAKI_BF16, "ozaki_i8": TAMM_PREC_OZAKI_I8,
         "bf16x3": TAMM_PREC_BF16X3}
@@ -74,6 +74,8 @@ PROTOTYPES = [
     ("tamm_contract", _i, [_vp, _d, _vp, _cp, _d, _vp, _cp, _vp, _cp, _i, _i]),
     ("tamm_contract_flops", _i, [_vp, _vp, _cp, _vp, _cp, _vp, _cp, _dp]),
     ("tamm_add", _i, [_vp, _vp, _cp, _d, _vp, _i, ctypes.POINTER(_cp), _dp]),
+    ("tamm_add_scaled", _i, [_vp, _vp, _cp, _d, _vp, _i, ctypes.POINTER(_cp), _dp, _vp]),
+    ("tamm_contract_adjoint", _i, [_vp, _d, _vp, _cp, _vp, _cp, _vp, _cp, _vp, _vp, _d, _i, _i]),
     ("tamm_energy", _i, [_vp, _d, _vp, _cp, _vp, _cp, _dp]),
     ("tamm_energy_async", _i, [_vp, _d, _vp, _cp, _vp, _cp, _vp]),
     ("tamm_norm", _i, [_vp, _vp, _dp]),
@@ -232,6 +234,16 @@ class Context:
         self.check(self.lib.tamm_contract(self.handle, alpha, C.handle, lc.encode(), beta, A.handle, la.encode(),
                                           B.handle, lb.encode(), prec, slices), "tamm_contract")
 
+    def contract_adjoint(self, alpha, dC, lc, A, la, B, lb, dA=None, dB=None, beta=0.0, precision="f64",
+                         slices: int = 0) -> None:
+        """dA(la) = beta dA + alpha dC(lc) B(lb), dB(lb) = beta dB + alpha A(la) dC(lc): the adjoint of
+        C(lc) = alpha A(la) B(lb); dA / dB (either may be None) have A's / B's block tables."""
+        prec = PREC[precision] if isinstance(precision, str) else int(precision)
+        self.check(self.lib.tamm_contract_adjoint(self.handle, alpha, dC.handle, lc.encode(), A.handle, la.encode(),
+                                                  B.handle, lb.encode(), dA.handle if dA is not None else None,
+                                                  dB.handle if dB is not None else None, beta, prec, slices),
+                   "tamm_contract_adjoint")
+
     def flops(self, C, lc, A, la, B, lb) -> float:
         f = ctypes.c_double()
         self.check(self.lib.tamm_contract_flops(self.handle, C.handle, lc.encode(), A.handle, la.encode(), B.handle,
@@ -244,6 +256,14 @@ class Context:
         las = (ctypes.c_char_p * n)(*[t[1].encode() for t in terms])
         al = (ctypes.c_double * n)(*[float(t[0]) for t in terms])
         self.check(self.lib.tamm_add(self.handle, C.handle, lc.encode(), beta, A.handle, n, las, al), "tamm_add")
+
+    def add_scaled(self, C, lc, beta, A, terms, scale_device_ptr: int) -> None:
+        """As ``add`` with every alpha multiplied by the device double at ``scale_device_ptr``."""
+        n = len(terms)
+        las = (ctypes.c_char_p * n)(*[t[1].encode() for t in terms])
+        al = (ctypes.c_double * n)(*[float(t[0]) for t in terms])
+        self.check(self.lib.tamm_add_scaled(self.handle, C.handle, lc.encode(), beta, A.handle, n, las, al,
+                                            ctypes.c_void_p(scale_device_ptr)), "tamm_add_scaled")
 
     def energy(self, alpha, A, la, B, lb) -> float:
         r = ctypes.c_double()

@@ -44,8 +44,12 @@ __device__ __forceinline__ void digits_step(const AddBlock& B, Digits& d) {
 __global__ void __launch_bounds__(256) add_kernel(double* __restrict__ dst, const double* __restrict__ src,
                                                   const AddBlock* __restrict__ blocks,
                                                   const ChunkItem* __restrict__ items, int n_terms, double beta,
-                                                  Alpha4 alpha) {
+                                                  Alpha4 alpha, const double* __restrict__ scale) {
   const ChunkItem it = items[blockIdx.x];
+  if (scale) {  // alpha_t * (*scale), read once per thread
+    const double sc = *scale;
+    for (int t = 0; t < n_terms; ++t) alpha.v[t] *= sc;
+  }
   const AddBlock& B = blocks[it.block];
   const int64_t end = min(B.n, it.start + (int64_t)kChunk);
   const int nm = B.nm;
@@ -252,12 +256,13 @@ __global__ void __launch_bounds__(256) gemm_f64_kernel(const double* __restrict_
 }  // namespace
 
 cudaError_t launch_add(tamm_ctx* ctx, double* dst, const double* src, const AddBlock* blocks,
-                       const ChunkItem* items, int64_t n_items, int n_terms, double beta, const double* alpha_host) {
+                       const ChunkItem* items, int64_t n_items, int n_terms, double beta, const double* alpha_host,
+                       const double* scale_device) {
   if (n_items == 0) return cudaSuccess;
   Alpha4 al{};
   for (int t = 0; t < n_terms; ++t) al.v[t] = alpha_host[t];
   kernel_begin(ctx, TAMM_KERNEL_ADD);
-  add_kernel<<<(unsigned)n_items, 256, 0, ctx->stream>>>(dst, src, blocks, items, n_terms, beta, al);
+  add_kernel<<<(unsigned)n_items, 256, 0, ctx->stream>>>(dst, src, blocks, items, n_terms, beta, al, scale_device);
   kernel_end(ctx, TAMM_KERNEL_ADD);
   return cudaGetLastError();
 }

@@ -59,6 +59,8 @@ __global__ void __launch_bounds__(1024) noalloc_final_kernel(const double* __res
 
 extern "C" tamm_status tamm_norm_noalloc(const double* x_device, int64_t n, double* result_device, void* stream) {
   if (n < 0 || !result_device || (n > 0 && !x_device)) return TAMM_EINVAL;
+  // a double load or store through a pointer that is not 8-byte aligned would fault on the GPU
+  if ((reinterpret_cast<uintptr_t>(x_device) | reinterpret_cast<uintptr_t>(result_device)) % 8) return TAMM_EINVAL;
   if (n > kNoallocMaxElems) return TAMM_ELIMIT;
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNoallocMaxDevices) {

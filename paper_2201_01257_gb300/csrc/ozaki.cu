@@ -137,7 +137,9 @@ __device__ __forceinline__ void pack_float3(const double x0, const double x1, ui
   for (int k = 0; k < 3; ++k) w[k] = b[k][0] | (b[k][1] << 16);
 }
 
-constexpr long long kSliceWaitCycles = 4000000000ll;  // ~2 s at 2 GHz: a bounded wait gives up after this
+// ~2 s at 2 GHz: how long a kernel waits for copies already in flight to land before it exits (the
+// dependency waits take their limit from the launch, TAMM_OPT_WAIT_CYCLES)
+constexpr long long kDrainWaitCycles = 4000000000ll;
 
 // One CTA (W = blockDim.x / 32 warps) slices rows [r0, r0+nr) of one block.
 // Dense summed range (every row one contiguous run): one warp per row, nr <=
@@ -158,7 +160,8 @@ __global__ void __launch_bounds__(256) ozaki_slice_kernel(const double* __restri
                                                           const SliceBlock* __restrict__ blocks,
                                                           const SliceItem* __restrict__ items,
                                                           uint8_t* __restrict__ tiles, int32_t* __restrict__ exps,
-                                                          int kbuf, int bulk, int* __restrict__ status) {
+                                                          int kbuf, int bulk, int* __restrict__ status,
+                                                          long long wait_cycles) {
   extern __shared__ __align__(16) double rowbuf[];
   __shared__ unsigned long long rmax[kOzSliceMaxRows];
   __shared__ int rexp[kOzSliceMaxRows];
@@ -199,7 +202,7 @@ __global__ void __launch_bounds__(256) ozaki_slice_kernel(const double* __restri
           const long long t0 = clock64();
           bool ok = true;
           while (!sm100::mbar_try_wait(&wbar[warp], 0)) {
-            if (clock64() - t0 > kSliceWaitCycles) {
+            if (clock64() - t0 > wait_cycles) {
               ok = false;
               break;
             }
@@ -207,7 +210,7 @@ __global__ void __launch_bounds__(256) ozaki_slice_kernel(const double* __restri
           if (!__all_sync(0xffffffffu, ok)) {
             if (lane == 0) atomicExch(status, TAMM_ETIMEOUT);
             const long long t1 = clock64();  // the copy must land before the CTA may exit
-            while (!sm100::mbar_try_wait(&wbar[warp], 0) && clock64() - t1 < kSliceWaitCycles) {
+            while (!sm100::mbar_try_wait(&wbar[warp], 0) && clock64() - t1 < kDrainWaitCycles) {
             }
             return;
           }
@@ -327,6 +330,8 @@ __global__ void __launch_bounds__(256) ozaki_slice_kernel(const double* __restri
 struct OzParams {
   int64_t n_items;
   int* status;
+  long long wait_cycles;  // limit of every dependency wait (the drains before exit keep kDrainWaitCycles)
+  int withhold;           // failure-path test hook: CTA 0 skips its first operand copy
   int stages;
   int chunk_tiles;  // K tiles per exact accumulation chunk (<= kOzChunkTiles)
   int n_problems;
@@ -342,7 +347,6 @@ constexpr int kThreads = 128 + 32 * kEpiWarps;
 constexpr int kRegsLow = 40;
 constexpr int kRegsHigh = 232;
 constexpr int kRegsLaunchNeeded = (128 * kRegsLow + 256 * kRegsHigh + kThreads - 1) / kThreads;
-constexpr long long kWaitCycles = 4000000000ll;  // ~2 s at 2 GHz: a bounded wait gives up after this
 
 // Accumulator buffers in the 512 TMEM columns: each holds four regions of H
 // columns, so items with H <= 64 keep two (H <= 32: four) chunks in flight
@@ -354,12 +358,12 @@ __device__ __forceinline__ uint32_t acc_buffers(uint32_t H) {
 }
 
 __device__ __forceinline__ bool wait_bounded(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
-                                             int* status) {
+                                             int* status, long long limit) {
   const long long t0 = clock64();
   uint32_t ns = 16;
   while (!sm100::mbar_try_wait(bar, parity)) {
     if (*abort_flag) return false;
-    if (clock64() - t0 > kWaitCycles) {
+    if (clock64() - t0 > limit) {
       *abort_flag = 1;
       atomicExch(status, TAMM_ETIMEOUT);
       return false;
@@ -495,6 +499,7 @@ __global__ void __launch_bounds__(kThreads, 1) ozaki_gemm_kernel(const __grid_co
     if (lane == 0) {
       int stage = 0;
       uint32_t phase = 0, issued_mask = 0, issued_parity = 0;
+      bool withhold = p.withhold != 0 && blockIdx.x == 0;  // test hook: leave the first stage unfilled
       for (int64_t i = blockIdx.x; i < p.n_items && !*abort_flag; i += gridDim.x) {
         const int q = problem_of(p, i);
         const OzItem it = p.problems[q].items[i - p.problems[q].item_begin];
@@ -511,13 +516,18 @@ __global__ void __launch_bounds__(kThreads, 1) ozaki_gemm_kernel(const __grid_co
           const uint8_t* a = a_tiles + tk.a_off + (size_t)((int64_t)it.mt * tk.k_tiles) * half_bytes;
           const uint8_t* b = b_tiles + tk.b_off + (size_t)((int64_t)it.nt * tk.k_tiles) * b_bytes;
           for (int kt = 0; kt < tk.k_tiles; ++kt) {
-            if (!wait_bounded(&empty[stage], phase ^ 1u, abort_flag, p.status)) break;
-            uint8_t* sa = smem + (size_t)stage * 2 * half_bytes;
-            sm100::mbar_arrive_expect_tx(&full[stage], half_bytes + b_bytes);
-            sm100::bulk_g2s(sa, a + (size_t)kt * half_bytes, half_bytes, &full[stage]);
-            sm100::bulk_g2s(sa + half_bytes, b + (size_t)kt * b_bytes, b_bytes, &full[stage]);
-            issued_mask |= 1u << stage;
-            issued_parity = (issued_parity & ~(1u << stage)) | (phase << stage);
+            if (!wait_bounded(&empty[stage], phase ^ 1u, abort_flag, p.status, p.wait_cycles)) break;
+            if (withhold) {
+              // no copy and no arrival: the MMA issuer's wait on this stage cannot end
+              withhold = false;
+            } else {
+              uint8_t* sa = smem + (size_t)stage * 2 * half_bytes;
+              sm100::mbar_arrive_expect_tx(&full[stage], half_bytes + b_bytes);
+              sm100::bulk_g2s(sa, a + (size_t)kt * half_bytes, half_bytes, &full[stage]);
+              sm100::bulk_g2s(sa + half_bytes, b + (size_t)kt * b_bytes, b_bytes, &full[stage]);
+              issued_mask |= 1u << stage;
+              issued_parity = (issued_parity & ~(1u << stage)) | (phase << stage);
+            }
             if (++stage == stages) {
               stage = 0;
               phase ^= 1u;
@@ -529,7 +539,7 @@ __global__ void __launch_bounds__(kThreads, 1) ozaki_gemm_kernel(const __grid_co
       for (int s = 0; s < stages; ++s) {
         if (!(issued_mask >> s & 1u)) continue;
         const long long t0 = clock64();
-        while (!sm100::mbar_try_wait(&full[s], (issued_parity >> s) & 1u) && clock64() - t0 < kWaitCycles) {
+        while (!sm100::mbar_try_wait(&full[s], (issued_parity >> s) & 1u) && clock64() - t0 < kDrainWaitCycles) {
         }
       }
     }
@@ -553,7 +563,7 @@ __global__ void __launch_bounds__(kThreads, 1) ozaki_gemm_kernel(const __grid_co
           // another buffer layout: every buffer still being drained must be free first
           for (int b = 0; b < kAccBufs && ok; ++b)
             if ((acc_used >> b) & 1u)
-              ok = wait_bounded(&acc_empty[b], ((acc_parity >> b) & 1u) ^ 1u, abort_flag, p.status);
+              ok = wait_bounded(&acc_empty[b], ((acc_parity >> b) & 1u) ^ 1u, abort_flag, p.status, p.wait_cycles);
           if (!ok) break;
           buf = 0;
           cur_H = H;
@@ -573,13 +583,17 @@ __global__ void __launch_bounds__(kThreads, 1) ozaki_gemm_kernel(const __grid_co
             const bool last = ++in_chunk == p.chunk_tiles || kt + 1 == k_tiles;
             if (last) in_chunk = 0;
             if (first) {
-              if (!wait_bounded(&acc_empty[buf], ((acc_parity >> buf) & 1u) ^ 1u, abort_flag, p.status)) {
+              if (!wait_bounded(&acc_empty[buf], ((acc_parity >> buf) & 1u) ^ 1u, abort_flag, p.status,
+                                p.wait_cycles)) {
                 ok = false;
                 break;
               }
               sm100::tc_fence_after();
             }
-            if (!wait_bounded(&full[stage], phase, abort_flag, p.status)) { ok = false; break; }
+            if (!wait_bounded(&full[stage], phase, abort_flag, p.status, p.wait_cycles)) {
+              ok = false;
+              break;
+            }
             sm100::tc_fence_after();
             // descriptor start addresses count 16-byte units and stay below 2^14, so stage and
             // operand offsets add straight onto the stage-0 descriptor
@@ -605,7 +619,7 @@ __global__ void __launch_bounds__(kThreads, 1) ozaki_gemm_kernel(const __grid_co
       // all issued MMAs must finish before TMEM is released
       sm100::mma_commit(drain);
       const long long t0 = clock64();
-      while (!sm100::mbar_try_wait(drain, 0) && clock64() - t0 < kWaitCycles) {
+      while (!sm100::mbar_try_wait(drain, 0) && clock64() - t0 < kDrainWaitCycles) {
       }
     }
     __syncwarp();
@@ -694,7 +708,7 @@ __global__ void __launch_bounds__(kThreads, 1) ozaki_gemm_kernel(const __grid_co
         const float sA = (ea == kOzExpZero) ? 0.0f : pow2f(ea - Eref);
         const int n_chunks = ok ? (k_tiles + p.chunk_tiles - 1) / p.chunk_tiles : 0;
         for (int ck = 0; ck < n_chunks; ++ck) {
-          if (!wait_bounded(&acc_full[buf], (acc_parity >> buf) & 1u, abort_flag, p.status)) {
+          if (!wait_bounded(&acc_full[buf], (acc_parity >> buf) & 1u, abort_flag, p.status, p.wait_cycles)) {
             ok = false;
             break;
           }
@@ -834,9 +848,8 @@ static cudaError_t slice_dispatch(tamm_ctx* ctx, const double* src, const SliceB
     }
   }
   const int bulk = (reinterpret_cast<uintptr_t>(src) & 15) == 0 ? 1 : 0;
-  ozaki_slice_kernel<S, kFloat><<<(unsigned)n_items, 32 * warps, smem, ctx->stream>>>(src, blocks, items, tiles,
-                                                                                      exps, kbuf, bulk,
-                                                                                      ctx->d_status);
+  ozaki_slice_kernel<S, kFloat><<<(unsigned)n_items, 32 * warps, smem, ctx->stream>>>(
+      src, blocks, items, tiles, exps, kbuf, bulk, ctx->d_status, ctx->oz_wait_cycles);
   return cudaGetLastError();
 }
 
@@ -917,6 +930,9 @@ cudaError_t launch_ozaki_gemm(tamm_ctx* ctx, OzProblem* problems, const int64_t*
   OzParams p{};  // the whole problem table travels as the kernel's parameter block
   p.n_items = n_items;
   p.status = ctx->d_status;
+  p.wait_cycles = ctx->oz_wait_cycles;
+  p.withhold = ctx->oz_test_withhold;
+  ctx->oz_test_withhold = 0;  // the hook applies to one launch
   p.stages = oz_stages(S);
   p.chunk_tiles = chunk_tiles;
   p.n_problems = n_problems;

@@ -229,6 +229,16 @@ extern "C" tamm_status tamm_ctx_set_option(tamm_ctx* ctx, int option, int64_t va
       ctx->oz_persistent = value != 0;
       return;
     }
+    if (option == TAMM_OPT_WAIT_CYCLES) {
+      if (value < 1000) throw Error(TAMM_EINVAL, "wait limit must be at least 1000 cycles");
+      ctx->oz_wait_cycles = (long long)value;
+      return;
+    }
+    if (option == TAMM_OPT_TEST_WITHHOLD_COPY) {
+      if (value != 0 && value != 1) throw Error(TAMM_EINVAL, "withhold must be 0 or 1");
+      ctx->oz_test_withhold = (int)value;
+      return;
+    }
     throw Error(TAMM_EINVAL, "unknown option %d", option);
   });
 }
@@ -566,6 +576,52 @@ extern "C" tamm_status tamm_add(tamm_ctx* ctx, tamm_tensor* C, const char* lc, d
     require_device(ctx);
     no_group(ctx, "an add");
     run_add(ctx, C, lc, beta, A, n_terms, la, alpha);
+  });
+}
+
+extern "C" tamm_status tamm_add_scaled(tamm_ctx* ctx, tamm_tensor* C, const char* lc, double beta,
+                                       const tamm_tensor* A, int n_terms, const char* const* la, const double* alpha,
+                                       const double* scale_device) {
+  if (!ctx) return TAMM_EINVAL;
+  return guarded(ctx, [&] {
+    require_device(ctx);
+    no_group(ctx, "an add");
+    if (!scale_device) throw Error(TAMM_EINVAL, "add: null scale pointer");
+    if (((uintptr_t)scale_device) % 8) throw Error(TAMM_EINVAL, "add: scale pointer not 8-byte aligned");
+    run_add(ctx, C, lc, beta, A, n_terms, la, alpha, scale_device);
+  });
+}
+
+namespace {
+// dX must have X's spaces and block table, so that its packed layout is X's.
+void same_blocks(const tamm_tensor* X, const tamm_tensor* dX, const char* what) {
+  if (dX->nm != X->nm) throw Error(TAMM_EINVAL, "adjoint: %s has %d modes, its operand %d", what, dX->nm, X->nm);
+  for (int m = 0; m < X->nm; ++m)
+    if (dX->sp[m] != X->sp[m]) throw Error(TAMM_EINVAL, "adjoint: %s mode %d is on another space", what, m);
+  if (dX->n_blocks != X->n_blocks || dX->tiles != X->tiles)
+    throw Error(TAMM_EINVAL, "adjoint: %s stores other blocks than its operand", what);
+}
+}  // namespace
+
+extern "C" tamm_status tamm_contract_adjoint(tamm_ctx* ctx, double alpha, const tamm_tensor* dC, const char* lc,
+                                             const tamm_tensor* A, const char* la, const tamm_tensor* B,
+                                             const char* lb, tamm_tensor* dA, tamm_tensor* dB, double beta,
+                                             int precision, int slices) {
+  if (!ctx) return TAMM_EINVAL;
+  return guarded(ctx, [&] {
+    require_device(ctx);
+    if (!dC || !A || !B || !lc || !la || !lb) throw Error(TAMM_EINVAL, "adjoint: null argument");
+    if (!dA && !dB) throw Error(TAMM_EINVAL, "adjoint: neither dA nor dB requested");
+    if (ctx->group_active && precision != TAMM_PREC_OZAKI_BF16 && precision != TAMM_PREC_BF16X3)
+      throw Error(TAMM_EINVAL, "only split-precision contractions can be grouped");
+    // the forward contraction itself must be valid: its label analysis rejects what it would
+    (void)contract_flops(ctx, dC, lc, A, la, B, lb);
+    if (dA) same_blocks(A, dA, "dA");
+    if (dB) same_blocks(B, dB, "dB");
+    if (dA && dB && dA->data && dA->data == dB->data) throw Error(TAMM_EINVAL, "adjoint: dA and dB alias");
+    // the adjoint of a MultOp is a MultOp with the label roles exchanged
+    if (dA) run_contract(ctx, alpha, dA, la, beta, dC, lc, B, lb, precision, slices);
+    if (dB) run_contract(ctx, alpha, dB, lb, beta, A, la, dC, lc, precision, slices);
   });
 }
 

@@ -27,7 +27,8 @@ struct AddPlan : Plan {
   int64_t n_items = 0;
   int n_terms = 1;
   AddPlan(tamm_ctx* c, const tamm_tensor& D, const char* ld, const tamm_tensor& S, int terms, const char* const* ls);
-  void run(double* dst, const double* src, double beta, const double* alpha) const;
+  void run(double* dst, const double* src, double beta, const double* alpha,
+           const double* scale_device = nullptr) const;
 };
 
 std::vector<AddBlock> build_add_blocks(const tamm_tensor& D, const char* ld, const tamm_tensor& S, int n_terms,

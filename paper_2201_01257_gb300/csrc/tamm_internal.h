@@ -155,7 +155,7 @@ struct tamm_ctx {
   tamm::Allocator allocator;
   std::string last_error;
   uint64_t next_id = 1;
-  int* d_status = nullptr;    // device status word (TAMM_ETIMEOUT / TAMM_ECHECK)
+  int* d_status = nullptr;    // device status word (TAMM_ETIMEOUT)
   double* d_reduce = nullptr; // partial sums of reductions
   size_t reduce_cap = 0;
   double* h_result = nullptr; // pinned host double for synchronous results
@@ -168,6 +168,8 @@ struct tamm_ctx {
   int oz_tile_policy = 1;      // split precision: output columns per work item (TAMM_OPT_OZAKI_TILE_POLICY)
   bool oz_panels = true;       // split precision: concatenate output blocks sharing their A blocks
   bool oz_split = true;        // split precision: split long summed ranges of small contractions
+  long long oz_wait_cycles = 4000000000ll;  // limit of a kernel's dependency waits (TAMM_OPT_WAIT_CYCLES)
+  int oz_test_withhold = 0;    // failure-path test hook (TAMM_OPT_TEST_WITHHOLD_COPY), one launch
   int64_t launches = 0;    // kernels launched by this context
   bool profiling = false;  // bracket launches with CUDA events
   struct TimedLaunch {
@@ -203,7 +205,8 @@ void* ctx_scratch(tamm_ctx* ctx, size_t bytes);  // valid until the next ctx_scr
 // ------------------------------------------------------------ kernel launch
 // Implemented in kernels_f64.cu.  All launch on ctx->stream; return cudaError_t.
 cudaError_t launch_add(tamm_ctx* ctx, double* dst, const double* src, const AddBlock* blocks,
-                       const ChunkItem* items, int64_t n_items, int n_terms, double beta, const double* alpha_host);
+                       const ChunkItem* items, int64_t n_items, int n_terms, double beta, const double* alpha_host,
+                       const double* scale_device = nullptr);
 // V = X1(p,r,q,s) - X1(p,s,q,r) over the listed blocks; `smem_bytes` = 8 * max ns * (nr + 1), at most
 // kPairSmemMax (the default dynamic shared memory limit, so no attribute call is needed).
 constexpr size_t kPairSmemMax = 48 * 1024;

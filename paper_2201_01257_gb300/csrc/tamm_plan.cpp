@@ -106,8 +106,10 @@ AddPlan::AddPlan(tamm_ctx* c, const tamm_tensor& D, const char* ld, const tamm_t
   d_items = upload(items);
 }
 
-void AddPlan::run(double* dst, const double* src, double beta, const double* alpha) const {
-  cuda_check(launch_add(ctx, dst, src, d_blocks, d_items, n_items, n_terms, beta, alpha), "add kernel");
+void AddPlan::run(double* dst, const double* src, double beta, const double* alpha,
+                  const double* scale_device) const {
+  cuda_check(launch_add(ctx, dst, src, d_blocks, d_items, n_items, n_terms, beta, alpha, scale_device),
+             "add kernel");
 }
 
 template <class P, class... Args>
@@ -122,7 +124,7 @@ static P* cached(tamm_ctx* ctx, const std::string& key, Args&&... args) {
 static std::string tid(const tamm_tensor* T) { return std::to_string(T->id); }
 
 void run_add(tamm_ctx* ctx, tamm_tensor* C, const char* lc, double beta, const tamm_tensor* A, int n_terms,
-             const char* const* la, const double* alpha) {
+             const char* const* la, const double* alpha, const double* scale_device) {
   if (!C || !A || !lc || !la || !alpha) throw Error(TAMM_EINVAL, "add: null argument");
   if (n_terms < 1 || n_terms > kMaxAddTerms) throw Error(TAMM_EINVAL, "add: 1..%d terms", kMaxAddTerms);
   if (beta != 0.0 && beta != 1.0) throw Error(TAMM_EINVAL, "add: beta must be 0 or 1");
@@ -140,7 +142,7 @@ void run_add(tamm_ctx* ctx, tamm_tensor* C, const char* lc, double beta, const t
   require_data(C, "add");
   require_data(A, "add");
   AddPlan* p = cached<AddPlan>(ctx, key, *C, lc, *A, n_terms, la);
-  p->run(C->data, A->data, beta, alpha);
+  p->run(C->data, A->data, beta, alpha, scale_device);
 }
 
 // -------------------------------------------------------------- reductions

@@ -40,7 +40,7 @@ void run_contract(tamm_ctx* ctx, double alpha, tamm_tensor* C, const char* lc, d
 double contract_flops(tamm_ctx* ctx, const tamm_tensor* C, const char* lc, const tamm_tensor* A, const char* la,
                       const tamm_tensor* B, const char* lb);
 void run_add(tamm_ctx* ctx, tamm_tensor* C, const char* lc, double beta, const tamm_tensor* A, int n_terms,
-             const char* const* la, const double* alpha);
+             const char* const* la, const double* alpha, const double* scale_device = nullptr);
 void run_energy(tamm_ctx* ctx, double alpha, const tamm_tensor* A, const char* la, const tamm_tensor* B,
                 const char* lb, double* out_device);
 void run_norm(tamm_ctx* ctx, const tamm_tensor* t, double* out_device);

@@ -66,3 +66,8 @@ def test_noalloc_norm_sizes(gpu_lib):
                                  ctypes.c_void_p(stream)) == tg.TAMM_ELIMIT
     assert lib.tamm_norm_noalloc(ctypes.c_void_p(x.data_ptr()), -1, ctypes.c_void_p(out.data_ptr()),
                                  ctypes.c_void_p(stream)) == tg.TAMM_EINVAL
+    # pointers that are not 8-byte aligned are refused before any launch
+    assert lib.tamm_norm_noalloc(ctypes.c_void_p(x.data_ptr() + 4), 8, ctypes.c_void_p(out.data_ptr()),
+                                 ctypes.c_void_p(stream)) == tg.TAMM_EINVAL
+    assert lib.tamm_norm_noalloc(ctypes.c_void_p(x.data_ptr()), 8, ctypes.c_void_p(out.data_ptr() + 4),
+                                 ctypes.c_void_p(stream)) == tg.TAMM_EINVAL
