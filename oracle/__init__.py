@@ -6,8 +6,10 @@ lives in ``tamm_oracle.c`` (plain nested loops over nonzero blocks, FP64); this
 module only marshals arguments and runs workload recipes step by step.
 
 Every function here is pinned by ``tests/test_oracle_pins.py`` (brute-force
-dense einsum, closed-form block counts, identities, invariants); none is
-"parity unpinned".
+dense einsum, closed-form block counts, identities, invariants),
+``tests/test_oracle_cholesky.py`` (the Cholesky-built tensor) and
+``tests/test_oracle_triples.py`` (the (T) correction against the antisymmetrised
+construction of its amplitudes); none is "parity unpinned".
 """
 from __future__ import annotations
 
@@ -75,6 +77,8 @@ def _load(path: str | None = None):
             L.oracle_norm.argtypes = [vp, dp]
             L.oracle_norm.restype = d
             L.oracle_cholesky_v.argtypes = [vp, vp, dp, dp, i64p, i64]
+            L.oracle_triples_energy.argtypes = [vp, dp, vp, dp, vp, dp, vp, dp, vp, dp, dp, dp, dp]
+            L.oracle_triples_wy.argtypes = [vp, dp, vp, dp, vp, dp, vp, dp, vp, dp, i64, i64, i64, dp, dp]
             if path is not None:
                 return L
             _lib = L
@@ -296,6 +300,30 @@ def cholesky_v(V: Tensor, X: Tensor, blocks=None) -> None:
     else:
         bl = _i64(blocks)
         _chk(_load().oracle_cholesky_v(V._h, X._h, _pd(X.data), _pd(V.data), _p(bl), len(bl)), "cholesky_v")
+
+
+def _triples_args(T: dict):
+    return (T["T"]._h, _pd(T["T"].data), T["t1"]._h, _pd(T["t1"].data), T["V_ooov"]._h, _pd(T["V_ooov"].data),
+            T["V_vovv"]._h, _pd(T["V_vovv"].data), T["V_oovv"]._h, _pd(T["V_oovv"].data))
+
+
+def triples_energy(T: dict, eps_o, eps_v) -> float:
+    """E(T) = sum_{i<j<k, a<b<c} (W + Y) W / D (Eqs. cc14, tensort, tensort2) from the tensors T, t1,
+    V_ooov, V_vovv, V_oovv of a ``triples`` recipe and the orbital energies."""
+    eo = np.ascontiguousarray(eps_o, dtype=np.float64)
+    ev = np.ascontiguousarray(eps_v, dtype=np.float64)
+    r = ctypes.c_double()
+    _chk(_load().oracle_triples_energy(*_triples_args(T), _pd(eo), _pd(ev), ctypes.byref(r)), "triples_energy")
+    return r.value
+
+
+def triples_wy(T: dict, i: int, j: int, k: int) -> tuple:
+    """W (Eq. tensort) and Y (Eq. tensort2) of the occupied triple (i, j, k) over every (a, b, c)."""
+    nv = T["T"].modes[0].n
+    w = np.zeros((nv, nv, nv))
+    y = np.zeros((nv, nv, nv))
+    _chk(_load().oracle_triples_wy(*_triples_args(T), int(i), int(j), int(k), _pd(w), _pd(y)), "triples_wy")
+    return w, y
 
 
 def antisymmetrize_add(R: Tensor, lr: str, X: Tensor, alpha: float = 1.0) -> None:

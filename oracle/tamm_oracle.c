@@ -630,3 +630,210 @@ int oracle_cholesky_v(const otensor* V, const otensor* X, const double* x, doubl
   }
   return OR_OK;
 }
+
+/* --------------------------------------------------- (T) triples correction */
+
+/*
+ * Perturbative triples correction of CCSD(T) (Sec. IV.B, Eqs. cc14, tensort,
+ * tensort2), for real amplitudes:
+ *
+ *   E(T) = sum_{i<j<k} sum_{a<b<c} (W + Y) * W / D,
+ *   D    = e_i + e_j + e_k - e_a - e_b - e_c,
+ *
+ * where W = <Phi_ijk^abc| V_N T2 |Phi> is the eighteen-term sum of Eq. tensort
+ * (nine terms summed over an occupied m, nine over a virtual e) and
+ * Y = <Phi_ijk^abc| V_N T1 |Phi> the nine products of Eq. tensort2.  For real
+ * amplitudes the bra factors <Phi|T2^+ V_N|Phi_ijk^abc> and <Phi|T1^+ V_N|...>
+ * equal W and Y.  Tensor conventions (upper indices first, as in the paper's
+ * v^{pq}_{rs} and t^{ij}_{ab}):
+ *   v^{ij}_{ma} = Vooov[i,j,m,a]   v^{ei}_{ab} = Vvovv[e,i,a,b]
+ *   v^{ij}_{ab} = Voovv[i,j,a,b]   t^{ij}_{ab} = T2[a,b,i,j]   t^i_a = T1[a,i]
+ * An entry of a block the tensor does not store is zero.
+ *
+ * Reading: the sixth term of Eq. tensort is printed as +v^{ik}_{mc} t^{mj}_{ab};
+ * W must change sign under the exchange of j and k (it is an amplitude of the
+ * antisymmetric determinant Phi_ijk^abc), which the other seventeen terms
+ * respect and which fixes that term's sign to minus.  It is taken with a minus.
+ */
+
+/* Dense copy of a block-sparse tensor (zeros where no block is stored). */
+static double* dense_copy(const otensor* X, const double* x) {
+  int64_t n = 1, dims[OR_MAX_MODES];
+  for (int m = 0; m < X->nm; ++m) {
+    dims[m] = X->sp[m]->n;
+    n *= dims[m];
+  }
+  double* d = (double*)calloc((size_t)n, sizeof(double));
+  if (!d) return NULL;
+  for (int64_t b = 0; b < X->n_blocks; ++b) {
+    const int64_t* tt = X->tiles + b * X->nm;
+    int64_t ext[OR_MAX_MODES], lo[OR_MAX_MODES], bn = 1;
+    for (int m = 0; m < X->nm; ++m) {
+      ext[m] = X->sp[m]->size[tt[m]];
+      lo[m] = X->sp[m]->off[tt[m]];
+      bn *= ext[m];
+    }
+    for (int64_t e = 0; e < bn; ++e) {
+      int64_t r = e, di = 0, idx[OR_MAX_MODES];
+      for (int m = X->nm - 1; m >= 0; --m) {
+        idx[m] = r % ext[m];
+        r /= ext[m];
+      }
+      for (int m = 0; m < X->nm; ++m) di = di * dims[m] + lo[m] + idx[m];
+      d[di] = x[X->off[b] + e];
+    }
+  }
+  return d;
+}
+
+typedef struct {
+  int64_t no, nv;
+  double *t2, *t1, *vo, *vv, *voo; /* dense T2[v,v,o,o], T1[v,o], Vooov, Vvovv, Voovv */
+} triples_in;
+
+#define T2_(a, b, i, j) in->t2[(((a) * nv + (b)) * no + (i)) * no + (j)]
+#define T1_(a, i) in->t1[(a) * no + (i)]
+#define VO_(i, j, m, a) in->vo[(((i) * no + (j)) * no + (m)) * nv + (a)]
+#define VV_(e, i, a, b) in->vv[(((e) * no + (i)) * nv + (a)) * nv + (b)]
+#define VOO_(i, j, a, b) in->voo[(((i) * no + (j)) * nv + (a)) * nv + (b)]
+
+/* W of Eq. tensort for one (i,j,k,a,b,c), any index order. */
+static double triples_w(const triples_in* in, int64_t i, int64_t j, int64_t k, int64_t a, int64_t b, int64_t c) {
+  const int64_t no = in->no, nv = in->nv;
+  double s = 0.0;
+  for (int64_t m = 0; m < no; ++m) { /* A: contractions over the occupied index m */
+    s += VO_(i, j, m, a) * T2_(b, c, m, k);
+    s -= VO_(i, j, m, b) * T2_(a, c, m, k);
+    s += VO_(i, j, m, c) * T2_(a, b, m, k);
+    s -= VO_(i, k, m, a) * T2_(b, c, m, j);
+    s += VO_(i, k, m, b) * T2_(a, c, m, j);
+    s -= VO_(i, k, m, c) * T2_(a, b, m, j);
+    s += VO_(j, k, m, a) * T2_(b, c, m, i);
+    s -= VO_(j, k, m, b) * T2_(a, c, m, i);
+    s += VO_(j, k, m, c) * T2_(a, b, m, i);
+  }
+  for (int64_t e = 0; e < nv; ++e) { /* B: contractions over the virtual index e */
+    s -= VV_(e, i, a, b) * T2_(e, c, j, k);
+    s += VV_(e, i, a, c) * T2_(e, b, j, k);
+    s -= VV_(e, i, b, c) * T2_(e, a, j, k);
+    s += VV_(e, j, a, b) * T2_(e, c, i, k);
+    s -= VV_(e, j, a, c) * T2_(e, b, i, k);
+    s += VV_(e, j, b, c) * T2_(e, a, i, k);
+    s -= VV_(e, k, a, b) * T2_(e, c, i, j);
+    s += VV_(e, k, a, c) * T2_(e, b, i, j);
+    s -= VV_(e, k, b, c) * T2_(e, a, i, j);
+  }
+  return s;
+}
+
+/* Y of Eq. tensort2 for one (i,j,k,a,b,c). */
+static double triples_y(const triples_in* in, int64_t i, int64_t j, int64_t k, int64_t a, int64_t b, int64_t c) {
+  const int64_t no = in->no, nv = in->nv;
+  return VOO_(i, j, a, b) * T1_(c, k) - VOO_(i, j, a, c) * T1_(b, k) + VOO_(i, j, b, c) * T1_(a, k) -
+         VOO_(i, k, a, b) * T1_(c, j) + VOO_(i, k, a, c) * T1_(b, j) - VOO_(i, k, b, c) * T1_(a, j) +
+         VOO_(j, k, a, b) * T1_(c, i) - VOO_(j, k, a, c) * T1_(b, i) + VOO_(j, k, b, c) * T1_(a, i);
+}
+
+#undef T2_
+#undef T1_
+#undef VO_
+#undef VV_
+#undef VOO_
+
+static int triples_load(triples_in* in, const otensor* T2, const double* t2, const otensor* T1, const double* t1,
+                        const otensor* Vo, const double* vo, const otensor* Vv, const double* vv, const otensor* Voo,
+                        const double* voo) {
+  memset(in, 0, sizeof(*in));
+  if (!T2 || !T1 || !Vo || !Vv || !Voo || T2->nm != 4 || T1->nm != 2 || Vo->nm != 4 || Vv->nm != 4 || Voo->nm != 4)
+    return OR_EINVAL;
+  const ospace* O = T2->sp[2];
+  const ospace* V = T2->sp[0];
+  if (T2->sp[1] != V || T2->sp[3] != O || T1->sp[0] != V || T1->sp[1] != O) return OR_EINVAL;
+  if (Vo->sp[0] != O || Vo->sp[1] != O || Vo->sp[2] != O || Vo->sp[3] != V) return OR_EINVAL;
+  if (Vv->sp[0] != V || Vv->sp[1] != O || Vv->sp[2] != V || Vv->sp[3] != V) return OR_EINVAL;
+  if (Voo->sp[0] != O || Voo->sp[1] != O || Voo->sp[2] != V || Voo->sp[3] != V) return OR_EINVAL;
+  in->no = O->n;
+  in->nv = V->n;
+  in->t2 = dense_copy(T2, t2);
+  in->t1 = dense_copy(T1, t1);
+  in->vo = dense_copy(Vo, vo);
+  in->vv = dense_copy(Vv, vv);
+  in->voo = dense_copy(Voo, voo);
+  if (!in->t2 || !in->t1 || !in->vo || !in->vv || !in->voo) return OR_ENOMEM;
+  return OR_OK;
+}
+
+static void triples_free(triples_in* in) {
+  free(in->t2);
+  free(in->t1);
+  free(in->vo);
+  free(in->vv);
+  free(in->voo);
+}
+
+/* E(T) of Eq. cc14 with the restricted sums i<j<k, a<b<c.  Deterministic: one
+ * partial sum per occupied triple (abc in lexicographic order), the partials
+ * then added in triple order.  `eps_o`, `eps_v`: orbital energies. */
+int oracle_triples_energy(const otensor* T2, const double* t2, const otensor* T1, const double* t1,
+                          const otensor* Vo, const double* vo, const otensor* Vv, const double* vv,
+                          const otensor* Voo, const double* voo, const double* eps_o, const double* eps_v,
+                          double* energy) {
+  triples_in in;
+  int st = triples_load(&in, T2, t2, T1, t1, Vo, vo, Vv, vv, Voo, voo);
+  if (st) {
+    triples_free(&in);
+    return st;
+  }
+  const int64_t no = in.no, nv = in.nv;
+  const int64_t n_trip = no * no * no;
+  double* part = (double*)calloc((size_t)(n_trip > 0 ? n_trip : 1), sizeof(double));
+  if (!part) {
+    triples_free(&in);
+    return OR_ENOMEM;
+  }
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int64_t q = 0; q < n_trip; ++q) {
+    const int64_t i = q / (no * no), j = (q / no) % no, k = q % no;
+    if (!(i < j && j < k)) continue;
+    double s = 0.0;
+    for (int64_t a = 0; a < nv; ++a)
+      for (int64_t b = a + 1; b < nv; ++b)
+        for (int64_t c = b + 1; c < nv; ++c) {
+          const double w = triples_w(&in, i, j, k, a, b, c);
+          const double y = triples_y(&in, i, j, k, a, b, c);
+          const double d = eps_o[i] + eps_o[j] + eps_o[k] - eps_v[a] - eps_v[b] - eps_v[c];
+          s += (w + y) * w / d;
+        }
+    part[q] = s;
+  }
+  double e = 0.0;
+  for (int64_t q = 0; q < n_trip; ++q) e += part[q];
+  free(part);
+  triples_free(&in);
+  *energy = e;
+  return OR_OK;
+}
+
+/* W and Y of one occupied triple (i,j,k), any order, over every (a,b,c):
+ * dense n_v^3 arrays, row-major over (a,b,c). */
+int oracle_triples_wy(const otensor* T2, const double* t2, const otensor* T1, const double* t1, const otensor* Vo,
+                      const double* vo, const otensor* Vv, const double* vv, const otensor* Voo, const double* voo,
+                      int64_t i, int64_t j, int64_t k, double* w, double* y) {
+  triples_in in;
+  int st = triples_load(&in, T2, t2, T1, t1, Vo, vo, Vv, vv, Voo, voo);
+  if (!st && (i < 0 || j < 0 || k < 0 || i >= in.no || j >= in.no || k >= in.no)) st = OR_EINVAL;
+  if (st) {
+    triples_free(&in);
+    return st;
+  }
+  const int64_t nv = in.nv;
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int64_t a = 0; a < nv; ++a)
+    for (int64_t b = 0; b < nv; ++b)
+      for (int64_t c = 0; c < nv; ++c) {
+        w[(a * nv + b) * nv + c] = triples_w(&in, i, j, k, a, b, c);
+        y[(a * nv + b) * nv + c] = triples_y(&in, i, j, k, a, b, c);
+      }
+  triples_free(&in);
+  return OR_OK;
+}

@@ -18,6 +18,8 @@ from __future__ import annotations
 
 from dataclasses import dataclass, field
 
+import numpy as np
+
 SEED_BASE = 2201012570
 
 
@@ -326,3 +328,36 @@ def batch_memory_bytes(O: int, V: int, slices: int = 6) -> int:
     vvvv = 3 * V ** 4 // 8
     t = 3 * V ** 2 * O ** 2 // 8
     return 8 * (vvvv + 2 * t) + 2 * slices * (vvvv + t)
+
+
+def triples(O: int, V: int, to: int, tv: int, seed_k: int = 7) -> Workload:
+    """Inputs of the perturbative triples correction E(T) (Sec. IV.B, Eqs. cc14, tensort, tensort2):
+    T2[a,b,i,j] ~ N(0, 0.01) and t1[a,i] ~ N(0, 0.01) as in the doubles recipes, and the three
+    two-electron blocks the equations read, V_ooov[i,j,m,a] (antisymmetric in i, j), V_vovv[e,i,a,b]
+    (antisymmetric in a, b) and V_oovv[i,j,a,b] (both pairs), ~ N(0, 0.1); spin block sparsity;
+    orbital energies from ``orbital_energies``.  The restricted sums run over occupied and
+    virtual spin-orbital triples i<j<k, a<b<c."""
+    w = _vt(seed_k, O, V, to, tv, f"triples_O{O}_V{V}")
+    w.tensors = {
+        "T": TensorSpec("T", ("virt", "virt", "occ", "occ"), 2, sigma=0.01, stream=2, anti01=True, anti23=True),
+        "t1": TensorSpec("t1", ("virt", "occ"), 1, sigma=0.01, stream=7),
+        "V_ooov": TensorSpec("V_ooov", ("occ", "occ", "occ", "virt"), 2, sigma=0.1, stream=8, anti01=True),
+        "V_vovv": TensorSpec("V_vovv", ("virt", "occ", "virt", "virt"), 2, sigma=0.1, stream=9, anti23=True),
+        "V_oovv": TensorSpec("V_oovv", ("occ", "occ", "virt", "virt"), 2, sigma=0.1, stream=3,
+                             anti01=True, anti23=True),
+    }
+    return w
+
+
+def orbital_energies(w: Workload) -> tuple:
+    """Seeded spin-orbital energies (alpha block, then the same values for beta), sorted within each
+    spin: occupied -(0.3 + 0.7|z|), virtual 0.2 + 0.8|z| with z a Philox normal, so every triples
+    denominator e_i + e_j + e_k - e_a - e_b - e_c is at most -1.5."""
+    import tamm_synth
+
+    O, V = w.spaces["occ"].size, w.spaces["virt"].size
+    zo = [abs(tamm_synth.normal(w.seed, 10, p)) for p in range(O // 2)]
+    zv = [abs(tamm_synth.normal(w.seed, 11, p)) for p in range(V // 2)]
+    eo = np.sort(-(0.3 + 0.7 * np.array(zo)))
+    ev = np.sort(0.2 + 0.8 * np.array(zv))
+    return np.concatenate([eo, eo]), np.concatenate([ev, ev])
