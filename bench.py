@@ -872,6 +872,66 @@ def run_doubles_term_case(args) -> dict:
             "TFLOP/s": round(run.flops(st) / ms / 1e9, 3), "nonzero_block_flops": run.flops(st)}
 
 
+def run_triples_case(args) -> dict:
+    """The perturbative triples correction E(T) (Sec. IV.B, Eqs. cc14, tensort, tensort2) of the ``triples``
+    recipe (default O=32 V=160, tiles 16/80): split precision (6 slices) and FP64, CUDA events per
+    evaluation, kernel classes timed by the library.  Throughput counts the block-GEMM flops of the U
+    accumulations (2 M N K over stored block pairs); the fused energy kernel's time is included."""
+    import torch
+
+    import paper_2201_01257_gb300 as tg
+    from paper_2201_01257_gb300 import workload as gw
+    from tamm_synth import workloads as wl
+
+    O_, V_, to, tv = (int(x) for x in (args.triples or "32,160,16,80").split(","))
+    w = wl.triples(O_, V_, to, tv)
+    ctx = tg.Context(0)
+    _, T = gw.build(ctx, w)
+    eo, ev = wl.orbital_energies(w)
+    deo = torch.tensor(eo, dtype=torch.float64, device="cuda:0")
+    dev = torch.tensor(ev, dtype=torch.float64, device="cuda:0")
+    out_e = torch.zeros(1, dtype=torch.float64, device="cuda:0")
+    ins = (T["T"], T["t1"], T["V_ooov"], T["V_vovv"], T["V_oovv"])
+    info = ctx.triples_info(*ins)
+    stream = torch.cuda.current_stream()
+    peaks = measured_peaks()
+    out = {"case": f"{w.name}: E(T) fused to a scalar, tiles {to}/{tv}", "n_triples": info["n_triples"],
+           "gemm_flops": info["gemm_flops"], "n_batches": info["n_batches"]}
+    energies = {}
+    for prec, reps in (("ozaki_bf16", max(1, args.steps)), ("f64", 1)):
+        run = lambda: ctx.triples_energy(*ins, deo.data_ptr(), dev.data_ptr(), out_e.data_ptr(), prec,
+                                         SLICES if prec == "ozaki_bf16" else 0)
+        for _ in range(max(1, args.warmup) if prec == "ozaki_bf16" else 1):
+            run()
+        ctx.sync()
+        ctx.profile_read()
+        ctx.profile(True)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            run()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ctx.profile(False)
+        prof = ctx.profile_read()
+        ms = e0.elapsed_time(e1) / reps
+        key = "split" if prec == "ozaki_bf16" else "f64"
+        energies[key] = float(out_e.item())
+        out[f"{key}_ms"] = round(ms, 3)
+        out[f"{key}_TFLOP/s"] = round(info["gemm_flops"] / ms / 1e9, 3)
+        out[f"{key}_kernel_ms"] = {k: round(v[0] / reps, 3) for k, v in prof.items() if v[1]}
+        if key == "split":
+            g_ms = prof["gemm_ozaki"][0] / reps
+            tf = info["gemm_flops"] * SLICES * (SLICES + 1) // 2 / (g_ms * 1e-3) / 1e12 if g_ms else None
+            out["split_gemm_roofline"] = {"achieved": round(tf, 1) if tf else None, "unit": "TFLOP/s",
+                                          "peak": peaks["bf16_tflops_sustained"],
+                                          "frac": round(tf / peaks["bf16_tflops_sustained"], 4) if tf else None,
+                                          "peak_source": f"{peaks['_source']} bf16_tflops_sustained"}
+    out["energy"] = energies
+    out["split_rel_err_vs_f64"] = abs(energies["split"] - energies["f64"]) / abs(energies["f64"])
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -892,6 +952,8 @@ def main():
     ap.add_argument("--cholesky", action="store_true",
                     help="time the ladder with V_vvvv formed on the fly from Cholesky vectors instead")
     ap.add_argument("--slab-gb", type=float, default=0.0, help="with --cholesky: slab buffer bound (0 = default)")
+    ap.add_argument("--triples", nargs="?", const="32,160,16,80", default="",
+                    help="O,V,to,tv: time the (T) correction instead (default 32,160,16,80)")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -909,6 +971,8 @@ def main():
         out = run_doubles_term_case(args)
     elif args.cholesky:
         out = run_cholesky_case(args)
+    elif args.triples:
+        out = run_triples_case(args)
     elif args.impl == "reference":
         out = run_reference(args, rank)
     else:

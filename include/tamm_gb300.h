@@ -141,7 +141,8 @@ TAMM_API tamm_status tamm_ctx_set_option(tamm_ctx* ctx, int option, int64_t valu
 #define TAMM_KERNEL_SLICE 3     /* split-precision operand slicing */
 #define TAMM_KERNEL_GEMM_OZ 4   /* split-precision tcgen05 block GEMM */
 #define TAMM_KERNEL_SPLIT_REDUCE 5 /* split precision: sum of split summed ranges into C */
-#define TAMM_KERNEL_CLASSES 6
+#define TAMM_KERNEL_TRIPLES 6   /* (T) correction: fused W, Y, denominators and reduction to a scalar */
+#define TAMM_KERNEL_CLASSES 7
 /* Number of kernels this context has launched since creation. */
 TAMM_API tamm_status tamm_ctx_launch_count(const tamm_ctx* ctx, int64_t* launches);
 /* enable != 0: bracket every later kernel launch with CUDA events on the
@@ -354,6 +355,49 @@ TAMM_API tamm_status tamm_norm_async(tamm_ctx* ctx, const tamm_tensor* t, double
  * aligned; refused before any launch), TAMM_ELIMIT (n above the limit),
  * TAMM_ECUDA (no usable current device or a failed launch). */
 TAMM_API tamm_status tamm_norm_noalloc(const double* x_device, int64_t n, double* result_device, void* stream);
+
+/* Perturbative triples correction of CCSD(T) (Sec. IV.B, Eqs. cc13-cc14,
+ * tensort, tensort2), real amplitudes, fused to a scalar:
+ *     E(T) = sum_{i<j<k} sum_{a<b<c} (W + Y) W / D,
+ *     D    = e_i + e_j + e_k - e_a - e_b - e_c,
+ * with W = <Phi_ijk^abc|V_N T2|Phi> (Eq. tensort: nine contractions over an
+ * occupied index m, nine over a virtual index e; its sixth term is taken with
+ * a minus sign, which the antisymmetry of W under j <-> k requires) and
+ * Y = <Phi_ijk^abc|V_N T1|Phi> (Eq. tensort2).  Tensors, upper indices first:
+ *     T2[a,b,i,j] = t^{ij}_{ab}   T1[a,i] = t^i_a   Vooov[i,j,m,a] = v^{ij}_{ma}
+ *     Vvovv[e,i,a,b] = v^{ei}_{ab}   Voovv[i,j,a,b] = v^{ij}_{ab}
+ * all on one occupied space (T2's modes 2, 3) and one virtual space (modes 0,
+ * 1), any block rule, with storage.  eps_occ / eps_virt: the n_o / n_v orbital
+ * energies in device memory.
+ * Method: for each occupied triple i<j<k one block-sparse accumulation gives
+ *     U[x,y,z] = sum over the cyclic rotations (p,q,r) of (i,j,k) of
+ *                sum_m T2[x,y,m,r] Vooov[p,q,m,z] + sum_e Vvovv[e,p,y,x] T2[e,z,q,r]
+ * (the signs of Eq. tensort absorbed by the antisymmetry of the inputs), so
+ * that W[a,b,c] = U[a,b,c] - U[a,c,b] + U[b,c,a].  U is computed by the block
+ * GEMMs (`precision` TAMM_PREC_F64 or TAMM_PREC_OZAKI_BF16, `slices` as in
+ * tamm_contract; the context's chunk, tile policy and grid options apply) for
+ * a batch of triples in a workspace of at most `workspace_bytes` (0 = 1 GiB),
+ * and a fused kernel forms W, Y and D for every a<b<c and reduces to the
+ * scalar: no six-index tensor is kept beyond one batch.  The inputs are first
+ * copied into GEMM order (scratch the size of T2 twice and of Vvovv).
+ * `energy_device`: one double of device memory; `triple_energies_device` (may
+ * be NULL): each occupied triple's contribution, triples i<j<k in
+ * lexicographic order (n_o (n_o - 1)(n_o - 2) / 6 doubles).  Deterministic;
+ * asynchronous.  Errors: TAMM_EINVAL (spaces, modes, null pointers, inside a
+ * group), TAMM_EUNSUPPORTED (precision, a lambda tensor), TAMM_ENOMEM, TAMM_ECUDA. */
+TAMM_API tamm_status tamm_triples_energy(tamm_ctx* ctx, const tamm_tensor* T2, const tamm_tensor* T1,
+                                         const tamm_tensor* Vooov, const tamm_tensor* Vvovv, const tamm_tensor* Voovv,
+                                         const double* eps_occ, const double* eps_virt, int precision, int slices,
+                                         int64_t workspace_bytes, double* energy_device,
+                                         double* triple_energies_device);
+/* Host-only counts for the same inputs: the number of occupied triples, the
+ * FP64-equivalent block-GEMM flops of one evaluation (2 M N K summed over the
+ * block pairs of every triple's U) and the number of workspace batches (any
+ * pointer may be NULL).  Errors: TAMM_EINVAL. */
+TAMM_API tamm_status tamm_triples_info(tamm_ctx* ctx, const tamm_tensor* T2, const tamm_tensor* T1,
+                                       const tamm_tensor* Vooov, const tamm_tensor* Vvovv, const tamm_tensor* Voovv,
+                                       int64_t workspace_bytes, int64_t* n_triples, double* gemm_flops,
+                                       int* n_batches);
 
 /* Autotuner of the split-precision path (TAMM_PREC_OZAKI_BF16) for one
  * contraction, the same tensors and labels as tamm_contract.  It runs the FP64

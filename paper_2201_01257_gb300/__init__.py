@@ -28,7 +28,7 @@ _lib = None
 TAMM_OK, TAMM_EINVAL, TAMM_ENOMEM, TAMM_ECUDA, TAMM_EUNSUPPORTED, TAMM_ETIMEOUT, TAMM_ECHECK, TAMM_ELIMIT = range(8)
 TAMM_SYM_DENSE, TAMM_SYM_SPIN, TAMM_SYM_SPIN_IRREP = 0, 1, 2
 TAMM_PREC_F64, TAMM_PREC_OZAKI_BF16, TAMM_PREC_OZAKI_I8, TAMM_PREC_BF16X3 = 0, 1, 2, 3
-KERNEL_CLASSES = ("add", "reduce", "gemm_f64", "slice", "gemm_ozaki", "split_reduce")
+KERNEL_CLASSES = ("add", "reduce", "gemm_f64", "slice", "gemm_ozaki", "split_reduce", "triples")
 (TAMM_OPT_OZAKI_CHUNK_K, TAMM_OPT_OZAKI_PERSISTENT, TAMM_OPT_OZAKI_TILE_POLICY, TAMM_OPT_OZAKI_PANELS,
  TAMM_OPT_OZAKI_SPLIT_K, TAMM_OPT_WAIT_CYCLES, TAMM_OPT_TEST_WITHHOLD_COPY) = range(7)
 SYM = {"dense": TAMM_SYM_DENSE, "spin": TAMM_SYM_SPIN, "spin_irrep": TAMM_SYM_SPIN_IRREP}
@@ -81,6 +81,8 @@ PROTOTYPES = [
     ("tamm_norm", _i, [_vp, _vp, _dp]),
     ("tamm_norm_async", _i, [_vp, _vp, _vp]),
     ("tamm_norm_noalloc", _i, [_vp, _i64, _vp, _vp]),
+    ("tamm_triples_energy", _i, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _i, _i, _i64, _vp, _vp]),
+    ("tamm_triples_info", _i, [_vp, _vp, _vp, _vp, _vp, _vp, _i64, _i64p, _dp, _ip]),
     ("tamm_autotune", _i, [_vp, _vp, _cp, _vp, _cp, _vp, _cp, _d, _ip, _ip, _ip, _ip, _dp, _dp]),
     ("tamm_group_begin", _i, [_vp]),
     ("tamm_group_end", _i, [_vp]),
@@ -274,6 +276,25 @@ class Context:
     def energy_async(self, alpha, A, la, B, lb, out_device_ptr: int) -> None:
         self.check(self.lib.tamm_energy_async(self.handle, alpha, A.handle, la.encode(), B.handle, lb.encode(),
                                               ctypes.c_void_p(out_device_ptr)), "tamm_energy_async")
+
+    def triples_energy(self, T2, T1, Vooov, Vvovv, Voovv, eps_occ_ptr: int, eps_virt_ptr: int, out_ptr: int,
+                       precision="f64", slices: int = 0, workspace_bytes: int = 0, per_triple_ptr: int = 0) -> None:
+        """E(T) (Sec. IV.B) into the device double at ``out_ptr``; orbital energies and the optional
+        per-triple output (``per_triple_ptr``) are device pointers."""
+        prec = PREC[precision] if isinstance(precision, str) else int(precision)
+        self.check(self.lib.tamm_triples_energy(self.handle, T2.handle, T1.handle, Vooov.handle, Vvovv.handle,
+                                                Voovv.handle, ctypes.c_void_p(eps_occ_ptr),
+                                                ctypes.c_void_p(eps_virt_ptr), prec, slices, int(workspace_bytes),
+                                                ctypes.c_void_p(out_ptr),
+                                                ctypes.c_void_p(per_triple_ptr) if per_triple_ptr else None),
+                   "tamm_triples_energy")
+
+    def triples_info(self, T2, T1, Vooov, Vvovv, Voovv, workspace_bytes: int = 0) -> dict:
+        n, f, b = ctypes.c_int64(), ctypes.c_double(), ctypes.c_int()
+        self.check(self.lib.tamm_triples_info(self.handle, T2.handle, T1.handle, Vooov.handle, Vvovv.handle,
+                                              Voovv.handle, int(workspace_bytes), ctypes.byref(n), ctypes.byref(f),
+                                              ctypes.byref(b)), "tamm_triples_info")
+        return {"n_triples": n.value, "gemm_flops": f.value, "n_batches": b.value}
 
     def norm(self, T) -> float:
         r = ctypes.c_double()

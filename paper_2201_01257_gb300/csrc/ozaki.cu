@@ -958,6 +958,39 @@ cudaError_t launch_ozaki_gemm(tamm_ctx* ctx, OzProblem* problems, const int64_t*
 // Host plan
 // ======================================================================
 
+// Slicing launch shape and items for an operand's records; record i covers
+// image rows [dst_row0, dst_row0 + extent[i]) (rows past its own are zero).
+// Warp row buffers hold K + 2 doubles (room for the aligned-down start) of
+// the longest dense row; as many warps (<= 8) as fit the shared-memory
+// budget.  Rows too long for one warp buffer go through the general path.
+void oz_slicing_items(std::vector<SliceBlock>& recs, const std::vector<int32_t>& extent,
+                      std::vector<SliceItem>& items, int& warps, int& kbuf) {
+  int64_t kmax = 0;
+  for (const SliceBlock& B : recs)
+    if (B.k_dense) kmax = std::max<int64_t>(kmax, B.K);
+  kbuf = (int)((kmax + 2 + 1) & ~int64_t(1));
+  warps = (int)std::min<int64_t>(8, (int64_t)kOzSliceSmemBudget / ((int64_t)kbuf * 8));
+  if (warps < 1) {
+    for (SliceBlock& B : recs) B.k_dense = 0;
+    warps = 8;
+    kbuf = 2;
+  }
+  for (size_t i = 0; i < recs.size(); ++i) {
+    const SliceBlock& B = recs[i];
+    // rows per slicing CTA: one per warp for a dense summed range, else enough rows for every
+    // thread to have work, at least 32 for coalescing along rows
+    int R;
+    if (B.k_dense) {
+      R = warps;
+    } else {
+      R = 32;
+      while (R < kOzSliceMaxRows && (int64_t)R * ((B.K + 7) / 8) < 32 * warps * 4) R *= 2;
+    }
+    for (int32_t r = 0; r < extent[i]; r += R)
+      items.push_back({(int32_t)i, r, std::min<int32_t>(R, extent[i] - r), 0});
+  }
+}
+
 struct OzakiPlan : Plan {
   ContractLayout lay;
   int S;
@@ -1025,39 +1058,6 @@ struct OzakiPlan : Plan {
       st *= B.kdim[m];
     }
     return B;
-  }
-
-  // Slicing launch shape and items for an operand's records; record i covers
-  // image rows [dst_row0, dst_row0 + extent[i]) (rows past its own are zero).
-  // Warp row buffers hold K + 2 doubles (room for the aligned-down start) of
-  // the longest dense row; as many warps (<= 8) as fit the shared-memory
-  // budget.  Rows too long for one warp buffer go through the general path.
-  static void slicing_items(std::vector<SliceBlock>& recs, const std::vector<int32_t>& extent,
-                            std::vector<SliceItem>& items, int& warps, int& kbuf) {
-    int64_t kmax = 0;
-    for (const SliceBlock& B : recs)
-      if (B.k_dense) kmax = std::max<int64_t>(kmax, B.K);
-    kbuf = (int)((kmax + 2 + 1) & ~int64_t(1));
-    warps = (int)std::min<int64_t>(8, (int64_t)kOzSliceSmemBudget / ((int64_t)kbuf * 8));
-    if (warps < 1) {
-      for (SliceBlock& B : recs) B.k_dense = 0;
-      warps = 8;
-      kbuf = 2;
-    }
-    for (size_t i = 0; i < recs.size(); ++i) {
-      const SliceBlock& B = recs[i];
-      // rows per slicing CTA: one per warp for a dense summed range, else enough rows for every
-      // thread to have work, at least 32 for coalescing along rows
-      int R;
-      if (B.k_dense) {
-        R = warps;
-      } else {
-        R = 32;
-        while (R < kOzSliceMaxRows && (int64_t)R * ((B.K + 7) / 8) < 32 * warps * 4) R *= 2;
-      }
-      for (int32_t r = 0; r < extent[i]; r += R)
-        items.push_back({(int32_t)i, r, std::min<int32_t>(R, extent[i] - r), 0});
-    }
   }
 
   OzakiPlan(tamm_ctx* c, const tamm_tensor* C, const char* lc, const tamm_tensor* A, const char* la,
@@ -1202,8 +1202,8 @@ struct OzakiPlan : Plan {
       group_k.push_back(Ksum);
     }
     std::vector<SliceItem> ia, ib;
-    slicing_items(sa, ext_a, ia, warps_a, kbuf_a);
-    slicing_items(sb, ext_b, ib, warps_b, kbuf_b);
+    oz_slicing_items(sa, ext_a, ia, warps_a, kbuf_a);
+    oz_slicing_items(sb, ext_b, ib, warps_b, kbuf_b);
 
     auto align = [](size_t x) { return (x + 1023) & ~size_t(1023); };
     off_ta = 0;

@@ -20,6 +20,7 @@
 #pragma once
 
 #include <algorithm>
+#include <vector>
 
 #include "tamm_contract.h"
 
@@ -185,6 +186,11 @@ inline int oz_tile_rows(int64_t rows, int policy) {
   }
   return 128;
 }
+
+// Slicing launch shape and items for an operand's records: record i covers image rows
+// [dst_row0, dst_row0 + extent[i]); sets the warps per CTA and the warp row buffer length.
+void oz_slicing_items(std::vector<SliceBlock>& recs, const std::vector<int32_t>& extent,
+                      std::vector<SliceItem>& items, int& warps, int& kbuf);
 
 // float_split (S = 3 only): BF16x3 floating pieces instead of integer digits.
 cudaError_t launch_ozaki_slice(tamm_ctx* ctx, const double* src, const SliceBlock* blocks, const SliceItem* items,

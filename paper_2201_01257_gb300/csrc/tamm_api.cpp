@@ -13,6 +13,7 @@
 #include "tamm_contract.h"
 #include "tamm_lambda.h"
 #include "tamm_plan.h"
+#include "tamm_triples.h"
 
 using namespace tamm;
 
@@ -622,6 +623,30 @@ extern "C" tamm_status tamm_contract_adjoint(tamm_ctx* ctx, double alpha, const 
     // the adjoint of a MultOp is a MultOp with the label roles exchanged
     if (dA) run_contract(ctx, alpha, dA, la, beta, dC, lc, B, lb, precision, slices);
     if (dB) run_contract(ctx, alpha, dB, lb, beta, A, la, dC, lc, precision, slices);
+  });
+}
+
+extern "C" tamm_status tamm_triples_energy(tamm_ctx* ctx, const tamm_tensor* T2, const tamm_tensor* T1,
+                                           const tamm_tensor* Vooov, const tamm_tensor* Vvovv,
+                                           const tamm_tensor* Voovv, const double* eps_occ, const double* eps_virt,
+                                           int precision, int slices, int64_t workspace_bytes,
+                                           double* energy_device, double* triple_energies_device) {
+  if (!ctx) return TAMM_EINVAL;
+  return guarded(ctx, [&] {
+    require_device(ctx);
+    no_group(ctx, "a triples correction");
+    run_triples(ctx, T2, T1, Vooov, Vvovv, Voovv, eps_occ, eps_virt, precision, slices, workspace_bytes,
+                energy_device, triple_energies_device);
+  });
+}
+
+extern "C" tamm_status tamm_triples_info(tamm_ctx* ctx, const tamm_tensor* T2, const tamm_tensor* T1,
+                                         const tamm_tensor* Vooov, const tamm_tensor* Vvovv, const tamm_tensor* Voovv,
+                                         int64_t workspace_bytes, int64_t* n_triples, double* gemm_flops,
+                                         int* n_batches) {
+  if (!ctx) return TAMM_EINVAL;
+  return guarded(ctx, [&] {
+    triples_info(ctx, T2, T1, Vooov, Vvovv, Voovv, workspace_bytes, n_triples, gemm_flops, n_batches);
   });
 }
 

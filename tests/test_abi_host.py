@@ -333,3 +333,43 @@ def test_header_is_plain_c(tmp_path):
                    "}\n")
     subprocess.check_call(["gcc", "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror",
                            "-I", os.path.join(ROOT, "include"), "-c", str(src), "-o", str(tmp_path / "use.o")])
+
+
+def test_triples_info_counts(hctx):
+    # occupied triples C(n_o, 3); block-GEMM flops = 2 M N K over the block pairs of every triple's U,
+    # enumerated here independently from the spin rule of the input tensors
+    import itertools
+
+    w = wl.triples(8, 24, 2, 6)
+    gs, os_ = spaces_for(hctx, w)
+    t = {n: hctx.tensor([gs[m] for m in s.modes], s.n_upper, s.sym, allocate=False) for n, s in w.tensors.items()}
+    info = hctx.triples_info(t["T"], t["t1"], t["V_ooov"], t["V_vovv"], t["V_oovv"])
+    assert info["n_triples"] == 8 * 7 * 6 // 6 and info["n_batches"] == 1
+    occ, vir = os_["occ"].tiles, os_["virt"].tiles
+    otile = [k for k, tl in enumerate(occ) for _ in range(tl[1])]
+    sp_o = [tl[2] for tl in occ]
+    sp_v = [tl[2] for tl in vir]
+
+    def stored(spins_up, spins_lo):
+        return sum(spins_up) == sum(spins_lo)
+
+    flops = 0
+    for i, j, k in itertools.combinations(range(8), 3):
+        s = sp_o[otile[i]] + sp_o[otile[j]] + sp_o[otile[k]]
+        for tx, ty, tz in itertools.product(range(len(vir)), repeat=3):
+            if sp_v[tx] + sp_v[ty] + sp_v[tz] != s:
+                continue
+            nxy, nz = vir[tx][1] * vir[ty][1], vir[tz][1]
+            for p, q, r in ((i, j, k), (j, k, i), (k, i, j)):
+                tp, tq, tr = otile[p], otile[q], otile[r]
+                for tm in range(len(occ)):
+                    if stored([sp_v[tx], sp_v[ty]], [sp_o[tm], sp_o[tr]]) and \
+                            stored([sp_o[tp], sp_o[tq]], [sp_o[tm], sp_v[tz]]):
+                        flops += 2 * nxy * nz * occ[tm][1]
+                for te in range(len(vir)):
+                    if stored([sp_v[te], sp_o[tp]], [sp_v[ty], sp_v[tx]]) and \
+                            stored([sp_v[te], sp_v[tz]], [sp_o[tq], sp_o[tr]]):
+                        flops += 2 * nxy * nz * vir[te][1]
+    assert info["gemm_flops"] == flops
+    # a tiny workspace: one triple per batch
+    assert hctx.triples_info(t["T"], t["t1"], t["V_ooov"], t["V_vovv"], t["V_oovv"], 8)["n_batches"] == 56
