@@ -230,6 +230,8 @@ def run_ours(args, rank: int, world: int) -> dict | None:
     ms_f64 = ev2.elapsed_time(ev3) / f64_steps
     r_64, w_64, e_64 = T["R"].download(), T["W"].download(), float(energy_dev.item())
     rel = lambda a, b: float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+    # measured FP64 throughput of this GPU: the FP64 path's roofline denominator
+    fp64_peak = {"dfma": round(ctx.fp64_peak("dfma"), 4), "dmma": round(ctx.fp64_peak("dmma"), 4)}
 
     # --- each contraction alone (not the headline): split precision and FP64 ---
     per_contraction = {}
@@ -324,6 +326,21 @@ def run_ours(args, rank: int, world: int) -> dict | None:
     ms_e2e = ev6.elapsed_time(ev7) / e2e_k
     r_e2e = out_host.numpy().copy()
 
+    # the copy bound of e2e: the same pinned host inputs copied alone (cudaMemcpyAsync, one per tensor)
+    plain = {k: torch.empty_like(T[k].data) for k in host}
+    for k, h in host.items():
+        plain[k][: h.numel()].copy_(h, non_blocking=True)
+    torch.cuda.synchronize()
+    ev8, ev9 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev8.record(stream)
+    for _ in range(2):
+        for k, h in host.items():
+            plain[k][: h.numel()].copy_(h, non_blocking=True)
+    ev9.record(stream)
+    torch.cuda.synchronize()
+    h2d_gbs = 2 * h2d / (ev8.elapsed_time(ev9) * 1e-3) / 1e9
+    del plain
+
     ms, ms_e2e, ms_f64 = (max_over_ranks(x, dist, f"cuda:{dev}") for x in (ms, ms_e2e, ms_f64))
     if dist is not None:
         dist.destroy_process_group()
@@ -371,7 +388,9 @@ def run_ours(args, rank: int, world: int) -> dict | None:
             "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
         },
         "f64": {"value": round(job_throughput(world, flops, ms_f64), 4), "unit": UNIT,
-                "ms_per_step": round(ms_f64, 2), "steps": f64_steps},
+                "ms_per_step": round(ms_f64, 2), "steps": f64_steps,
+                "peak_measured_tflops": fp64_peak,
+                "frac_of_measured_peak": round(job_throughput(world, flops, ms_f64) / max(fp64_peak.values()), 4)},
         "speedup_vs_f64": round(ms_f64 / ms, 2),
         "per_contraction": per_contraction,
         "rel_err_vs_f64": {"R": rel(r_oz, r_64), "W": rel(w_oz, w_64), "energy": abs(e_oz - e_64) / abs(e_64)},
@@ -380,7 +399,9 @@ def run_ours(args, rank: int, world: int) -> dict | None:
                 "steps": e2e_k, "pipelined": "inputs of step k+1 copied during step k (two buffer sets)",
                 "serial": {"value": round(job_throughput(world, flops, ms_e2e_serial), 3),
                            "ms_per_step": round(ms_e2e_serial, 3)},
-                "rel_err_R_vs_device_step": rel(r_e2e, r_oz)},
+                "rel_err_R_vs_device_step": rel(r_e2e, r_oz),
+                "plain_pinned_h2d_GBps": round(h2d_gbs, 1),
+                "copy_bound_ms": round(h2d / (h2d_gbs * 1e9) * 1e3, 3)},
         "gpu_launches": launches,
         "kernel_ms_per_step": {k: round(v[0] / args.steps, 3) for k, v in prof.items()},
         "roofline": {
@@ -898,6 +919,22 @@ def run_triples_case(args) -> dict:
     out = {"case": f"{w.name}: E(T) fused to a scalar, tiles {to}/{tv}", "n_triples": info["n_triples"],
            "gemm_flops": info["gemm_flops"], "n_batches": info["n_batches"]}
     energies = {}
+    # split precision: the tile policy (output columns per work item) picked by timing, like the autotuner
+    pol_ms = {}
+    for policy in (1, 3):
+        ctx.set_option(tg.TAMM_OPT_OZAKI_TILE_POLICY, policy)
+        for _ in range(2):
+            ctx.triples_energy(*ins, deo.data_ptr(), dev.data_ptr(), out_e.data_ptr(), "ozaki_bf16", SLICES)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        ctx.triples_energy(*ins, deo.data_ptr(), dev.data_ptr(), out_e.data_ptr(), "ozaki_bf16", SLICES)
+        b.record(stream)
+        torch.cuda.synchronize()
+        pol_ms[policy] = a.elapsed_time(b)
+    best = min(pol_ms, key=pol_ms.get)
+    ctx.set_option(tg.TAMM_OPT_OZAKI_TILE_POLICY, best)
+    out["split_tile_policy_ms"] = {str(k): round(v, 3) for k, v in pol_ms.items()}
+    out["split_tile_policy"] = best
     for prec, reps in (("ozaki_bf16", max(1, args.steps)), ("f64", 1)):
         run = lambda: ctx.triples_energy(*ins, deo.data_ptr(), dev.data_ptr(), out_e.data_ptr(), prec,
                                          SLICES if prec == "ozaki_bf16" else 0)
@@ -932,6 +969,81 @@ def run_triples_case(args) -> dict:
     return out
 
 
+def run_residual_case(args) -> dict:
+    """One full CCSD residual (T1 and T2 equations, Stanton-Gauss intermediates, the energy and the
+    residual norms: 55 library operations in 11 dependency levels) at O=40 V=240, tiles 20/40 by default:
+    operation by operation, through the scheduler (each level's split-precision contractions as one
+    grouped launch), and that scheduled run captured in one CUDA graph; split precision (6 slices) and
+    FP64.  Inputs are seeded normals drawn on the device.  Throughput counts the nonzero-block flops of
+    the 36 contractions."""
+    import torch
+
+    import paper_2201_01257_gb300 as tg
+    from paper_2201_01257_gb300 import workload as gw
+    from tamm_synth import workloads as wl
+
+    O_, V_, to, tv = (int(x) for x in (args.residual or "40,240,20,40").split(","))
+    w = wl.ccsd_residual(O_, V_, to, tv)
+    stream = torch.cuda.Stream(0)
+    ctx = tg.Context(0, stream=stream)
+    with torch.cuda.stream(stream):
+        sp, T = gw.build(ctx, w, fill=False)
+        for k, (name, spec) in enumerate(w.tensors.items()):
+            if spec.sigma:
+                _device_fill(T[name], spec, w.seed * 64 + k)
+        run = gw.Runner(ctx, w, sp, T)
+        flops = sum(run.flops(st) for st in w.steps if isinstance(st, wl.ContractSpec))
+        e = torch.zeros(8, dtype=torch.float64, device="cuda:0")
+
+        def timed(fn, k, warm):
+            for _ in range(warm):
+                fn()
+            ctx.sync()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            for _ in range(k):
+                fn()
+            b.record(stream)
+            ctx.sync()
+            return a.elapsed_time(b) / k
+
+        out = {"case": f"{w.name}: CCSD T1 + T2 residual, energy and norms, tiles {to}/{tv}", "operations": len(w.steps),
+               "contractions": sum(isinstance(st, wl.ContractSpec) for st in w.steps), "nonzero_block_flops": flops}
+        k = max(1, args.steps)
+        ms_seq = timed(lambda: run.run("ozaki_bf16", SLICES, energy_out=e.data_ptr()), k, max(1, args.warmup))
+        sch = run.scheduled("ozaki_bf16", SLICES, energy_out=e.data_ptr())
+        out["levels"] = max(sch.levels()) + 1
+        ms_sch = timed(sch.execute, k, 1)
+        ctx.profile_read()
+        ctx.profile(True)
+        sch.execute()
+        ctx.sync()
+        ctx.profile(False)
+        prof = ctx.profile_read()
+        with ctx.capture() as cap:
+            sch.execute()
+        g = cap.graph
+        ms_graph = timed(g.launch, k, 1)
+        r2_split = T["R2"].download()
+        e_split = e.cpu().numpy()[:4].copy()
+        ms64 = timed(lambda: run.run("f64", 0, energy_out=e.data_ptr()), 1, 1)
+        r2_64 = T["R2"].download()
+        e_64 = e.cpu().numpy()[:4].copy()
+    out.update({
+        "split_sequential_ms": round(ms_seq, 3), "split_scheduled_ms": round(ms_sch, 3),
+        "split_graph_ms": round(ms_graph, 3), "graph_kernels": g.kernel_launches,
+        "split_sequential_TFLOP/s": round(flops / ms_seq / 1e9, 3),
+        "split_scheduled_TFLOP/s": round(flops / ms_sch / 1e9, 3),
+        "split_graph_TFLOP/s": round(flops / ms_graph / 1e9, 3),
+        "f64_ms": round(ms64, 3), "f64_TFLOP/s": round(flops / ms64 / 1e9, 4),
+        "scheduled_kernel_ms": {kk: round(v[0], 3) for kk, v in prof.items() if v[1]},
+        "split_rel_err_vs_f64": {"R2": float(np.linalg.norm(r2_split - r2_64) / np.linalg.norm(r2_64)),
+                                 "energy_t2": float(abs(e_split[0] - e_64[0]) / abs(e_64[0]))},
+    })
+    g.destroy()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -952,6 +1064,8 @@ def main():
     ap.add_argument("--cholesky", action="store_true",
                     help="time the ladder with V_vvvv formed on the fly from Cholesky vectors instead")
     ap.add_argument("--slab-gb", type=float, default=0.0, help="with --cholesky: slab buffer bound (0 = default)")
+    ap.add_argument("--residual", nargs="?", const="40,240,20,40", default="",
+                    help="O,V,to,tv: time one full CCSD residual, sequential vs scheduled vs graph, instead")
     ap.add_argument("--triples", nargs="?", const="32,160,16,80", default="",
                     help="O,V,to,tv: time the (T) correction instead (default 32,160,16,80)")
     args = ap.parse_args()
@@ -973,6 +1087,8 @@ def main():
         out = run_cholesky_case(args)
     elif args.triples:
         out = run_triples_case(args)
+    elif args.residual:
+        out = run_residual_case(args)
     elif args.impl == "reference":
         out = run_reference(args, rank)
     else:

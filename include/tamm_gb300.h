@@ -399,6 +399,16 @@ TAMM_API tamm_status tamm_triples_info(tamm_ctx* ctx, const tamm_tensor* T2, con
                                        int64_t workspace_bytes, int64_t* n_triples, double* gemm_flops,
                                        int* n_batches);
 
+/* FP64 throughput of this device, measured: the denominator of the FP64
+ * path's roofline (the paper has no counterpart; it gives no kernel rates).
+ * kind 0: scalar fused multiply-adds (DFMA), 8 independent chains per thread;
+ * kind 1: the warp-wide FP64 tensor-core MMA (mma.sync m8n8k4 f64), 8
+ * independent accumulators per warp.  8 CTAs of 256 threads per SM, 4096
+ * steps, one untimed launch then one timed with CUDA events on the context's
+ * stream; `tflops` receives the flop rate.  Synchronises.
+ * Errors: TAMM_EINVAL (kind, null pointer, inside a group or capture), TAMM_ECUDA. */
+TAMM_API tamm_status tamm_fp64_peak(tamm_ctx* ctx, int kind, double* tflops);
+
 /* Autotuner of the split-precision path (TAMM_PREC_OZAKI_BF16) for one
  * contraction, the same tensors and labels as tamm_contract.  It runs the FP64
  * contraction once as the reference, then for each exact-chunk length (1280,

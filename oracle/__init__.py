@@ -356,7 +356,8 @@ def run_step(w: wl.Workload, tensors: dict, step) -> float | None:
     if isinstance(step, wl.EnergySpec):
         return energy(step.alpha, tensors[step.a], step.la, tensors[step.b], step.lb)
     if isinstance(step, wl.AddSpec):
-        add(step.alpha, tensors[step.c], step.lc, step.beta, tensors[step.a], step.la)
+        for t, (al, la) in enumerate(step.terms):
+            add(al, tensors[step.c], step.lc, step.beta if t == 0 else 1.0, tensors[step.a], la)
         return None
     C, A, B = tensors[step.c], tensors[step.a], tensors[step.b]
     if step.antisym:

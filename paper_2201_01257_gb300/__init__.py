@@ -83,6 +83,7 @@ PROTOTYPES = [
     ("tamm_norm_noalloc", _i, [_vp, _i64, _vp, _vp]),
     ("tamm_triples_energy", _i, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _i, _i, _i64, _vp, _vp]),
     ("tamm_triples_info", _i, [_vp, _vp, _vp, _vp, _vp, _vp, _i64, _i64p, _dp, _ip]),
+    ("tamm_fp64_peak", _i, [_vp, _i, _dp]),
     ("tamm_autotune", _i, [_vp, _vp, _cp, _vp, _cp, _vp, _cp, _d, _ip, _ip, _ip, _ip, _dp, _dp]),
     ("tamm_group_begin", _i, [_vp]),
     ("tamm_group_end", _i, [_vp]),
@@ -295,6 +296,13 @@ class Context:
                                               Voovv.handle, int(workspace_bytes), ctypes.byref(n), ctypes.byref(f),
                                               ctypes.byref(b)), "tamm_triples_info")
         return {"n_triples": n.value, "gemm_flops": f.value, "n_batches": b.value}
+
+    def fp64_peak(self, kind: str = "dfma") -> float:
+        """Measured FP64 TFLOP/s of this device: ``dfma`` (scalar FMA) or ``dmma`` (FP64 tensor-core MMA)."""
+        r = ctypes.c_double()
+        self.check(self.lib.tamm_fp64_peak(self.handle, {"dfma": 0, "dmma": 1}[kind], ctypes.byref(r)),
+                   "tamm_fp64_peak")
+        return r.value
 
     def norm(self, T) -> float:
         r = ctypes.c_double()

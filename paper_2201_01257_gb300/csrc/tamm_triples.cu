@@ -52,9 +52,19 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
+// 1/d for d < 0 of moderate size: an FP32 reciprocal refined by one Newton step in FP64, relative
+// error about 2^-47 (the FP32 seed is good to 2^-23 and the step squares the error); two FP64
+// operations instead of an IEEE division, whose cost the narrow FP64 pipe of this chip makes large.
+__device__ __forceinline__ double recip_newton(double d) {
+  const double r0 = (double)__frcp_rn(__double2float_rn(d));
+  return fma(r0, fma(-d, r0, 1.0), r0);
+}
+
 // One item per CTA.  A thread owns four consecutive a (one 32-byte sector of U[b,c,a]) and one c and
 // walks b, so U[a,b,c] is read coalesced across the warp (consecutive c), U[a,c,b] along one row per
-// thread and U[b,c,a] in whole sectors.  FP64 throughout; the CTA's sum goes to partials[blockIdx.x].
+// thread and U[b,c,a] in whole sectors.  Y of Eq. tensort2 is nine fused multiply-adds: each T1 factor
+// carries its pair's sign (pairs (ij)k, (ik)j, (jk)i: +, -, +) and the virtual split's (ab|c +, ac|b -,
+// bc|a +).  FP64 throughout; the CTA's sum goes to partials[blockIdx.x].
 __global__ void __launch_bounds__(256) triples_energy_kernel(const double* __restrict__ U,
                                                              const TriplesItem* __restrict__ items,
                                                              const double* __restrict__ voo,
@@ -70,32 +80,33 @@ __global__ void __launch_bounds__(256) triples_energy_kernel(const double* __res
   const double* U2 = U + it.u_off[1];
   const double* U3 = U + it.u_off[2];
   const int nquad = (na + 3) / 4;
+  // the single occupied orbital of pair P ((ij) -> k, (ik) -> j, (jk) -> i) and the pair's sign
+  constexpr int kSingle[3] = {2, 1, 0};
+  constexpr double kSign[3] = {1.0, -1.0, 1.0};
   double acc = 0.0;
   for (int u = threadIdx.x; u < nquad * nc; u += blockDim.x) {
     const int cl = u % nc, q = u / nc;
     const int c = c0 + cl;
-    const double ec = eps_v[c];
-    // T1[c, o] for o = i, j, k
-    double t1c[3];
+    const double e_c = e_occ - eps_v[c];
+    double tc[3];  // sign_P * T1[c, single(P)]           (term  v_P[a,b] t1[c])
 #pragma unroll
-    for (int o = 0; o < 3; ++o)
-      t1c[o] = it.t1_off[2 * 3 + o] >= 0 ? t1[it.t1_off[2 * 3 + o] + (int64_t)cl * it.occ_tsz[o] + it.occ_loc[o]]
-                                         : 0.0;
+    for (int P = 0; P < 3; ++P) {
+      const int o = kSingle[P];
+      const int64_t off = it.t1_off[2 * 3 + o];
+      tc[P] = off >= 0 ? kSign[P] * t1[off + (int64_t)cl * it.occ_tsz[o] + it.occ_loc[o]] : 0.0;
+    }
     for (int al = 4 * q; al < min(na, 4 * q + 4); ++al) {
       const int a = a0 + al;
       if (a >= c) break;
-      const double ea = eps_v[a];
-      double t1a[3];
-#pragma unroll
-      for (int o = 0; o < 3; ++o)
-        t1a[o] = it.t1_off[0 * 3 + o] >= 0 ? t1[it.t1_off[0 * 3 + o] + (int64_t)al * it.occ_tsz[o] + it.occ_loc[o]]
-                                           : 0.0;
-      // Voovv[p,q,a,c] for the three pairs (virtual pair ac)
-      double vac[3];
+      const double e_ac = e_c - eps_v[a];
+      double ta[3], vac[3];  // sign_P * T1[a, single(P)] (term  v_P[b,c] t1[a]);  v_P[a,c]
 #pragma unroll
       for (int P = 0; P < 3; ++P) {
-        const int64_t off = it.voo_off[P * 3 + 1];
-        vac[P] = off >= 0 ? voo[off + ((int64_t)it.pair_pre[P] * na + al) * nc + cl] : 0.0;
+        const int o = kSingle[P];
+        const int64_t off = it.t1_off[0 * 3 + o];
+        ta[P] = off >= 0 ? kSign[P] * t1[off + (int64_t)al * it.occ_tsz[o] + it.occ_loc[o]] : 0.0;
+        const int64_t ov = it.voo_off[P * 3 + 1];
+        vac[P] = ov >= 0 ? voo[ov + ((int64_t)it.pair_pre[P] * na + al) * nc + cl] : 0.0;
       }
       for (int bl = 0; bl < nb; ++bl) {
         const int b = b0 + bl;
@@ -103,29 +114,20 @@ __global__ void __launch_bounds__(256) triples_energy_kernel(const double* __res
         if (b >= c) break;
         const double w = U1[((int64_t)al * nb + bl) * nc + cl] - U2[((int64_t)al * nc + cl) * nb + bl] +
                          U3[((int64_t)bl * nc + cl) * na + al];
-        double vab[3], vbc[3], t1b[3];
-#pragma unroll
-        for (int P = 0; P < 3; ++P) {
-          const int64_t oab = it.voo_off[P * 3 + 0], obc = it.voo_off[P * 3 + 2];
-          vab[P] = oab >= 0 ? voo[oab + ((int64_t)it.pair_pre[P] * na + al) * nb + bl] : 0.0;
-          vbc[P] = obc >= 0 ? voo[obc + ((int64_t)it.pair_pre[P] * nb + bl) * nc + cl] : 0.0;
-        }
-#pragma unroll
-        for (int o = 0; o < 3; ++o)
-          t1b[o] = it.t1_off[1 * 3 + o] >= 0 ? t1[it.t1_off[1 * 3 + o] + (int64_t)bl * it.occ_tsz[o] + it.occ_loc[o]]
-                                             : 0.0;
-        // Eq. tensort2: pairs (ij)k, (ik)j, (jk)i with the signs +, -, + and, inside each, the
-        // virtual splits ab|c, ac|b, bc|a with +, -, +; o indexes the single occupied orbital (k, j, i)
         double y = 0.0;
-        const int single[3] = {2, 1, 0};
-        const double psign[3] = {1.0, -1.0, 1.0};
 #pragma unroll
         for (int P = 0; P < 3; ++P) {
-          const int o = single[P];
-          y += psign[P] * (vab[P] * t1c[o] - vac[P] * t1b[o] + vbc[P] * t1a[o]);
+          const int o = kSingle[P];
+          const int64_t oab = it.voo_off[P * 3 + 0], obc = it.voo_off[P * 3 + 2], ot = it.t1_off[1 * 3 + o];
+          const double vab = oab >= 0 ? voo[oab + ((int64_t)it.pair_pre[P] * na + al) * nb + bl] : 0.0;
+          const double vbc = obc >= 0 ? voo[obc + ((int64_t)it.pair_pre[P] * nb + bl) * nc + cl] : 0.0;
+          const double tb = ot >= 0 ? kSign[P] * t1[ot + (int64_t)bl * it.occ_tsz[o] + it.occ_loc[o]] : 0.0;
+          y = fma(vab, tc[P], y);   // + v_P[a,b] t1[c]
+          y = fma(-vac[P], tb, y);  // - v_P[a,c] t1[b]
+          y = fma(vbc, ta[P], y);   // + v_P[b,c] t1[a]
         }
-        const double d = e_occ - ea - eps_v[b] - ec;
-        acc += (w + y) * w / d;
+        const double d = e_ac - eps_v[b];  // e_i + e_j + e_k - e_a - e_b - e_c
+        acc = fma((w + y) * w, recip_newton(d), acc);
       }
     }
   }

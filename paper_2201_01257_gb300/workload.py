@@ -85,15 +85,22 @@ class Runner:
             return form + self.ctx.flops(X, lx, T[step.a], step.la, T[step.b], step.lb)
         return form + self.ctx.flops(T[step.c], step.lc, T[step.a], step.la, T[step.b], step.lb)
 
+    def energy_slot(self, step, energy_out: int) -> int:
+        """Device address of an energy step's result: the k-th energy step of the recipe writes the k-th
+        double at ``energy_out``."""
+        k = [s.name for s in self.w.steps if isinstance(s, wl.EnergySpec)].index(step.name)
+        return energy_out + 8 * k
+
     def run_step(self, step, precision="f64", slices: int = 0, energy_out=None):
         T, ctx = self.tensors, self.ctx
         if isinstance(step, wl.EnergySpec):
             if energy_out is not None:
-                ctx.energy_async(step.alpha, T[step.a], step.la, T[step.b], step.lb, energy_out)
+                ctx.energy_async(step.alpha, T[step.a], step.la, T[step.b], step.lb,
+                                 self.energy_slot(step, energy_out))
                 return None
             return ctx.energy(step.alpha, T[step.a], step.la, T[step.b], step.lb)
         if isinstance(step, wl.AddSpec):
-            ctx.add(T[step.c], step.lc, step.beta, T[step.a], [(step.alpha, step.la)])
+            ctx.add(T[step.c], step.lc, step.beta, T[step.a], step.terms)
             return None
         if step.antisym:
             X, lx = self.scratch_for(step)
@@ -122,9 +129,10 @@ class Runner:
             if isinstance(step, wl.EnergySpec):
                 if energy_out is None:
                     raise ValueError(f"{step.name}: a scheduled energy needs a device result pointer")
-                sch.energy_async(step.alpha, T[step.a], step.la, T[step.b], step.lb, energy_out)
+                sch.energy_async(step.alpha, T[step.a], step.la, T[step.b], step.lb,
+                                 self.energy_slot(step, energy_out))
             elif isinstance(step, wl.AddSpec):
-                sch.add(T[step.c], step.lc, step.beta, T[step.a], [(step.alpha, step.la)])
+                sch.add(T[step.c], step.lc, step.beta, T[step.a], step.terms)
             elif step.antisym:
                 X, lx = self.scratch_for(step)
                 sch.contract(step.alpha, X, lx, 0.0, T[step.a], step.la, T[step.b], step.lb, precision, slices)

@@ -66,7 +66,8 @@ class ContractSpec:
 
 @dataclass(frozen=True)
 class AddSpec:
-    """``C(lc) = beta*C + alpha * A(la)`` (permuted add)."""
+    """``C(lc) = beta*C + alpha * A(la) + sum alpha_t * A(la_t)`` (permuted add; ``more`` holds the
+    extra (alpha_t, la_t) terms, at most three)."""
     name: str
     c: str
     lc: str
@@ -74,6 +75,11 @@ class AddSpec:
     la: str
     alpha: float
     beta: float = 1.0
+    more: tuple = ()
+
+    @property
+    def terms(self) -> list:
+        return [(self.alpha, self.la)] + list(self.more)
 
 
 @dataclass(frozen=True)
@@ -361,3 +367,101 @@ def orbital_energies(w: Workload) -> tuple:
     eo = np.sort(-(0.3 + 0.7 * np.array(zo)))
     ev = np.sort(0.2 + 0.8 * np.array(zv))
     return np.concatenate([eo, eo]), np.concatenate([ev, ev])
+
+
+def ccsd_residual(O: int, V: int, to: int, tv: int, seed_k: int = 8) -> Workload:
+    """One full CCSD residual (T1 and T2 equations and the correlation energy) in spin orbitals,
+    canonical Hartree-Fock reference, as a list of library operations: the Stanton-Gauss
+    intermediates (tau~, tau, F_ae, F_mi, F_me, W_mnij, W_abef, W_mbej) and then every term of the
+    T1 and T2 residuals, each a binary contraction or a permuted add (P(ab), P(ij) and P(ab)P(ij) as
+    multi-term adds).  Canonical orbitals make the Fock matrix diagonal, so it enters only the
+    amplitude update, not the residual.  Integrals by index type, drawn independently (N(0, 0.1),
+    antisymmetrised within same-space pairs); amplitudes T2 ~ N(0, 0.01), t1 ~ N(0, 0.01).
+    <mb||ij> is read as <ij||mb> (V_ooov; real orbitals); <am||ef> = -<ma||ef>, <mn||ej> = -<mn||je>,
+    <na||if> = -<na||fi>, <nm||ei> = -<nm||ie> (antisymmetry of the lower pair)."""
+    w = _vt(seed_k, O, V, to, tv, f"ccsd_residual_O{O}_V{V}")
+    o, v = "occ", "virt"
+    ts = {
+        "T": ((v, v, o, o), 2, 0.01, 2, True, True), "t1": ((v, o), 1, 0.01, 7, False, False),
+        "V_oooo": ((o, o, o, o), 2, 0.1, 4, True, True), "V_ooov": ((o, o, o, v), 2, 0.1, 8, True, False),
+        "V_oovv": ((o, o, v, v), 2, 0.1, 3, True, True), "V_ovvv": ((o, v, v, v), 2, 0.1, 12, False, True),
+        "V_ovvo": ((o, v, v, o), 2, 0.1, 5, False, False), "V_vvvv": ((v, v, v, v), 2, 0.1, 1, True, True),
+        "V_vvvo": ((v, v, v, o), 2, 0.1, 6, True, False),
+    }
+    w.tensors = {n: TensorSpec(n, m, nu, sigma=sg, stream=st, anti01=a01, anti23=a23)
+                 for n, (m, nu, sg, st, a01, a23) in ts.items()}
+    work = {"Tt": (v, v, o, o), "Tau": (v, v, o, o), "Fvv": (v, v), "Foo": (o, o), "Fov": (o, v),
+            "Woooo": (o, o, o, o), "Xoooo": (o, o, o, o), "Wvvvv": (v, v, v, v), "Yvvvv": (v, v, v, v),
+            "Wovvo": (o, v, v, o), "Y1": (o, o, v, o), "R1": (v, o), "R2": (v, v, o, o), "Fbe": (v, v),
+            "X1": (v, v, o, o), "Fmj": (o, o), "X2": (v, v, o, o), "X3": (v, v, o, o), "Y2": (o, v, o, o),
+            "X4": (v, v, o, o), "X5": (v, v, o, o), "Y3": (o, v)}
+    for n, m in work.items():
+        w.tensors[n] = TensorSpec(n, m, len(m) // 2)
+    C, A = ContractSpec, AddSpec
+    w.steps = [
+        # tau~ = T + 1/2 (t t - t t),  tau = T + (t t - t t)
+        A("tt_copy", "Tt", "abij", "T", "abij", 1.0, beta=0.0),
+        C("tt_1", "Tt", "abij", "t1", "ai", "t1", "bj", 0.5),
+        C("tt_2", "Tt", "abij", "t1", "bi", "t1", "aj", -0.5),
+        A("tau_copy", "Tau", "abij", "T", "abij", 1.0, beta=0.0),
+        C("tau_1", "Tau", "abij", "t1", "ai", "t1", "bj", 1.0),
+        C("tau_2", "Tau", "abij", "t1", "bi", "t1", "aj", -1.0),
+        # F_ae, F_mi, F_me
+        C("fae_1", "Fvv", "ae", "V_ovvv", "mafe", "t1", "fm", 1.0, beta=0.0),
+        C("fae_2", "Fvv", "ae", "Tt", "afmn", "V_oovv", "mnef", -0.5),
+        C("fmi_1", "Foo", "mi", "V_ooov", "mnie", "t1", "en", 1.0, beta=0.0),
+        C("fmi_2", "Foo", "mi", "V_oovv", "mnef", "Tt", "efin", 0.5),
+        C("fme", "Fov", "me", "V_oovv", "mnef", "t1", "fn", 1.0, beta=0.0),
+        # W_mnij = <mn||ij> + P(ij) t_j^e <mn||ie> + 1/4 tau_ij^ef <mn||ef>
+        A("wmnij_copy", "Woooo", "mnij", "V_oooo", "mnij", 1.0, beta=0.0),
+        C("wmnij_x", "Xoooo", "mnij", "V_ooov", "mnie", "t1", "ej", 1.0, beta=0.0),
+        A("wmnij_pij", "Woooo", "mnij", "Xoooo", "mnij", 1.0, more=((-1.0, "mnji"),)),
+        C("wmnij_tau", "Woooo", "mnij", "V_oovv", "mnef", "Tau", "efij", 0.25),
+        # W_abef = <ab||ef> - P(ab) t_m^b <am||ef> + 1/4 tau_mn^ab <mn||ef>
+        A("wabef_copy", "Wvvvv", "abef", "V_vvvv", "abef", 1.0, beta=0.0),
+        C("wabef_y", "Yvvvv", "abef", "V_ovvv", "maef", "t1", "bm", 1.0, beta=0.0),
+        A("wabef_pab", "Wvvvv", "abef", "Yvvvv", "abef", 1.0, more=((-1.0, "baef"),)),
+        C("wabef_tau", "Wvvvv", "abef", "Tau", "abmn", "V_oovv", "mnef", 0.25),
+        # W_mbej = <mb||ej> + t_j^f <mb||ef> - t_n^b <mn||ej> - (1/2 t_jn^fb + t_j^f t_n^b) <mn||ef>
+        A("wmbej_copy", "Wovvo", "mbej", "V_ovvo", "mbej", 1.0, beta=0.0),
+        C("wmbej_1", "Wovvo", "mbej", "V_ovvv", "mbef", "t1", "fj", 1.0),
+        C("wmbej_2", "Wovvo", "mbej", "V_ooov", "mnje", "t1", "bn", 1.0),
+        C("wmbej_3", "Wovvo", "mbej", "T", "fbjn", "V_oovv", "mnef", -0.5),
+        C("wmbej_y", "Y1", "mnej", "V_oovv", "mnef", "t1", "fj", 1.0, beta=0.0),
+        C("wmbej_4", "Wovvo", "mbej", "Y1", "mnej", "t1", "bn", -1.0),
+        # T1 residual (terms that read only inputs first)
+        C("r1_ovvo", "R1", "ai", "V_ovvo", "nafi", "t1", "fn", 1.0, beta=0.0),
+        C("r1_ovvv", "R1", "ai", "V_ovvv", "maef", "T", "efim", -0.5),
+        C("r1_ooov", "R1", "ai", "T", "aemn", "V_ooov", "nmie", 0.5),
+        C("r1_fae", "R1", "ai", "Fvv", "ae", "t1", "ei", 1.0),
+        C("r1_fmi", "R1", "ai", "t1", "am", "Foo", "mi", -1.0),
+        C("r1_fme", "R1", "ai", "T", "aeim", "Fov", "me", 1.0),
+        # T2 residual (terms in the order their inputs become ready)
+        A("r2_v", "R2", "abij", "V_oovv", "ijab", 1.0, beta=0.0),
+        C("r2_vvvo", "X4", "abij", "V_vvvo", "abej", "t1", "ei", 1.0, beta=0.0),
+        A("r2_vvvo_pij", "R2", "abij", "X4", "abij", 1.0, more=((-1.0, "abji"),)),
+        C("r2_ooov", "X5", "abij", "t1", "am", "V_ooov", "ijmb", 1.0, beta=0.0),
+        A("r2_ooov_pab", "R2", "abij", "X5", "abij", -1.0, more=((1.0, "baij"),)),
+        C("r2_wmnij", "R2", "abij", "Tau", "abmn", "Woooo", "mnij", 0.5),
+        C("r2_wabef", "R2", "abij", "Wvvvv", "abef", "Tau", "efij", 0.5),
+        A("fbe_copy", "Fbe", "be", "Fvv", "be", 1.0, beta=0.0),
+        C("fbe_1", "Fbe", "be", "t1", "bm", "Fov", "me", -0.5),
+        C("r2_fbe", "X1", "abij", "T", "aeij", "Fbe", "be", 1.0, beta=0.0),
+        A("r2_fbe_pab", "R2", "abij", "X1", "abij", 1.0, more=((-1.0, "baij"),)),
+        A("fmj_copy", "Fmj", "mj", "Foo", "mj", 1.0, beta=0.0),
+        C("fmj_1", "Fmj", "mj", "Fov", "me", "t1", "ej", 0.5),
+        C("r2_fmj", "X2", "abij", "T", "abim", "Fmj", "mj", 1.0, beta=0.0),
+        A("r2_fmj_pij", "R2", "abij", "X2", "abij", -1.0, more=((1.0, "abji"),)),
+        C("r2_y2", "Y2", "mbij", "V_ovvo", "mbej", "t1", "ei", 1.0, beta=0.0),
+        C("r2_wmbej", "X3", "abij", "T", "aeim", "Wovvo", "mbej", 1.0, beta=0.0),
+        C("r2_tty", "X3", "abij", "t1", "am", "Y2", "mbij", -1.0),
+        A("r2_ring_pabij", "R2", "abij", "X3", "abij", 1.0,
+          more=((-1.0, "baij"), (-1.0, "abji"), (1.0, "baji"))),
+        # correlation energy and squared residual norms
+        EnergySpec("e_t2", "V_oovv", "ijab", "T", "abij", 0.25),
+        C("e_y3", "Y3", "jb", "V_oovv", "ijab", "t1", "ai", 1.0, beta=0.0),
+        EnergySpec("e_t1t1", "Y3", "jb", "t1", "bj", 0.5),
+        EnergySpec("r1_sq", "R1", "ai", "R1", "ai", 1.0),
+        EnergySpec("r2_sq", "R2", "abij", "R2", "abij", 1.0),
+    ]
+    return w
