@@ -511,7 +511,9 @@ TAMM_API tamm_status tamm_graph_end(tamm_ctx* ctx, tamm_graph** graph);
 TAMM_API tamm_status tamm_graph_launch(tamm_graph* graph);
 /* Number of library kernels one launch of the graph runs. */
 TAMM_API tamm_status tamm_graph_info(const tamm_graph* graph, int64_t* kernel_launches);
-/* NULL is ignored.  The graph must not be running (synchronise first). */
+/* NULL is ignored.  The graph must not be running (synchronise first).  A
+ * graph destroyed while its context has a capture open is freed when that
+ * capture ends (freeing it inside the capture would invalidate the capture). */
 TAMM_API void tamm_graph_destroy(tamm_graph* graph);
 
 #ifdef __cplusplus

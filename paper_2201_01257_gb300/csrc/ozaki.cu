@@ -88,6 +88,11 @@ __device__ __forceinline__ int64_t mixed_offset(int32_t idx, int n, const int32_
 
 // Offsets of the 8 consecutive summed indices k0..k0+7 (entries past K are unused).
 __device__ __forceinline__ void k_offsets8(const SliceBlock& B, int32_t k0, int64_t (&off)[8]) {
+  if (B.nk == 1) {  // one summed mode: a plain stride, no mixed-radix decomposition
+#pragma unroll
+    for (int j = 0; j < 8; ++j) off[j] = (int64_t)(k0 + j) * B.kstride[0];
+    return;
+  }
   int32_t kk[4] = {0, 0, 0, 0};
   int32_t r = k0;
   int64_t o = 0;

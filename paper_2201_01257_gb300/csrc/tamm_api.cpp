@@ -187,6 +187,11 @@ extern "C" void tamm_ctx_destroy(tamm_ctx* ctx) {
     return;
   }
   cudaSetDevice(ctx->device);
+  for (auto& d : ctx->deferred_graphs) {
+    if (d.second) cudaGraphExecDestroy(d.second);
+    if (d.first) cudaGraphDestroy(d.first);
+  }
+  ctx->deferred_graphs.clear();
   ctx->plans.clear();
   ctx_free(ctx, ctx->scratch.ptr, ctx->scratch.bytes);
   ctx_free(ctx, ctx->d_reduce, ctx->reduce_cap * sizeof(double));
@@ -790,6 +795,11 @@ extern "C" tamm_status tamm_graph_end(tamm_ctx* ctx, tamm_graph** out) {
     cudaGraph_t g = nullptr;
     const cudaError_t e = cudaStreamEndCapture(ctx->stream, &g);
     ctx->capturing = false;
+    for (auto& d : ctx->deferred_graphs) {
+      if (d.second) cudaGraphExecDestroy(d.second);
+      if (d.first) cudaGraphDestroy(d.first);
+    }
+    ctx->deferred_graphs.clear();
     const int64_t n = ctx->launches - ctx->capture_launch0;
     if (ctx->capture_failed || e != cudaSuccess) {
       if (g) cudaGraphDestroy(g);
@@ -831,6 +841,11 @@ extern "C" tamm_status tamm_graph_info(const tamm_graph* g, int64_t* kernel_laun
 
 extern "C" void tamm_graph_destroy(tamm_graph* g) {
   if (!g) return;
+  if (g->ctx && g->ctx->capturing) {  // freed when the open capture ends
+    g->ctx->deferred_graphs.emplace_back(g->graph, g->exec);
+    delete g;
+    return;
+  }
   if (g->exec) cudaGraphExecDestroy(g->exec);
   if (g->graph) cudaGraphDestroy(g->graph);
   (void)cudaGetLastError();

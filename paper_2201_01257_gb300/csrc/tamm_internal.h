@@ -184,6 +184,9 @@ struct tamm_ctx {
   bool capturing = false;                     // between tamm_graph_begin and tamm_graph_end
   bool capture_failed = false;                // an operation failed while capturing
   int64_t capture_launch0 = 0;
+  // graphs destroyed while this context was capturing: freed after the capture ends (destroying a
+  // graph inside an open capture would invalidate it)
+  std::vector<std::pair<cudaGraph_t, cudaGraphExec_t>> deferred_graphs;
 };
 
 namespace tamm {

@@ -107,3 +107,12 @@ def test_scheduled_ccsd_residual(gpu_lib, shape):
             ctx.sync()
             for k in RESIDUAL_OUT:
                 assert np.array_equal(gt[k].download(), ref[k]), (prec, "graph", k)
+            # keep this graph alive across the next capture: its destruction is deferred to the end of
+            # that capture, which must still succeed
+            prev = cap.graph
+        with ctx.capture() as cap2:
+            prev.destroy()
+            sch.execute()
+        cap2.graph.launch()
+        ctx.sync()
+        cap2.graph.destroy()
