@@ -381,7 +381,8 @@ def run_ours(args, rank: int, world: int) -> dict | None:
             "precision": "ozaki_bf16",
             "slices": ({k: v["slices"] for k, v in tuned.items()} if tuned else oz_slices),
             "autotuned": ({k: {"slices": v["slices"], "chunk_k": v["chunk_k"], "tile_policy": v["tile_policy"],
-                               "persistent": v["persistent"], "rel_err_vs_f64_gpu": v["rel_err"],
+                               "persistent": v["persistent"], "shared_scale": v["shared_scale"],
+                               "rel_err_vs_f64_gpu": v["rel_err"],
                                "ms": round(v["ms"], 3)}
                            for k, v in tuned.items()} if tuned else None),
             "autotune_seconds": round(tune_s, 2) if tuned else None,

@@ -122,6 +122,13 @@ TAMM_API const char* tamm_last_error(const tamm_ctx* ctx);
                                     pairs into up to 8 consecutive ranges, computed in parallel into a
                                     workspace and added in range order (deterministic; a different
                                     rounding from the unsplit sum); 0 = never split */
+#define TAMM_OPT_OZAKI_SHARED_SCALE 7 /* split precision: 0 (default) = each block's rows and columns are
+                                         scaled by their own maxima; 1 = every output row (column) takes one
+                                         exponent, the maximum over all operand blocks that feed it, so that
+                                         all block pairs of an output tile share their scaling and the exact
+                                         accumulation chunks run across block pairs (fewer accumulator
+                                         drains when each pair's summed range is short; a pre-pass of row
+                                         maxima and some precision for blocks far below their row's maximum) */
 #define TAMM_OPT_WAIT_CYCLES 5 /* split precision: SM clock cycles a kernel waits for one dependency (an
                                   operand copy, an MMA batch, a drained accumulator) before it records
                                   TAMM_ETIMEOUT and stops; >= 1000, default 4,000,000,000 (about 2 s).
@@ -412,9 +419,10 @@ TAMM_API tamm_status tamm_fp64_peak(tamm_ctx* ctx, int kind, double* tflops);
 /* Autotuner of the split-precision path (TAMM_PREC_OZAKI_BF16) for one
  * contraction, the same tensors and labels as tamm_contract.  It runs the FP64
  * contraction once as the reference, then for each exact-chunk length (1280,
- * 640, 320 summed indices) the smallest slice count (3..8) whose normwise
- * relative error against that reference is at most target_rel_err / 2 on the
- * given operands, times each such candidate under every tile policy
+ * 640, 320 summed indices) and for each scaling (TAMM_OPT_OZAKI_SHARED_SCALE
+ * 0 and 1) the smallest slice count (3..8) whose normwise relative error
+ * against that reference is at most target_rel_err / 2 on the given operands,
+ * times each such candidate under every tile policy
  * (TAMM_OPT_OZAKI_TILE_POLICY) and grid kind (TAMM_OPT_OZAKI_PERSISTENT;
  * CUDA events, mean of three runs after one untimed run) and keeps the
  * fastest.  C's data is not touched: the
@@ -423,14 +431,14 @@ TAMM_API tamm_status tamm_fp64_peak(tamm_ctx* ctx, int kind, double* tflops);
  * context and used by every later tamm_contract of the same tensors and
  * labels with precision TAMM_PREC_OZAKI_BF16 and slices = 0.  Outputs (each
  * may be NULL): the slice count, the chunk length, the tile policy, the grid
- * kind (1 = persistent), the measured error and the mean time in ms of the
- * chosen configuration.  Tune
+ * kind (1 = persistent), the scaling (1 = shared), the measured error and the
+ * mean time in ms of the chosen configuration.  Tune
  * on representative operands: a zero product is refused (TAMM_EINVAL).  Synchronises.  Errors: TAMM_EINVAL, TAMM_ENOMEM,
  * TAMM_ECUDA, TAMM_EUNSUPPORTED (no candidate reaches the target). */
 TAMM_API tamm_status tamm_autotune(tamm_ctx* ctx, const tamm_tensor* C, const char* lc, const tamm_tensor* A,
                                    const char* la, const tamm_tensor* B, const char* lb, double target_rel_err,
-                                   int* slices, int* chunk_k, int* tile_policy, int* persistent, double* rel_err,
-                                   double* ms);
+                                   int* slices, int* chunk_k, int* tile_policy, int* persistent, int* shared_scale,
+                                   double* rel_err, double* ms);
 
 /* ------------------------------------------------------ grouped execution */
 

@@ -30,7 +30,7 @@ TAMM_SYM_DENSE, TAMM_SYM_SPIN, TAMM_SYM_SPIN_IRREP = 0, 1, 2
 TAMM_PREC_F64, TAMM_PREC_OZAKI_BF16, TAMM_PREC_OZAKI_I8, TAMM_PREC_BF16X3 = 0, 1, 2, 3
 KERNEL_CLASSES = ("add", "reduce", "gemm_f64", "slice", "gemm_ozaki", "split_reduce", "triples")
 (TAMM_OPT_OZAKI_CHUNK_K, TAMM_OPT_OZAKI_PERSISTENT, TAMM_OPT_OZAKI_TILE_POLICY, TAMM_OPT_OZAKI_PANELS,
- TAMM_OPT_OZAKI_SPLIT_K, TAMM_OPT_WAIT_CYCLES, TAMM_OPT_TEST_WITHHOLD_COPY) = range(7)
+ TAMM_OPT_OZAKI_SPLIT_K, TAMM_OPT_WAIT_CYCLES, TAMM_OPT_TEST_WITHHOLD_COPY, TAMM_OPT_OZAKI_SHARED_SCALE) = range(8)
 SYM = {"dense": TAMM_SYM_DENSE, "spin": TAMM_SYM_SPIN, "spin_irrep": TAMM_SYM_SPIN_IRREP}
 PREC = {"f64": TAMM_PREC_F64, "ozaki_bf16": TAMM_PREC_OZAKI_BF16, "ozaki_i8": TAMM_PREC_OZAKI_I8,
         "bf16x3": TAMM_PREC_BF16X3}
@@ -84,7 +84,7 @@ PROTOTYPES = [
     ("tamm_triples_energy", _i, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _i, _i, _i64, _vp, _vp]),
     ("tamm_triples_info", _i, [_vp, _vp, _vp, _vp, _vp, _vp, _i64, _i64p, _dp, _ip]),
     ("tamm_fp64_peak", _i, [_vp, _i, _dp]),
-    ("tamm_autotune", _i, [_vp, _vp, _cp, _vp, _cp, _vp, _cp, _d, _ip, _ip, _ip, _ip, _dp, _dp]),
+    ("tamm_autotune", _i, [_vp, _vp, _cp, _vp, _cp, _vp, _cp, _d, _ip, _ip, _ip, _ip, _ip, _dp, _dp]),
     ("tamm_group_begin", _i, [_vp]),
     ("tamm_group_end", _i, [_vp]),
     ("tamm_group_cancel", _i, [_vp]),
@@ -332,14 +332,15 @@ class Context:
 
     def autotune(self, C, lc, A, la, B, lb, target: float = 1e-10) -> dict:
         """Pick slices and chunk length for this split-precision contraction (used when slices = 0)."""
-        s, ck, tp, pe = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        s, ck, tp, pe, sh = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
         err, ms = ctypes.c_double(), ctypes.c_double()
         self.check(self.lib.tamm_autotune(self.handle, C.handle, lc.encode(), A.handle, la.encode(), B.handle,
                                           lb.encode(), float(target), ctypes.byref(s), ctypes.byref(ck),
-                                          ctypes.byref(tp), ctypes.byref(pe), ctypes.byref(err), ctypes.byref(ms)),
+                                          ctypes.byref(tp), ctypes.byref(pe), ctypes.byref(sh), ctypes.byref(err),
+                                          ctypes.byref(ms)),
                    "tamm_autotune")
         return {"slices": s.value, "chunk_k": ck.value, "tile_policy": tp.value, "persistent": pe.value,
-                "rel_err": err.value, "ms": ms.value}
+                "shared_scale": sh.value, "rel_err": err.value, "ms": ms.value}
 
     # grouped execution ---------------------------------------------------
     def group_begin(self) -> None:

@@ -166,7 +166,8 @@ __global__ void __launch_bounds__(256) ozaki_slice_kernel(const double* __restri
                                                           const SliceItem* __restrict__ items,
                                                           uint8_t* __restrict__ tiles, int32_t* __restrict__ exps,
                                                           int kbuf, int bulk, int* __restrict__ status,
-                                                          long long wait_cycles) {
+                                                          long long wait_cycles, int mode,
+                                                          unsigned long long* __restrict__ smax) {
   extern __shared__ __align__(16) double rowbuf[];
   __shared__ unsigned long long rmax[kOzSliceMaxRows];
   __shared__ int rexp[kOzSliceMaxRows];
@@ -230,6 +231,11 @@ __global__ void __launch_bounds__(256) ozaki_slice_kernel(const double* __restri
         m = max(m, (unsigned long long)__double_as_longlong(buf[shift + k]) & 0x7FFFFFFFFFFFFFFFull);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (mode == kOzSliceSharedMax) {  // fold the row maximum into its shared slot, write nothing else
+      if (lane == 0 && live && m != 0ull) atomicMax(&smax[B.shared_off + grow], m);
+      return;
+    }
+    if (mode == kOzSliceSharedPack) m = live ? smax[B.shared_off + grow] : 0ull;
     int e = kOzExpZero;
     if (m != 0ull) (void)frexp(__longlong_as_double((long long)m), &e);
     if (kFloat && m != 0ull) e = 6;  // floating pieces: unit scale
@@ -265,8 +271,9 @@ __global__ void __launch_bounds__(256) ozaki_slice_kernel(const double* __restri
   }
   __syncthreads();
 
-  // ---- general layouts: two passes over global memory
-  const int nch = (K + 7) / 8;
+  // ---- general layouts: two passes over global memory (the maximum pass is skipped when the
+  // exponents come from the shared slots)
+  const int nch = mode == kOzSliceSharedPack ? 0 : (K + 7) / 8;
   for (int u = tid; u < nr * nch; u += blockDim.x) {
     const int r = B.k_contig ? u / nch : u % nr;
     const int ch = B.k_contig ? u % nch : u / nr;
@@ -284,6 +291,15 @@ __global__ void __launch_bounds__(256) ozaki_slice_kernel(const double* __restri
     if (m) atomicMax(&rmax[r], m);
   }
   __syncthreads();
+  if (mode == kOzSliceSharedMax) {
+    for (int r = tid; r < nr; r += blockDim.x)
+      if (roff[r] >= 0 && rmax[r] != 0ull) atomicMax(&smax[B.shared_off + it.r0 + r], rmax[r]);
+    return;
+  }
+  if (mode == kOzSliceSharedPack) {
+    for (int r = tid; r < nr; r += blockDim.x) rmax[r] = roff[r] >= 0 ? smax[B.shared_off + it.r0 + r] : 0ull;
+    __syncthreads();
+  }
   for (int r = tid; r < nr; r += blockDim.x) {
     int e = kOzExpZero;
     if (rmax[r] != 0ull) (void)frexp(__longlong_as_double((long long)rmax[r]), &e);
@@ -579,13 +595,17 @@ __global__ void __launch_bounds__(kThreads, 1) ozaki_gemm_kernel(const __grid_co
         const uint32_t idesc1 = sm100::idesc_bf16_f32(128, full_tile ? H : (uint32_t)((n_valid + 15) & ~15));
         const uint32_t idesc2 = sm100::idesc_bf16_f32(128, 2u * H);
         int kt_next = it.t0 < it.t1 ? tasks[it.t0].k_tiles : 0;
+        int in_chunk = 0;  // position inside the current chunk (no division on the issue path)
         for (int t = it.t0; t < it.t1 && ok; ++t) {
           const int k_tiles = kt_next;
           if (t + 1 < it.t1) kt_next = tasks[t + 1].k_tiles;  // loaded while this task issues
-          int in_chunk = 0;  // position inside the current chunk (no division on the issue path)
+          // a chunk ends with its task, unless the group's tasks share their scaling (then only with the
+          // item's last task)
+          const bool chunk_ends_with_task = !g.shared || t + 1 == it.t1;
+          if (!g.shared) in_chunk = 0;
           for (int kt = 0; kt < k_tiles; ++kt) {
             const bool first = in_chunk == 0;
-            const bool last = ++in_chunk == p.chunk_tiles || kt + 1 == k_tiles;
+            const bool last = ++in_chunk == p.chunk_tiles || (kt + 1 == k_tiles && chunk_ends_with_task);
             if (last) in_chunk = 0;
             if (first) {
               if (!wait_bounded(&acc_empty[buf], ((acc_parity >> buf) & 1u) ^ 1u, abort_flag, p.status,
@@ -698,9 +718,15 @@ __global__ void __launch_bounds__(kThreads, 1) ozaki_gemm_kernel(const __grid_co
         if (has_col) eb_next = b_exp[t0.b_exp + bcol];
         kt_next = t0.k_tiles;
       }
-      for (int t = it.t0; t < it.t1; ++t, ++task_count) {
-        const int ea = ea_next, eb = eb_next, k_tiles = kt_next;
-        if (t + 1 < it.t1) {
+      // shared scaling: the item's tasks are one sequence of chunks with the first task's scales (every
+      // task has the same exponents), as the MMA issuer chunks them
+      int shared_tiles = 0;
+      if (g.shared)
+        for (int t = it.t0; t < it.t1; ++t) shared_tiles += tasks[t].k_tiles;
+      const int t_end = g.shared ? min(it.t1, it.t0 + 1) : it.t1;
+      for (int t = it.t0; t < t_end; ++t, ++task_count) {
+        const int ea = ea_next, eb = eb_next, k_tiles = g.shared ? shared_tiles : kt_next;
+        if (t + 1 < t_end) {
           const OzTask tn = tasks[t + 1];
           ea_next = a_exp[tn.a_exp + arow];
           if (has_col) eb_next = b_exp[tn.b_exp + bcol];
@@ -839,7 +865,8 @@ static std::mutex g_attr_mutex;
 
 template <int S, bool kFloat = false>
 static cudaError_t slice_dispatch(tamm_ctx* ctx, const double* src, const SliceBlock* blocks, const SliceItem* items,
-                                  int64_t n_items, uint8_t* tiles, int32_t* exps, int warps, int kbuf) {
+                                  int64_t n_items, uint8_t* tiles, int32_t* exps, int warps, int kbuf, int mode,
+                                  unsigned long long* smax) {
   static size_t attr_bytes[kMaxDevices] = {};  // dynamic shared memory opted in so far, per device
   const size_t smem = (size_t)warps * kbuf * sizeof(double);
   if (ctx->device < 0 || ctx->device >= kMaxDevices) return cudaErrorInvalidDevice;
@@ -854,30 +881,31 @@ static cudaError_t slice_dispatch(tamm_ctx* ctx, const double* src, const SliceB
   }
   const int bulk = (reinterpret_cast<uintptr_t>(src) & 15) == 0 ? 1 : 0;
   ozaki_slice_kernel<S, kFloat><<<(unsigned)n_items, 32 * warps, smem, ctx->stream>>>(
-      src, blocks, items, tiles, exps, kbuf, bulk, ctx->d_status, ctx->oz_wait_cycles);
+      src, blocks, items, tiles, exps, kbuf, bulk, ctx->d_status, ctx->oz_wait_cycles, mode, smax);
   return cudaGetLastError();
 }
 
 cudaError_t launch_ozaki_slice(tamm_ctx* ctx, const double* src, const SliceBlock* blocks, const SliceItem* items,
                                int64_t n_items, int S, bool float_split, uint8_t* tiles, int32_t* exps, int warps,
-                               int kbuf) {
+                               int kbuf, int mode, unsigned long long* smax) {
   if (n_items == 0) return cudaSuccess;
   if (warps < 1 || warps > 8 || kbuf < 2 || (size_t)warps * kbuf * sizeof(double) > kOzSliceSmemMax)
     return cudaErrorInvalidValue;
+  if (mode != kOzSliceOwn && (!smax || float_split)) return cudaErrorInvalidValue;
   kernel_begin(ctx, TAMM_KERNEL_SLICE);
   cudaError_t e = cudaErrorInvalidValue;
   if (float_split) {
-    if (S == 3) e = slice_dispatch<3, true>(ctx, src, blocks, items, n_items, tiles, exps, warps, kbuf);
+    if (S == 3) e = slice_dispatch<3, true>(ctx, src, blocks, items, n_items, tiles, exps, warps, kbuf, mode, smax);
     kernel_end(ctx, TAMM_KERNEL_SLICE);
     return e;
   }
   switch (S) {
-    case 3: e = slice_dispatch<3>(ctx, src, blocks, items, n_items, tiles, exps, warps, kbuf); break;
-    case 4: e = slice_dispatch<4>(ctx, src, blocks, items, n_items, tiles, exps, warps, kbuf); break;
-    case 5: e = slice_dispatch<5>(ctx, src, blocks, items, n_items, tiles, exps, warps, kbuf); break;
-    case 6: e = slice_dispatch<6>(ctx, src, blocks, items, n_items, tiles, exps, warps, kbuf); break;
-    case 7: e = slice_dispatch<7>(ctx, src, blocks, items, n_items, tiles, exps, warps, kbuf); break;
-    case 8: e = slice_dispatch<8>(ctx, src, blocks, items, n_items, tiles, exps, warps, kbuf); break;
+    case 3: e = slice_dispatch<3>(ctx, src, blocks, items, n_items, tiles, exps, warps, kbuf, mode, smax); break;
+    case 4: e = slice_dispatch<4>(ctx, src, blocks, items, n_items, tiles, exps, warps, kbuf, mode, smax); break;
+    case 5: e = slice_dispatch<5>(ctx, src, blocks, items, n_items, tiles, exps, warps, kbuf, mode, smax); break;
+    case 6: e = slice_dispatch<6>(ctx, src, blocks, items, n_items, tiles, exps, warps, kbuf, mode, smax); break;
+    case 7: e = slice_dispatch<7>(ctx, src, blocks, items, n_items, tiles, exps, warps, kbuf, mode, smax); break;
+    case 8: e = slice_dispatch<8>(ctx, src, blocks, items, n_items, tiles, exps, warps, kbuf, mode, smax); break;
   }
   kernel_end(ctx, TAMM_KERNEL_SLICE);
   return e;
@@ -1015,6 +1043,11 @@ struct OzakiPlan : Plan {
   int64_t n_red = 0;
   std::unique_ptr<AddPlan> perm_out;
   size_t off_ta = 0, off_tb = 0, off_ea = 0, off_eb = 0, off_x = 0, off_ws = 0, scratch_bytes = 0;
+  // shared scaling: one exponent per output row (A operand rows with the same free-left tiles) and per
+  // output column (B operand rows with the same free-right tiles), over every block that feeds it
+  bool shared = false;
+  int64_t slots_a = 0, slots_b = 0;
+  size_t off_sa = 0, off_sb = 0;
   int warps_a = 8, kbuf_a = 2, warps_b = 8, kbuf_b = 2;  // slicing launch shapes
 
   // Geometry of block b of the GEMM-order operand `gemm` (blocks of `native`
@@ -1066,8 +1099,19 @@ struct OzakiPlan : Plan {
   }
 
   OzakiPlan(tamm_ctx* c, const tamm_tensor* C, const char* lc, const tamm_tensor* A, const char* la,
-            const tamm_tensor* B, const char* lb, int slices, int tile_policy, bool panels, bool allow_split)
-      : Plan(c), lay(c, C, lc, A, la, B, lb), S(slices) {
+            const tamm_tensor* B, const char* lb, int slices, int tile_policy, bool panels, bool allow_split,
+            bool shared_scale)
+      : Plan(c), lay(c, C, lc, A, la, B, lb), S(slices), shared(shared_scale) {
+    std::map<std::vector<int64_t>, int64_t> slot_a, slot_b;  // free tile tuple -> first slot
+    auto slot_of = [](std::map<std::vector<int64_t>, int64_t>& m, int64_t& n, std::vector<int64_t> key,
+                      int64_t rows) {
+      auto it = m.find(key);
+      if (it != m.end()) return it->second;
+      const int64_t base = n;
+      m[key] = base;
+      n += rows;
+      return base;
+    };
     const int nfl = (int)lay.free_left.size(), nfr = (int)lay.free_right.size(), nk = (int)lay.summed.size();
     auto perm_of = [](const std::string& need, const std::string& have) {
       std::vector<int> p(need.size());
@@ -1090,6 +1134,10 @@ struct OzakiPlan : Plan {
       R.tile_off = ta;
       R.exp_off = ea;
       R.dst_row0 = 0;
+      {
+        const int64_t* gt = &Lg.tiles[(size_t)(b * Lg.nm)];
+        R.shared_off = slot_of(slot_a, slots_a, std::vector<int64_t>(gt, gt + nfl), R.rows);
+      }
       ta += (int64_t)R.row_tiles * R.k_tiles * S * kOzTileM * 32;
       ea += (int64_t)R.row_tiles * kOzTileM;
       sa.push_back(R);
@@ -1144,6 +1192,8 @@ struct OzakiPlan : Plan {
       gg.N = (int32_t)Np;
       gg.n_tile = H;
       gg.nsplit = 1;
+      gg.shared = shared ? 1 : 0;
+      gg.pad = 0;
       gg.ws_off = 0;
       if (mem.size() == 1) {
         gg.c_off = O.off[(size_t)g0.out_block];
@@ -1184,6 +1234,10 @@ struct OzakiPlan : Plan {
             R.tile_off = im.tile_off;
             R.exp_off = im.exp_off;
             R.dst_row0 = row0;
+            {
+              const int64_t* gt = &Rg.tiles[(size_t)(key[m + 1] * Rg.nm)];
+              R.shared_off = slot_of(slot_b, slots_b, std::vector<int64_t>(gt + nk, gt + nk + nfr), R.rows);
+            }
             const bool last = m + 1 == mem.size();
             ext_b.push_back(last ? row_tiles * H - row0 : R.rows);
             row0 += R.rows;
@@ -1267,6 +1321,12 @@ struct OzakiPlan : Plan {
           for (int32_t nt = 0; nt < nts; ++nt) items.push_back({gi, mt, nt, gg.nsplit > 1 ? sp : -1, t0, t1});
       }
     }
+    if (shared) {
+      off_sa = scratch_bytes;
+      scratch_bytes += align((size_t)std::max<int64_t>(slots_a, 1) * 8);
+      off_sb = scratch_bytes;
+      scratch_bytes += align((size_t)std::max<int64_t>(slots_b, 1) * 8);
+    }
     if (ws_doubles) {
       off_ws = scratch_bytes;
       scratch_bytes += align((size_t)ws_doubles * 8);
@@ -1298,6 +1358,7 @@ void run_contract_ozaki(tamm_ctx* ctx, double alpha, tamm_tensor* C, const char*
   bool persistent = ctx->oz_persistent;
   const bool panels = ctx->oz_panels;
   const bool allow_split = ctx->oz_split;
+  bool shared = ctx->oz_shared;
   if (slices == 0) {
     slices = kOzDefaultSlices;
     if (!float_split) {
@@ -1307,13 +1368,14 @@ void run_contract_ozaki(tamm_ctx* ctx, double alpha, tamm_tensor* C, const char*
         chunk_k = t->second.chunk_k;
         tile_policy = t->second.tile_policy;
         persistent = t->second.persistent;
+        shared = t->second.shared;
       }
     }
   }
   if (slices < kOzMinSlices || slices > kOzMaxSlices)
     throw Error(TAMM_EINVAL, "ozaki: slices must be %d..%d (0 = %d)", kOzMinSlices, kOzMaxSlices, kOzDefaultSlices);
   const std::string key = "oz" + std::to_string(slices) + "|" + std::to_string(tile_policy) +
-                          (panels ? "p" : "") + (allow_split ? "s|" : "|") +
+                          (panels ? "p" : "") + (allow_split ? "s" : "") + (shared && !float_split ? "h|" : "|") +
                           std::to_string(C->id) + "|" + lc + "|" + std::to_string(A->id) + "|" + la + "|" +
                           std::to_string(B->id) + "|" + lb;
   OzakiPlan* p;
@@ -1322,7 +1384,7 @@ void run_contract_ozaki(tamm_ctx* ctx, double alpha, tamm_tensor* C, const char*
     p = static_cast<OzakiPlan*>(itp->second.get());
   } else {
     if (ctx->capturing) throw Error(TAMM_EINVAL, "a new contraction plan cannot be built during graph capture");
-    p = new OzakiPlan(ctx, C, lc, A, la, B, lb, slices, tile_policy, panels, allow_split);
+    p = new OzakiPlan(ctx, C, lc, A, la, B, lb, slices, tile_policy, panels, allow_split, shared && !float_split);
     ctx->plans[key].reset(p);
   }
   OzOpRecord op;
@@ -1367,12 +1429,28 @@ void execute_ozaki(tamm_ctx* ctx, const std::vector<OzOpRecord>& ops) {
     uint8_t* tb = (uint8_t*)(s + p->off_tb);
     int32_t* ea = (int32_t*)(s + p->off_ea);
     int32_t* eb = (int32_t*)(s + p->off_eb);
-    cuda_check(launch_ozaki_slice(ctx, ops[i].left, p->d_sa, p->d_ia, p->n_ia, ops[i].slices, ops[i].float_split,
-                                  ta, ea, p->warps_a, p->kbuf_a),
-               "ozaki slice (left)");
-    cuda_check(launch_ozaki_slice(ctx, ops[i].right, p->d_sb, p->d_ib, p->n_ib, ops[i].slices,
-                                  ops[i].float_split, tb, eb, p->warps_b, p->kbuf_b),
-               "ozaki slice (right)");
+    if (p->shared) {
+      // shared scaling: every row maximum into its slot, then every row sliced with its slot's exponent
+      unsigned long long* sma = (unsigned long long*)(s + p->off_sa);
+      unsigned long long* smb = (unsigned long long*)(s + p->off_sb);
+      cuda_check(cudaMemsetAsync(sma, 0, (size_t)p->slots_a * 8, ctx->stream), "shared maxima clear");
+      cuda_check(cudaMemsetAsync(smb, 0, (size_t)p->slots_b * 8, ctx->stream), "shared maxima clear");
+      for (int mode : {kOzSliceSharedMax, kOzSliceSharedPack}) {
+        cuda_check(launch_ozaki_slice(ctx, ops[i].left, p->d_sa, p->d_ia, p->n_ia, ops[i].slices, false, ta, ea,
+                                      p->warps_a, p->kbuf_a, mode, sma),
+                   "ozaki slice (left)");
+        cuda_check(launch_ozaki_slice(ctx, ops[i].right, p->d_sb, p->d_ib, p->n_ib, ops[i].slices, false, tb, eb,
+                                      p->warps_b, p->kbuf_b, mode, smb),
+                   "ozaki slice (right)");
+      }
+    } else {
+      cuda_check(launch_ozaki_slice(ctx, ops[i].left, p->d_sa, p->d_ia, p->n_ia, ops[i].slices, ops[i].float_split,
+                                    ta, ea, p->warps_a, p->kbuf_a),
+                 "ozaki slice (left)");
+      cuda_check(launch_ozaki_slice(ctx, ops[i].right, p->d_sb, p->d_ib, p->n_ib, ops[i].slices,
+                                    ops[i].float_split, tb, eb, p->warps_b, p->kbuf_b),
+                 "ozaki slice (right)");
+    }
     OzProblem& pr = probs[i];
     pr.a_tiles = ta;
     pr.b_tiles = tb;

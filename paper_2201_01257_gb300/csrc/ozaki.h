@@ -46,6 +46,7 @@ struct SliceBlock {
   int64_t src_off;
   int64_t tile_off;  // byte offset of this block's first tile in the sliced buffer (tiles ordered [row tile][k tile])
   int64_t exp_off;   // exponent of row 0
+  int64_t shared_off;  // shared scaling: slot of row 0 in the shared row-maximum array (see kOzSliceShared*)
   int32_t rows, K;
   int32_t row_tiles, k_tiles;
   int32_t nr, nk;
@@ -56,6 +57,15 @@ struct SliceBlock {
   int32_t tile_rows; // rows per tile H (a multiple of 16, <= 128): a tile is S slices of H x 16 bf16
   int32_t dst_row0;  // image row of this block's row 0 (blocks concatenated along rows share an image)
 };
+
+// Slicing modes.  Own: each row's exponent comes from the row's maximum over this block.  Shared
+// scaling takes two launches: kOzSliceSharedMax folds every row's maximum into its slot of a shared
+// array (all blocks whose rows meet the same output rows or columns share slots) and writes no
+// tiles; kOzSliceSharedPack then slices every row with the exponent of its slot, so that all block
+// pairs of an output tile are scaled alike and their products may share one exact accumulation chunk.
+constexpr int kOzSliceOwn = 0;
+constexpr int kOzSliceSharedMax = 1;
+constexpr int kOzSliceSharedPack = 2;
 
 constexpr int kOzSliceMaxRows = 128;  // rows per slicing CTA
 constexpr size_t kOzSliceSmemBudget = 104 * 1024;  // warp row buffers of one slicing CTA (two CTAs per SM)
@@ -83,6 +93,9 @@ struct OzGroup {
   int32_t task_begin, task_end;
   int32_t n_tile;  // output columns per work item = rows per B tile (a multiple of 16, <= 128)
   int32_t nsplit;
+  int32_t shared;  // every task of the group has the same row and column exponents (shared scaling): the
+                   // exact accumulation chunks run across task boundaries
+  int32_t pad;
 };
 
 struct OzTask {
@@ -193,9 +206,11 @@ void oz_slicing_items(std::vector<SliceBlock>& recs, const std::vector<int32_t>&
                       std::vector<SliceItem>& items, int& warps, int& kbuf);
 
 // float_split (S = 3 only): BF16x3 floating pieces instead of integer digits.
+// mode: kOzSliceOwn / kOzSliceSharedMax / kOzSliceSharedPack; smax: the shared row-maximum array (|x| bit
+// patterns, zeroed before the kOzSliceSharedMax launches), unused in kOzSliceOwn.
 cudaError_t launch_ozaki_slice(tamm_ctx* ctx, const double* src, const SliceBlock* blocks, const SliceItem* items,
                                int64_t n_items, int S, bool float_split, uint8_t* tiles, int32_t* exps, int warps,
-                               int kbuf);
+                               int kbuf, int mode = kOzSliceOwn, unsigned long long* smax = nullptr);
 // Reduction of split groups' partials into C (after the GEMM launch).
 cudaError_t launch_ozaki_reduce(tamm_ctx* ctx, const OzReduceItem* items, int64_t n_items, const OzGroup* groups,
                                 const double* ws, double* c, const int64_t* col_base, const int32_t* col_stride,

@@ -110,6 +110,7 @@ struct TunedConfig {
   int chunk_k;
   int tile_policy;
   bool persistent;
+  bool shared;  // shared row/column scaling (TAMM_OPT_OZAKI_SHARED_SCALE)
 };
 
 }  // namespace tamm
@@ -168,6 +169,7 @@ struct tamm_ctx {
   int oz_tile_policy = 1;      // split precision: output columns per work item (TAMM_OPT_OZAKI_TILE_POLICY)
   bool oz_panels = true;       // split precision: concatenate output blocks sharing their A blocks
   bool oz_split = true;        // split precision: split long summed ranges of small contractions
+  bool oz_shared = false;      // split precision: shared row/column scaling (TAMM_OPT_OZAKI_SHARED_SCALE)
   long long oz_wait_cycles = 4000000000ll;  // limit of a kernel's dependency waits (TAMM_OPT_WAIT_CYCLES)
   int oz_test_withhold = 0;    // failure-path test hook (TAMM_OPT_TEST_WITHHOLD_COPY), one launch
   int64_t launches = 0;    // kernels launched by this context

@@ -209,6 +209,8 @@ struct TriplesPlan : Plan {
 
   // split path (built on first use for a slice count and tile policy)
   int oz_S = 0, oz_policy = -1;
+  bool oz_shared = false;
+  int64_t slots_a = 0, slots_b = 0;  // shared scaling: rows (x,y) of each (x-tile, y-tile), columns z of each z-tile
   std::vector<SliceBlock> rec[4];  // A from Tq, A from Vp, B from Vooov, B from Tz
   std::vector<SliceItem> sitems[4];
   int warps[4] = {8, 8, 8, 8}, kbuf[4] = {2, 2, 2, 2};
@@ -442,10 +444,23 @@ struct TriplesPlan : Plan {
   }
 
   // Split-precision images and tasks for slice count S (kept until another S or policy is asked for).
-  void build_split(int S, int policy) {
-    if (S == oz_S && policy == oz_policy) return;
+  void build_split(int S, int policy, bool shared) {
+    if (S == oz_S && policy == oz_policy && shared == oz_shared) return;
     oz_S = S;
     oz_policy = policy;
+    oz_shared = shared;
+    // shared-scaling slots: one per U row (x,y) of each tile pair and one per U column z of each tile
+    std::vector<int64_t> base_a((size_t)ntv * ntv), base_b((size_t)ntv);
+    slots_a = slots_b = 0;
+    for (int x = 0; x < ntv; ++x)
+      for (int y = 0; y < ntv; ++y) {
+        base_a[(size_t)(x * ntv + y)] = slots_a;
+        slots_a += V->size[(size_t)x] * V->size[(size_t)y];
+      }
+    for (int z = 0; z < ntv; ++z) {
+      base_b[(size_t)z] = slots_b;
+      slots_b += V->size[(size_t)z];
+    }
     for (int s = 0; s < 4; ++s) {
       rec[s].clear();
       sitems[s].clear();
@@ -457,7 +472,7 @@ struct TriplesPlan : Plan {
     std::vector<int32_t> iaq((size_t)no * ntv * ntv * nto, -1), iaz((size_t)no * ntv * ntv * ntv, -1);
     std::vector<int32_t> ibq((size_t)no * no * nto * ntv, -1), ibz((size_t)no * no * ntv * ntv, -1);
     auto add_rec = [&](int set, int64_t src_off, int64_t rows, int32_t rstride, int64_t K, int32_t kstride,
-                       bool is_a, int H) {
+                       bool is_a, int H, int64_t slot) {
       SliceBlock B;
       memset(&B, 0, sizeof(B));
       B.src_off = src_off;
@@ -475,6 +490,7 @@ struct TriplesPlan : Plan {
       B.tile_rows = is_a ? kOzTileM : H;
       B.row_tiles = (int32_t)((rows + B.tile_rows - 1) / B.tile_rows);
       B.dst_row0 = 0;
+      B.shared_off = slot;
       int64_t& bytes = is_a ? a_bytes : b_bytes;
       int64_t& erow = is_a ? a_rows : b_rows;
       B.tile_off = bytes;
@@ -493,7 +509,8 @@ struct TriplesPlan : Plan {
         if (tt[0] != occ[(size_t)r].tile) continue;
         const int64_t nx = V->size[(size_t)tt[1]], ny = V->size[(size_t)tt[2]], nk = O->size[(size_t)tt[3]];
         iaq[(size_t)(((r * ntv + tt[1]) * ntv + tt[2]) * nto + tt[3])] =
-            add_rec(0, T2q.off[(size_t)b] + occ[(size_t)r].loc * nx * ny * nk, nx * ny, (int32_t)nk, nk, 1, true, 0);
+            add_rec(0, T2q.off[(size_t)b] + occ[(size_t)r].loc * nx * ny * nk, nx * ny, (int32_t)nk, nk, 1, true, 0,
+                    base_a[(size_t)(tt[1] * ntv + tt[2])]);
       }
     for (int32_t p = 0; p < no; ++p)
       for (int64_t b = 0; b < Vp->n_blocks; ++b) {
@@ -501,7 +518,8 @@ struct TriplesPlan : Plan {
         if (tt[0] != occ[(size_t)p].tile) continue;
         const int64_t nx = V->size[(size_t)tt[1]], ny = V->size[(size_t)tt[2]], nk = V->size[(size_t)tt[3]];
         iaz[(size_t)(((p * ntv + tt[1]) * ntv + tt[2]) * ntv + tt[3])] =
-            add_rec(1, Vp->off[(size_t)b] + occ[(size_t)p].loc * nx * ny * nk, nx * ny, (int32_t)nk, nk, 1, true, 0);
+            add_rec(1, Vp->off[(size_t)b] + occ[(size_t)p].loc * nx * ny * nk, nx * ny, (int32_t)nk, nk, 1, true, 0,
+                    base_a[(size_t)(tt[1] * ntv + tt[2])]);
       }
     // B images of every ordered occupied pair and stored block
     for (int32_t p = 0; p < no; ++p)
@@ -515,7 +533,7 @@ struct TriplesPlan : Plan {
             const int64_t nk = O->size[(size_t)tm], nz = V->size[(size_t)tz];
             ibq[(size_t)(((p * no + q) * nto + tm) * ntv + tz)] =
                 add_rec(2, vo_->off[(size_t)b] + ((int64_t)op.loc * O->size[(size_t)oq.tile] + oq.loc) * nk * nz, nz, 1,
-                        nk, (int32_t)nz, false, H_of(tz));
+                        nk, (int32_t)nz, false, H_of(tz), base_b[(size_t)tz]);
           }
         for (int te = 0; te < ntv; ++te)
           for (int tz = 0; tz < ntv; ++tz) {
@@ -524,7 +542,7 @@ struct TriplesPlan : Plan {
             const int64_t nk = V->size[(size_t)te], nz = V->size[(size_t)tz];
             ibz[(size_t)(((p * no + q) * ntv + te) * ntv + tz)] =
                 add_rec(3, Tz->off[(size_t)b] + ((int64_t)op.loc * O->size[(size_t)oq.tile] + oq.loc) * nk * nz, nz, 1,
-                        nk, (int32_t)nz, false, H_of(tz));
+                        nk, (int32_t)nz, false, H_of(tz), base_b[(size_t)tz]);
           }
       }
     for (int s = 0; s < 4; ++s) oz_slicing_items(rec[s], ext[s], sitems[s], warps[s], kbuf[s]);
@@ -549,6 +567,7 @@ struct TriplesPlan : Plan {
           gg.N = (int32_t)nz;
           gg.n_tile = H;
           gg.nsplit = 1;
+          gg.shared = shared ? 1 : 0;
           gg.task_begin = (int32_t)tasks.size();
           for_pairs(t, tx, ty, tz, *t2_, *vo_, *vv_, [&](bool is_z, int tk, int32_t p, int32_t q, int32_t r) {
             int32_t ia, ib, sa, sb;
@@ -666,17 +685,23 @@ void run_triples(tamm_ctx* ctx, const tamm_tensor* T2, const tamm_tensor* T1, co
     ctx->plans[key].reset(p);
   }
   if (precision == TAMM_PREC_OZAKI_BF16) {
-    if (ctx->capturing && (p->oz_S != slices || p->oz_policy != ctx->oz_tile_policy))
+    if (ctx->capturing && (p->oz_S != slices || p->oz_policy != ctx->oz_tile_policy || p->oz_shared != ctx->oz_shared))
       throw Error(TAMM_EINVAL, "triples: split-precision images must be planned before graph capture");
-    p->build_split(slices, ctx->oz_tile_policy);
+    p->build_split(slices, ctx->oz_tile_policy, ctx->oz_shared);
   }
   // scratch: U workspace, partials, then (split path) images and exponents
   auto align = [](size_t x) { return (x + 1023) & ~size_t(1023); };
   const size_t ws_bytes = align((size_t)std::max<int64_t>(p->ws_elems, 1) * 8);
   const size_t part_bytes = align((size_t)std::max<int64_t>(p->n_eitems, 1) * 8);
   size_t total = ws_bytes + part_bytes;
-  size_t off_a = 0, off_b = 0, off_ea = 0, off_eb = 0;
+  size_t off_a = 0, off_b = 0, off_ea = 0, off_eb = 0, off_sa = 0, off_sb = 0;
   if (precision == TAMM_PREC_OZAKI_BF16) {
+    if (p->oz_shared) {
+      off_sa = total;
+      total += align((size_t)std::max<int64_t>(p->slots_a, 1) * 8);
+      off_sb = total;
+      total += align((size_t)std::max<int64_t>(p->slots_b, 1) * 8);
+    }
     off_a = total;
     total += align((size_t)p->a_bytes);
     off_b = total;
@@ -702,10 +727,23 @@ void run_triples(tamm_ctx* ctx, const tamm_tensor* T2, const tamm_tensor* T1, co
     ea = (int32_t*)(scratch + off_ea);
     eb = (int32_t*)(scratch + off_eb);
     const double* src[4] = {p->Tq->data, p->Vp->data, Vo->data, p->Tz->data};
-    for (int s = 0; s < 4; ++s)
-      cuda_check(launch_ozaki_slice(ctx, src[s], p->d_rec[s], p->d_sitems[s], (int64_t)p->sitems[s].size(), slices,
-                                    false, s < 2 ? ta : tb, s < 2 ? ea : eb, p->warps[s], p->kbuf[s]),
-                 "triples slicing");
+    if (p->oz_shared) {
+      // one exponent per U row and column over all six block pairs: maxima first, then the slices
+      unsigned long long* sm[2] = {(unsigned long long*)(scratch + off_sa), (unsigned long long*)(scratch + off_sb)};
+      cuda_check(cudaMemsetAsync(sm[0], 0, (size_t)p->slots_a * 8, ctx->stream), "triples maxima clear");
+      cuda_check(cudaMemsetAsync(sm[1], 0, (size_t)p->slots_b * 8, ctx->stream), "triples maxima clear");
+      for (int mode : {kOzSliceSharedMax, kOzSliceSharedPack})
+        for (int s = 0; s < 4; ++s)
+          cuda_check(launch_ozaki_slice(ctx, src[s], p->d_rec[s], p->d_sitems[s], (int64_t)p->sitems[s].size(),
+                                        slices, false, s < 2 ? ta : tb, s < 2 ? ea : eb, p->warps[s], p->kbuf[s],
+                                        mode, sm[s < 2 ? 0 : 1]),
+                     "triples slicing");
+    } else {
+      for (int s = 0; s < 4; ++s)
+        cuda_check(launch_ozaki_slice(ctx, src[s], p->d_rec[s], p->d_sitems[s], (int64_t)p->sitems[s].size(), slices,
+                                      false, s < 2 ? ta : tb, s < 2 ? ea : eb, p->warps[s], p->kbuf[s]),
+                   "triples slicing");
+    }
   }
   for (int64_t bch = 0; bch < p->n_batches; ++bch) {
     if (precision == TAMM_PREC_F64) {

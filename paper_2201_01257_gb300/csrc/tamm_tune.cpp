@@ -17,6 +17,9 @@
 //   * the run time of every passing candidate under each tile policy and
 //     grid kind (CUDA events, after one untimed run); both split the same
 //     arithmetic into different work items, so they change time, not results;
+//   * all of the above once with each block's own row/column scaling and once
+//     with shared scaling (one exponent per output row and column, so that
+//     short block pairs share accumulation chunks), whose error differs;
 // and keeps the fastest.  The result is remembered per (tensors, labels) and
 // used by tamm_contract whenever slices = 0.
 #include <algorithm>
@@ -75,7 +78,7 @@ double diff_norm(tamm_ctx* ctx, const double* x, const double* y, int64_t n) {
 extern "C" tamm_status tamm_autotune(tamm_ctx* ctx, const tamm_tensor* C, const char* lc, const tamm_tensor* A,
                                      const char* la, const tamm_tensor* B, const char* lb, double target_rel_err,
                                      int* slices, int* chunk_k, int* tile_policy, int* persistent,
-                                     double* rel_err, double* ms) {
+                                     int* shared_scale, double* rel_err, double* ms) {
   if (!ctx) return TAMM_EINVAL;
   void* ref = nullptr;
   void* trial = nullptr;
@@ -84,6 +87,7 @@ extern "C" tamm_status tamm_autotune(tamm_ctx* ctx, const tamm_tensor* C, const 
   const int saved_chunk = ctx->oz_chunk_k;
   const int saved_policy = ctx->oz_tile_policy;
   const bool saved_persistent = ctx->oz_persistent;
+  const bool saved_shared = ctx->oz_shared;
   tamm_status st = TAMM_OK;
   try {
     if (ctx->host_only) throw Error(TAMM_ECUDA, "host-only context (device -1) cannot run device work");
@@ -105,9 +109,11 @@ extern "C" tamm_status tamm_autotune(tamm_ctx* ctx, const tamm_tensor* C, const 
     cuda_check(cudaEventCreate(&e0), "cudaEventCreate");
     cuda_check(cudaEventCreate(&e1), "cudaEventCreate");
     int best_s = 0, best_chunk = 0, best_policy = 0;
-    bool best_persistent = false;
+    bool best_persistent = false, best_shared = false;
     double best_ms = 0.0, best_err = 0.0;
+    for (int sh = 0; sh < 2; ++sh)
     for (int chunk : kChunks) {
+      ctx->oz_shared = sh != 0;
       ctx->oz_chunk_k = chunk;
       ctx->oz_tile_policy = saved_policy;
       ctx->oz_persistent = saved_persistent;
@@ -143,6 +149,7 @@ extern "C" tamm_status tamm_autotune(tamm_ctx* ctx, const tamm_tensor* C, const 
           best_chunk = chunk;
           best_policy = policy;
           best_persistent = persistent;
+          best_shared = sh != 0;
           best_ms = t;
           best_err = err_ok;
         }
@@ -151,8 +158,9 @@ extern "C" tamm_status tamm_autotune(tamm_ctx* ctx, const tamm_tensor* C, const 
     if (best_s == 0)
       throw Error(TAMM_EUNSUPPORTED, "autotune: no slice count (<= %d) reaches %.3g on these operands", kOzMaxSlices,
                   target_rel_err);
-    ctx->tuned[tune_key(C, lc, A, la, B, lb)] = {best_s, best_chunk, best_policy, best_persistent};
+    ctx->tuned[tune_key(C, lc, A, la, B, lb)] = {best_s, best_chunk, best_policy, best_persistent, best_shared};
     if (slices) *slices = best_s;
+    if (shared_scale) *shared_scale = best_shared ? 1 : 0;
     if (chunk_k) *chunk_k = best_chunk;
     if (tile_policy) *tile_policy = best_policy;
     if (persistent) *persistent = best_persistent ? 1 : 0;
@@ -169,6 +177,7 @@ extern "C" tamm_status tamm_autotune(tamm_ctx* ctx, const tamm_tensor* C, const 
   ctx->oz_chunk_k = saved_chunk;
   ctx->oz_tile_policy = saved_policy;
   ctx->oz_persistent = saved_persistent;
+  ctx->oz_shared = saved_shared;
   if (e0) cudaEventDestroy(e0);
   if (e1) cudaEventDestroy(e1);
   if (ref) ctx_free(ctx, ref, bytes);
