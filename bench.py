@@ -882,18 +882,24 @@ def run_doubles_term_case(args) -> dict:
     run = gw.Runner(ctx, w, sp, T)
     run.run("f64")
     st = next(x for x in w.steps if x.name == name)
+    tuned = run.autotune(1e-10, steps=[st])[st.name]  # slices, chunk, tile policy, grid and scaling
     for _ in range(max(1, args.warmup)):
-        run.run("ozaki_bf16", SLICES, steps=[st])
+        run.run("ozaki_bf16", 0, steps=[st])
     ctx.sync()
+    ctx.profile_read()
+    ctx.profile(True)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
     for _ in range(args.steps):
-        run.run("ozaki_bf16", SLICES, steps=[st])
+        run.run("ozaki_bf16", 0, steps=[st])
     e1.record()
     ctx.sync()
+    ctx.profile(False)
+    prof = ctx.profile_read()
     ms = e0.elapsed_time(e1) / args.steps
-    return {"case": f"{w.name} {name}, split precision", "ms": round(ms, 3),
-            "TFLOP/s": round(run.flops(st) / ms / 1e9, 3), "nonzero_block_flops": run.flops(st)}
+    return {"case": f"{w.name} {name}, split precision, autotuned", "ms": round(ms, 3),
+            "TFLOP/s": round(run.flops(st) / ms / 1e9, 3), "nonzero_block_flops": run.flops(st), "tuned": tuned,
+            "kernel_ms": {k: round(v[0] / args.steps, 4) for k, v in prof.items() if v[1]}}
 
 
 def run_triples_case(args) -> dict:
@@ -922,22 +928,29 @@ def run_triples_case(args) -> dict:
     out = {"case": f"{w.name}: E(T) fused to a scalar, tiles {to}/{tv}", "n_triples": info["n_triples"],
            "gemm_flops": info["gemm_flops"], "n_batches": info["n_batches"]}
     energies = {}
-    # split precision: the tile policy (output columns per work item) picked by timing, like the autotuner
-    pol_ms = {}
+    # split precision: tile policy (output columns per work item), grid kind and scaling picked by timing,
+    # like the autotuner (all give the same arithmetic per output element except the scaling, whose error
+    # is reported below against FP64)
+    cfg_ms = {}
     for policy in (1, 3):
-        ctx.set_option(tg.TAMM_OPT_OZAKI_TILE_POLICY, policy)
-        for _ in range(2):
-            ctx.triples_energy(*ins, deo.data_ptr(), dev.data_ptr(), out_e.data_ptr(), "ozaki_bf16", SLICES)
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        ctx.triples_energy(*ins, deo.data_ptr(), dev.data_ptr(), out_e.data_ptr(), "ozaki_bf16", SLICES)
-        b.record(stream)
-        torch.cuda.synchronize()
-        pol_ms[policy] = a.elapsed_time(b)
-    best = min(pol_ms, key=pol_ms.get)
-    ctx.set_option(tg.TAMM_OPT_OZAKI_TILE_POLICY, best)
-    out["split_tile_policy_ms"] = {str(k): round(v, 3) for k, v in pol_ms.items()}
-    out["split_tile_policy"] = best
+        for persistent in (0, 1):
+            for shared in (0, 1):
+                ctx.set_option(tg.TAMM_OPT_OZAKI_TILE_POLICY, policy)
+                ctx.set_option(tg.TAMM_OPT_OZAKI_PERSISTENT, persistent)
+                ctx.set_option(tg.TAMM_OPT_OZAKI_SHARED_SCALE, shared)
+                ctx.triples_energy(*ins, deo.data_ptr(), dev.data_ptr(), out_e.data_ptr(), "ozaki_bf16", SLICES)
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                ctx.triples_energy(*ins, deo.data_ptr(), dev.data_ptr(), out_e.data_ptr(), "ozaki_bf16", SLICES)
+                b.record(stream)
+                torch.cuda.synchronize()
+                cfg_ms[(policy, persistent, shared)] = a.elapsed_time(b)
+    best = min(cfg_ms, key=cfg_ms.get)
+    for opt, val in zip((tg.TAMM_OPT_OZAKI_TILE_POLICY, tg.TAMM_OPT_OZAKI_PERSISTENT, tg.TAMM_OPT_OZAKI_SHARED_SCALE),
+                        best):
+        ctx.set_option(opt, val)
+    out["split_config_ms"] = {f"policy{k[0]}_persistent{k[1]}_shared{k[2]}": round(v, 3) for k, v in cfg_ms.items()}
+    out["split_config"] = {"tile_policy": best[0], "persistent": best[1], "shared_scale": best[2]}
     for prec, reps in (("ozaki_bf16", max(1, args.steps)), ("f64", 1)):
         run = lambda: ctx.triples_energy(*ins, deo.data_ptr(), dev.data_ptr(), out_e.data_ptr(), prec,
                                          SLICES if prec == "ozaki_bf16" else 0)
