@@ -1060,6 +1060,59 @@ def run_residual_case(args) -> dict:
     return out
 
 
+def run_gradients_case(args) -> dict:
+    """Differentiation (O=32 V=192, tiles 16/32): E = 1/4 V_oovv(ijab) T'(abij), T' = T + 1/2 V_vvvv(abef) T(efij),
+    forward and backward through torch.autograd (the hand-written adjoint: two adjoint contractions and two
+    scaled permuted adds), split precision (6 slices), BF16x3 and FP64, storing T' or recomputing it.  Each
+    pass ends with the library's status check.  Throughput counts the three contractions (forward ladder and
+    the two adjoint GEMMs, 2 M N K over stored block pairs)."""
+    import torch
+
+    import paper_2201_01257_gb300 as tg
+    from paper_2201_01257_gb300 import autograd as ga
+    from paper_2201_01257_gb300 import workload as gw
+    from tamm_synth import workloads as wl
+
+    w = wl.ladder_energy_o32_v192()
+    ctx = tg.Context(0)
+    _, T = gw.build(ctx, w)
+    run = gw.Runner(ctx, w, _, T)
+    ladder = next(st for st in w.steps if st.name == "ladder")
+    flops = 3 * run.flops(ladder)  # forward ladder + dT and dV_vvvv adjoints (same block pairs)
+    stream = torch.cuda.current_stream()
+    out = {"case": f"{w.name}: E and dE/dT, dE/dV_vvvv, dE/dV_oovv through torch.autograd",
+           "contraction_flops_per_pass": flops}
+    grads = {}
+    for prec, slices, recompute, reps in (("ozaki_bf16", SLICES, False, max(1, args.steps)),
+                                         ("ozaki_bf16", SLICES, True, max(1, args.steps)),
+                                         ("bf16x3", 0, False, max(1, args.steps)), ("f64", 0, False, 1)):
+        def step():
+            v = T["V_vvvv"].data.detach().requires_grad_(True)
+            t = T["T"].data.detach().requires_grad_(True)
+            voo = T["V_oovv"].data.detach().requires_grad_(True)
+            E = ga.ladder_energy(ctx, T["V_vvvv"], v, T["T"], t, T["V_oovv"], voo, prec, slices, recompute)
+            E.backward()
+            return E, v, t, voo
+        step()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            E, v, t, voo = step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        key = f"{prec}{'_recompute' if recompute else ''}"
+        out[f"{key}_ms"] = round(ms, 3)
+        out[f"{key}_TFLOP/s"] = round(flops / ms / 1e9, 3)
+        grads[key] = {"E": float(E.item()), "T": t.grad.detach().cpu().numpy(), "V": v.grad.detach().cpu().numpy()}
+    ref = grads["f64"]
+    rel = lambda a, b: float(np.linalg.norm(a - b) / np.linalg.norm(b))
+    out["rel_err_vs_f64"] = {k: {"E": abs(g["E"] - ref["E"]) / abs(ref["E"]), "dT": rel(g["T"], ref["T"]),
+                                 "dV_vvvv": rel(g["V"], ref["V"])} for k, g in grads.items() if k != "f64"}
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -1080,6 +1133,8 @@ def main():
     ap.add_argument("--cholesky", action="store_true",
                     help="time the ladder with V_vvvv formed on the fly from Cholesky vectors instead")
     ap.add_argument("--slab-gb", type=float, default=0.0, help="with --cholesky: slab buffer bound (0 = default)")
+    ap.add_argument("--gradients", action="store_true",
+                    help="time the O=32 V=192 ladder-energy forward + backward through autograd instead")
     ap.add_argument("--residual", nargs="?", const="40,240,20,40", default="",
                     help="O,V,to,tv: time one full CCSD residual, sequential vs scheduled vs graph, instead")
     ap.add_argument("--triples", nargs="?", const="32,160,16,80", default="",
@@ -1105,6 +1160,8 @@ def main():
         out = run_triples_case(args)
     elif args.residual:
         out = run_residual_case(args)
+    elif args.gradients:
+        out = run_gradients_case(args)
     elif args.impl == "reference":
         out = run_reference(args, rank)
     else:

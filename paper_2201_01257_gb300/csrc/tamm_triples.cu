@@ -44,7 +44,7 @@ struct TriplesItem {
   int32_t occ_tsz[3];  // their tile sizes
   int32_t occ[3];      // i, j, k (orbital energies)
   int32_t vlo[3], vn[3];  // offsets and sizes of ta, tb, tc
-  int32_t pad;
+  int32_t a_begin, a_end;  // the item's range of a inside ta (a tile triple is split so CTAs carry similar work)
 };
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -79,13 +79,13 @@ __global__ void __launch_bounds__(256) triples_energy_kernel(const double* __res
   const double* U1 = U + it.u_off[0];
   const double* U2 = U + it.u_off[1];
   const double* U3 = U + it.u_off[2];
-  const int nquad = (na + 3) / 4;
+  const int q0 = it.a_begin / 4, nquad = (it.a_end + 3) / 4 - q0;
   // the single occupied orbital of pair P ((ij) -> k, (ik) -> j, (jk) -> i) and the pair's sign
   constexpr int kSingle[3] = {2, 1, 0};
   constexpr double kSign[3] = {1.0, -1.0, 1.0};
   double acc = 0.0;
   for (int u = threadIdx.x; u < nquad * nc; u += blockDim.x) {
-    const int cl = u % nc, q = u / nc;
+    const int cl = u % nc, q = q0 + u / nc;
     const int c = c0 + cl;
     const double e_c = e_occ - eps_v[c];
     double tc[3];  // sign_P * T1[c, single(P)]           (term  v_P[a,b] t1[c])
@@ -95,7 +95,7 @@ __global__ void __launch_bounds__(256) triples_energy_kernel(const double* __res
       const int64_t off = it.t1_off[2 * 3 + o];
       tc[P] = off >= 0 ? kSign[P] * t1[off + (int64_t)cl * it.occ_tsz[o] + it.occ_loc[o]] : 0.0;
     }
-    for (int al = 4 * q; al < min(na, 4 * q + 4); ++al) {
+    for (int al = 4 * q; al < min(it.a_end, 4 * q + 4); ++al) {
       const int a = a0 + al;
       if (a >= c) break;
       const double e_ac = e_c - eps_v[a];
@@ -161,6 +161,8 @@ namespace {
 struct Occ {
   int32_t tile, loc;
 };
+
+constexpr int32_t kEnergyRows = 8;  // values of a per fused energy work item
 
 // Spin-allowed output blocks (tx,ty,tz) of U for one total spin of the occupied triple, packed.
 struct BlockTable {
@@ -431,7 +433,12 @@ struct TriplesPlan : Plan {
                 it.vlo[v] = (int32_t)V->off[(size_t)vt[v]];
                 it.vn[v] = (int32_t)V->size[(size_t)vt[v]];
               }
-              items.push_back(it);
+              // a ranges of kEnergyRows (a multiple of 4: whole sectors of U[b,c,a])
+              for (int32_t a0 = 0; a0 < it.vn[0]; a0 += kEnergyRows) {
+                it.a_begin = a0;
+                it.a_end = std::min<int32_t>(it.vn[0], a0 + kEnergyRows);
+                items.push_back(it);
+              }
             }
       }
       eitem_begin.push_back((int64_t)items.size());
