@@ -256,6 +256,28 @@ def run_ours(args, rank: int, world: int) -> dict | None:
             res["split_TFLOP/s" if prec == "oz" else "f64_TFLOP/s"] = round(res["nonzero_block_flops"] / t / 1e9, 3)
         per_contraction[st.name] = res
 
+    # --- the two transposed permuted adds of the step alone (tiled through shared memory): GB/s ---
+    add_bw = {}
+    ring = next(st for st in w.steps if st.name == "ring")
+    X, lx = run.scratch_for(ring)
+    from paper_2201_01257_gb300 import workload as gw_
+
+    for name, fn, nbytes in (
+            ("ring_antisymmetriser", lambda: ctx.add(T["R"], "abij", 1.0, X, gw_.antisym_terms("abij", lx)),
+             T["R"].n_elems * 8 * (4 + 2)),  # four source terms read, R read and written
+            ("transposition_ij", lambda: ctx.add(T["R"], "abij", 1.0, X, [(1.0, gw_.antisym_terms("abij", lx)[2][1])]),
+             T["R"].n_elems * 8 * (1 + 2))):
+        fn()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(5):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        t_ms = a.elapsed_time(b) / 5
+        add_bw[name] = {"ms": round(t_ms, 4), "GB/s": round(nbytes / (t_ms * 1e-3) / 1e9, 1),
+                        "frac_of_hbm": round(nbytes / (t_ms * 1e-3) / 1e9 / measured_peaks()["hbm_gbs"], 3)}
+
     # --- end to end through the C ABI: pinned host inputs in, result out, every step ---
     # Every step copies all of its inputs from pinned host memory and reads R and the energy back.
     # Pipelined (the reported figure): the inputs of step k+1 are copied, on a second stream through
@@ -396,6 +418,7 @@ def run_ours(args, rank: int, world: int) -> dict | None:
                 "frac_of_measured_peak": round(job_throughput(world, flops, ms_f64) / max(fp64_peak.values()), 4)},
         "speedup_vs_f64": round(ms_f64 / ms, 2),
         "per_contraction": per_contraction,
+        "permuted_adds": add_bw,
         "rel_err_vs_f64": {"R": rel(r_oz, r_64), "W": rel(w_oz, w_64), "energy": abs(e_oz - e_64) / abs(e_64)},
         "e2e": {"value": round(job_throughput(world, flops, ms_e2e), 3), "unit": UNIT,
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": round(ms_e2e, 3),

@@ -40,7 +40,15 @@ __device__ __forceinline__ void digits_step(const AddBlock& B, Digits& d) {
   }
 }
 
-// dst = beta*dst + sum_t alpha_t * src(perm_t), one chunk of one block per CTA.
+// First term of a sum: alpha * v without an FP64 multiply when alpha is +-1 (GB300's FP64 pipe is narrow;
+// a copy then moves bits only), then the further terms by fused multiply-adds.
+__device__ __forceinline__ double term0(double alpha, double v) {
+  return alpha == 1.0 ? v : (alpha == -1.0 ? -v : alpha * v);
+}
+
+// dst = beta*dst + sum_t alpha_t * src(perm_t), one chunk of one block per CTA (any layout: each source
+// term is read through its strides).  NM: modes of the block.
+template <int NM>
 __global__ void __launch_bounds__(256) add_kernel(double* __restrict__ dst, const double* __restrict__ src,
                                                   const AddBlock* __restrict__ blocks,
                                                   const ChunkItem* __restrict__ items, int n_terms, double beta,
@@ -52,20 +60,89 @@ __global__ void __launch_bounds__(256) add_kernel(double* __restrict__ dst, cons
   }
   const AddBlock& B = blocks[it.block];
   const int64_t end = min(B.n, it.start + (int64_t)kChunk);
-  const int nm = B.nm;
   Digits dg;
   digits_init(B, (int32_t)(it.start + threadIdx.x), (int32_t)blockDim.x, dg);
   for (int64_t e = it.start + threadIdx.x; e < end; e += blockDim.x, digits_step(B, dg)) {
-    const int32_t* idx = dg.idx;
     double acc = 0.0;
+    bool any = false;
     for (int t = 0; t < n_terms; ++t) {
       if (B.src_off[t] < 0) continue;
       int64_t s = B.src_off[t];
-      for (int m = 0; m < nm; ++m) s += (int64_t)idx[m] * B.sstride[t][m];
-      acc = fma(alpha.v[t], src[s], acc);
+#pragma unroll
+      for (int m = 0; m < NM; ++m) s += (int64_t)dg.idx[m] * B.sstride[t][m];
+      const double v = src[s];
+      acc = any ? fma(alpha.v[t], v, acc) : term0(alpha.v[t], v);
+      any = true;
     }
     double* d = dst + B.dst_off + e;
-    *d = beta != 0.0 ? fma(beta, *d, acc) : acc;
+    *d = beta != 0.0 ? *d + acc : acc;  // beta is 0 or 1
+  }
+}
+
+// The same sum for a block whose source terms read the destination's last mode q with a stride (a
+// transposition): the work item is a TP x TQ tile of the plane of q and the block's "row" mode p (the
+// mode every transposed term reads contiguously), for a run of indices of the other modes.  The
+// transposed terms are staged through shared memory with reads that run along p (coalesced), and the
+// destination and the untransposed terms are then read and written along q (coalesced).
+__global__ void __launch_bounds__(256) add_tiled_kernel(double* __restrict__ dst, const double* __restrict__ src,
+                                                        const AddBlock* __restrict__ blocks,
+                                                        const TileItem* __restrict__ items, int n_terms, double beta,
+                                                        Alpha4 alpha, const double* __restrict__ scale) {
+  __shared__ double tile[kMaxAddTerms][kAddTile][kAddTile + 1];
+  const TileItem it = items[blockIdx.x];
+  if (scale) {
+    const double sc = *scale;
+    for (int t = 0; t < n_terms; ++t) alpha.v[t] *= sc;
+  }
+  const AddBlock& B = blocks[it.block];
+  const int nm = B.nm, p = B.tmode, q = nm - 1;
+  const int TP = min(kAddTile, B.dim[p] - it.p0), TQ = min(kAddTile, B.dim[q] - it.q0);
+  int64_t dstr[kMaxKernelModes];
+  {
+    int64_t st = 1;
+    for (int m = nm - 1; m >= 0; --m) {
+      dstr[m] = st;
+      st *= B.dim[m];
+    }
+  }
+  bool trans[kMaxAddTerms];
+  for (int t = 0; t < kMaxAddTerms; ++t) trans[t] = t < n_terms && B.src_off[t] >= 0 && B.sstride[t][q] != 1;
+  for (int o = it.o0; o < it.o0 + it.n_o; ++o) {
+    // indices of the modes other than p and q, row-major over them
+    int64_t dbase = B.dst_off + (int64_t)it.p0 * dstr[p] + it.q0;
+    int64_t sbase[kMaxAddTerms];
+    for (int t = 0; t < n_terms; ++t)
+      sbase[t] = B.src_off[t] + (int64_t)it.p0 * B.sstride[t][p] + (int64_t)it.q0 * B.sstride[t][q];
+    int r = o;
+    for (int m = nm - 1; m >= 0; --m) {
+      if (m == p || m == q) continue;
+      const int x = r % B.dim[m];
+      r /= B.dim[m];
+      dbase += x * dstr[m];
+      for (int t = 0; t < n_terms; ++t) sbase[t] += (int64_t)x * B.sstride[t][m];
+    }
+    for (int t = 0; t < n_terms; ++t) {
+      if (!trans[t]) continue;
+      for (int u = threadIdx.x; u < TP * TQ; u += blockDim.x) {
+        const int pl = u % TP, ql = u / TP;  // along p: consecutive source addresses
+        tile[t][pl][ql] = src[sbase[t] + pl + (int64_t)ql * B.sstride[t][q]];
+      }
+    }
+    __syncthreads();
+    for (int u = threadIdx.x; u < TP * TQ; u += blockDim.x) {
+      const int ql = u % TQ, pl = u / TQ;  // along q: consecutive destination addresses
+      double acc = 0.0;
+      bool any = false;
+      for (int t = 0; t < n_terms; ++t) {
+        if (B.src_off[t] < 0) continue;
+        const double v = trans[t] ? tile[t][pl][ql] : src[sbase[t] + (int64_t)pl * B.sstride[t][p] + ql];
+        acc = any ? fma(alpha.v[t], v, acc) : term0(alpha.v[t], v);
+        any = true;
+      }
+      double* d = dst + dbase + (int64_t)pl * dstr[p] + ql;
+      *d = beta != 0.0 ? *d + acc : acc;
+    }
+    __syncthreads();
   }
 }
 
@@ -257,13 +334,30 @@ __global__ void __launch_bounds__(256) gemm_f64_kernel(const double* __restrict_
 
 cudaError_t launch_add(tamm_ctx* ctx, double* dst, const double* src, const AddBlock* blocks,
                        const ChunkItem* items, int64_t n_items, int n_terms, double beta, const double* alpha_host,
-                       const double* scale_device) {
-  if (n_items == 0) return cudaSuccess;
+                       const double* scale_device, int nm, const TileItem* tiles, int64_t n_tiles) {
+  if (n_items == 0 && n_tiles == 0) return cudaSuccess;
   Alpha4 al{};
   for (int t = 0; t < n_terms; ++t) al.v[t] = alpha_host[t];
-  kernel_begin(ctx, TAMM_KERNEL_ADD);
-  add_kernel<<<(unsigned)n_items, 256, 0, ctx->stream>>>(dst, src, blocks, items, n_terms, beta, al, scale_device);
-  kernel_end(ctx, TAMM_KERNEL_ADD);
+  if (n_items > 0) {
+    kernel_begin(ctx, TAMM_KERNEL_ADD);
+    switch (nm) {
+      case 1: add_kernel<1><<<(unsigned)n_items, 256, 0, ctx->stream>>>(dst, src, blocks, items, n_terms, beta, al,
+                                                                        scale_device); break;
+      case 2: add_kernel<2><<<(unsigned)n_items, 256, 0, ctx->stream>>>(dst, src, blocks, items, n_terms, beta, al,
+                                                                        scale_device); break;
+      case 3: add_kernel<3><<<(unsigned)n_items, 256, 0, ctx->stream>>>(dst, src, blocks, items, n_terms, beta, al,
+                                                                        scale_device); break;
+      default: add_kernel<4><<<(unsigned)n_items, 256, 0, ctx->stream>>>(dst, src, blocks, items, n_terms, beta, al,
+                                                                         scale_device); break;
+    }
+    kernel_end(ctx, TAMM_KERNEL_ADD);
+  }
+  if (n_tiles > 0) {
+    kernel_begin(ctx, TAMM_KERNEL_ADD);
+    add_tiled_kernel<<<(unsigned)n_tiles, 256, 0, ctx->stream>>>(dst, src, blocks, tiles, n_terms, beta, al,
+                                                                  scale_device);
+    kernel_end(ctx, TAMM_KERNEL_ADD);
+  }
   return cudaGetLastError();
 }
 

@@ -25,6 +25,9 @@ struct AddPlan : Plan {
   AddBlock* d_blocks = nullptr;
   ChunkItem* d_items = nullptr;
   int64_t n_items = 0;
+  TileItem* d_tiles = nullptr;  // blocks on the transposition path
+  int64_t n_tiles = 0;
+  int nm = kMaxKernelModes;
   int n_terms = 1;
   AddPlan(tamm_ctx* c, const tamm_tensor& D, const char* ld, const tamm_tensor& S, int terms, const char* const* ls);
   void run(double* dst, const double* src, double beta, const double* alpha,

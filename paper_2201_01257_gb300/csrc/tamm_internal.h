@@ -33,6 +33,18 @@ struct AddBlock {
   int32_t dim[kMaxKernelModes];
   int64_t src_off[kMaxAddTerms];
   int32_t sstride[kMaxAddTerms][kMaxKernelModes];
+  int32_t tmode;  // mode that every term reading the last mode with a stride reads contiguously (tiled
+                  // transposition path), or -1
+};
+
+// A tile of a transposed permuted add: rows [p0, p0 + kAddTile) of the block's mode tmode, columns
+// [q0, q0 + kAddTile) of its last mode, for the indices o0 .. o0 + n_o - 1 of its other modes (row-major).
+constexpr int kAddTile = 32;
+struct TileItem {
+  int32_t block;
+  int32_t p0, q0;
+  int32_t o0, n_o;
+  int32_t pad;
 };
 
 // One block of the Cholesky pair difference V[p,q,r,s] = X1[p,r,q,s] - X1[p,s,q,r]: V's block (tiles
@@ -209,9 +221,11 @@ void* ctx_scratch(tamm_ctx* ctx, size_t bytes);  // valid until the next ctx_scr
 
 // ------------------------------------------------------------ kernel launch
 // Implemented in kernels_f64.cu.  All launch on ctx->stream; return cudaError_t.
+// Chunked items (any layout; nm = the blocks' mode count) and tiled items (blocks with tmode >= 0).
 cudaError_t launch_add(tamm_ctx* ctx, double* dst, const double* src, const AddBlock* blocks,
                        const ChunkItem* items, int64_t n_items, int n_terms, double beta, const double* alpha_host,
-                       const double* scale_device = nullptr);
+                       const double* scale_device = nullptr, int nm = kMaxKernelModes,
+                       const TileItem* tiles = nullptr, int64_t n_tiles = 0);
 // V = X1(p,r,q,s) - X1(p,s,q,r) over the listed blocks; `smem_bytes` = 8 * max ns * (nr + 1), at most
 // kPairSmemMax (the default dynamic shared memory limit, so no attribute call is needed).
 constexpr size_t kPairSmemMax = 48 * 1024;

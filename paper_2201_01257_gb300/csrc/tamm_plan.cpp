@@ -85,6 +85,20 @@ std::vector<AddBlock> build_add_blocks(const tamm_tensor& D, const char* ld, con
       ab.src_off[t] = S.off[(size_t)sb];
       for (int m = 0; m < D.nm; ++m) ab.sstride[t][m] = (int32_t)stride[posS[t][m]];
     }
+    // transposition: the terms that read the last destination mode with a stride must all read one
+    // other destination mode contiguously, which then becomes the tile's row mode
+    ab.tmode = -1;
+    bool ok = D.nm >= 2 && ab.dim[D.nm - 1] > 1;
+    int tm = -1;
+    for (int t = 0; t < n_terms && ok; ++t) {
+      if (ab.src_off[t] < 0 || ab.sstride[t][D.nm - 1] == 1) continue;
+      int p = -1;
+      for (int m = 0; m < D.nm - 1; ++m)
+        if (ab.sstride[t][m] == 1 && ab.dim[m] > 1) p = m;
+      if (p < 0 || (tm >= 0 && p != tm)) ok = false;
+      tm = p;
+    }
+    if (ok && tm >= 0) ab.tmode = tm;
   }
   return out;
 }
@@ -96,19 +110,48 @@ std::vector<ChunkItem> build_chunks(const std::vector<AddBlock>& blocks) {
   return items;
 }
 
+// Tiles of the blocks that take the transposition path; the other blocks get chunks.
+static void build_add_items(const std::vector<AddBlock>& blocks, std::vector<ChunkItem>& chunks,
+                            std::vector<TileItem>& tiles) {
+  for (size_t b = 0; b < blocks.size(); ++b) {
+    const AddBlock& B = blocks[b];
+    if (B.tmode < 0) {
+      for (int64_t s = 0; s < B.n; s += kChunk) chunks.push_back({(int32_t)b, 0, s});
+      continue;
+    }
+    const int p = B.tmode, q = B.nm - 1;
+    int64_t outer = 1;
+    for (int m = 0; m < B.nm; ++m)
+      if (m != p && m != q) outer *= B.dim[m];
+    for (int32_t p0 = 0; p0 < B.dim[p]; p0 += kAddTile)
+      for (int32_t q0 = 0; q0 < B.dim[q]; q0 += kAddTile) {
+        const int64_t tp = std::min<int64_t>(kAddTile, B.dim[p] - p0), tq = std::min<int64_t>(kAddTile, B.dim[q] - q0);
+        const int32_t per = (int32_t)std::max<int64_t>(1, 4096 / (tp * tq));  // about 4096 elements per item
+        for (int64_t o = 0; o < outer; o += per)
+          tiles.push_back({(int32_t)b, p0, q0, (int32_t)o, (int32_t)std::min<int64_t>(per, outer - o), 0});
+      }
+  }
+}
+
 AddPlan::AddPlan(tamm_ctx* c, const tamm_tensor& D, const char* ld, const tamm_tensor& S, int terms,
                  const char* const* ls)
     : Plan(c), n_terms(terms) {
   auto blocks = build_add_blocks(D, ld, S, terms, ls);
-  auto items = build_chunks(blocks);
+  std::vector<ChunkItem> items;
+  std::vector<TileItem> tiles;
+  build_add_items(blocks, items, tiles);
   n_items = (int64_t)items.size();
+  n_tiles = (int64_t)tiles.size();
+  nm = D.nm;
+  if (n_tiles) d_tiles = upload(tiles);
   d_blocks = upload(blocks);
   d_items = upload(items);
 }
 
 void AddPlan::run(double* dst, const double* src, double beta, const double* alpha,
                   const double* scale_device) const {
-  cuda_check(launch_add(ctx, dst, src, d_blocks, d_items, n_items, n_terms, beta, alpha, scale_device),
+  cuda_check(launch_add(ctx, dst, src, d_blocks, d_items, n_items, n_terms, beta, alpha, scale_device, nm, d_tiles,
+                        n_tiles),
              "add kernel");
 }
 
