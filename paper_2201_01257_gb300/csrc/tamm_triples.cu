@@ -52,88 +52,147 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
-// 1/d for d < 0 of moderate size: an FP32 reciprocal refined by one Newton step in FP64, relative
-// error about 2^-47 (the FP32 seed is good to 2^-23 and the step squares the error); two FP64
-// operations instead of an IEEE division, whose cost the narrow FP64 pipe of this chip makes large.
-__device__ __forceinline__ double recip_newton(double d) {
-  const double r0 = (double)__frcp_rn(__double2float_rn(d));
-  return fma(r0, fma(-d, r0, 1.0), r0);
+// ---- double-float arithmetic: a value is hi + lo, two FP32 numbers with |lo| <= ulp(hi) / 2, about 48
+// significant bits.  GB300 issues FP32 operations at 64 times its FP64 rate, so the fused energy
+// evaluates W, Y, the denominator and (W + Y) W / D in this form.  Error-free transformations
+// (Knuth's TwoSum, Dekker's FastTwoSum, the FMA product error) with explicitly rounded operations, so
+// that no multiply-add contraction changes them.
+struct df {
+  float hi, lo;
+};
+
+__device__ __forceinline__ df two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b), bb = __fsub_rn(s, a);
+  return {s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
+}
+__device__ __forceinline__ df fast_two_sum(float a, float b) {  // |a| >= |b| (or a == 0)
+  const float s = __fadd_rn(a, b);
+  return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ df df_add(df x, df y) {
+  const df s = two_sum(x.hi, y.hi);
+  return fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(x.lo, y.lo)));
+}
+__device__ __forceinline__ df df_neg(df x) { return {-x.hi, -x.lo}; }
+__device__ __forceinline__ df df_mul(df x, df y) {
+  const float p = __fmul_rn(x.hi, y.hi);
+  float e = __fmaf_rn(x.hi, y.hi, -p);
+  e = __fmaf_rn(x.hi, y.lo, e);
+  e = __fmaf_rn(x.lo, y.hi, e);
+  return fast_two_sum(p, e);
+}
+// x / d: quotient of the leading parts, then one correction from the double-float residual x - q d.
+__device__ __forceinline__ df df_div(df x, df d) {
+  const float r = __frcp_rn(d.hi);
+  const float q1 = __fmul_rn(x.hi, r);
+  const df res = df_add(x, df_neg(df_mul({q1, 0.0f}, d)));
+  const float q2 = __fmul_rn(res.hi, r);
+  return fast_two_sum(q1, q2);
+}
+// A double split into hi (its leading 24 bits, truncated) and lo (the rest, rounded to 24 bits), built from
+// the bit pattern with integer operations (no FP64 instruction).  Magnitudes below 2^-74 read as zero;
+// the inputs here are amplitudes, integrals and orbital energies, far inside the range.
+__device__ __forceinline__ df df_from(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const int E = (int)((b >> 52) & 0x7FF) - 1023;
+  if (E < -74) return {0.0f, 0.0f};
+  const uint32_t sign = (uint32_t)(b >> 63) << 31;
+  const unsigned long long m = b & ((1ull << 52) - 1);
+  const float hi = __uint_as_float(sign | (uint32_t)(E + 127) << 23 | (uint32_t)(m >> 29));
+  const float rem = __uint2float_rn((uint32_t)(m & ((1u << 29) - 1)));  // the low 29 mantissa bits
+  const float lo = __fmul_rn(rem, __uint_as_float((uint32_t)(E - 52 + 127) << 23));
+  return {hi, sign ? -lo : lo};
+}
+
+// Double-float copies of the fused kernel's small inputs (V_oovv, T1, orbital energies).
+__global__ void to_df_kernel(const double* __restrict__ x, int64_t n, float2* __restrict__ out) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const df v = df_from(x[i]);
+    out[i] = make_float2(v.hi, v.lo);
+  }
+}
+
+__device__ __forceinline__ df ld(const float2* p, int64_t i) {
+  const float2 v = p[i];
+  return {v.x, v.y};
 }
 
 // One item per CTA.  A thread owns four consecutive a (one 32-byte sector of U[b,c,a]) and one c and
 // walks b, so U[a,b,c] is read coalesced across the warp (consecutive c), U[a,c,b] along one row per
-// thread and U[b,c,a] in whole sectors.  Y of Eq. tensort2 is nine fused multiply-adds: each T1 factor
-// carries its pair's sign (pairs (ij)k, (ik)j, (jk)i: +, -, +) and the virtual split's (ab|c +, ac|b -,
-// bc|a +).  FP64 throughout; the CTA's sum goes to partials[blockIdx.x].
+// thread and U[b,c,a] in whole sectors.  Y of Eq. tensort2 is nine products: each T1 factor carries
+// its pair's sign (pairs (ij)k, (ik)j, (jk)i: +, -, +) and the virtual split's (ab|c +, ac|b -, bc|a +).
+// Double-float arithmetic; the CTA's sum goes to partials[blockIdx.x] in FP64.
 __global__ void __launch_bounds__(256) triples_energy_kernel(const double* __restrict__ U,
                                                              const TriplesItem* __restrict__ items,
-                                                             const double* __restrict__ voo,
-                                                             const double* __restrict__ t1,
-                                                             const double* __restrict__ eps_o,
-                                                             const double* __restrict__ eps_v,
+                                                             const float2* __restrict__ voo,
+                                                             const float2* __restrict__ t1,
+                                                             const float2* __restrict__ eps_o,
+                                                             const float2* __restrict__ eps_v,
                                                              double* __restrict__ partials) {
   const TriplesItem& it = items[blockIdx.x];
   const int na = it.vn[0], nb = it.vn[1], nc = it.vn[2];
   const int a0 = it.vlo[0], b0 = it.vlo[1], c0 = it.vlo[2];
-  const double e_occ = eps_o[it.occ[0]] + eps_o[it.occ[1]] + eps_o[it.occ[2]];
+  const df e_occ = df_add(df_add(ld(eps_o, it.occ[0]), ld(eps_o, it.occ[1])), ld(eps_o, it.occ[2]));
   const double* U1 = U + it.u_off[0];
   const double* U2 = U + it.u_off[1];
   const double* U3 = U + it.u_off[2];
   const int q0 = it.a_begin / 4, nquad = (it.a_end + 3) / 4 - q0;
   // the single occupied orbital of pair P ((ij) -> k, (ik) -> j, (jk) -> i) and the pair's sign
   constexpr int kSingle[3] = {2, 1, 0};
-  constexpr double kSign[3] = {1.0, -1.0, 1.0};
-  double acc = 0.0;
+  constexpr float kSign[3] = {1.0f, -1.0f, 1.0f};
+  auto t1s = [&](int v, int P, int l) -> df {  // sign_P * T1[virtual v (local index l), single(P)]
+    const int o = kSingle[P];
+    const int64_t off = it.t1_off[v * 3 + o];
+    if (off < 0) return {0.0f, 0.0f};
+    const df x = ld(t1, off + (int64_t)l * it.occ_tsz[o] + it.occ_loc[o]);
+    return {kSign[P] * x.hi, kSign[P] * x.lo};
+  };
+  df acc = {0.0f, 0.0f};
   for (int u = threadIdx.x; u < nquad * nc; u += blockDim.x) {
     const int cl = u % nc, q = q0 + u / nc;
     const int c = c0 + cl;
-    const double e_c = e_occ - eps_v[c];
-    double tc[3];  // sign_P * T1[c, single(P)]           (term  v_P[a,b] t1[c])
+    const df e_c = df_add(e_occ, df_neg(ld(eps_v, c)));
+    df tc[3];  // term v_P[a,b] t1[c]
 #pragma unroll
-    for (int P = 0; P < 3; ++P) {
-      const int o = kSingle[P];
-      const int64_t off = it.t1_off[2 * 3 + o];
-      tc[P] = off >= 0 ? kSign[P] * t1[off + (int64_t)cl * it.occ_tsz[o] + it.occ_loc[o]] : 0.0;
-    }
+    for (int P = 0; P < 3; ++P) tc[P] = t1s(2, P, cl);
     for (int al = 4 * q; al < min(it.a_end, 4 * q + 4); ++al) {
       const int a = a0 + al;
       if (a >= c) break;
-      const double e_ac = e_c - eps_v[a];
-      double ta[3], vac[3];  // sign_P * T1[a, single(P)] (term  v_P[b,c] t1[a]);  v_P[a,c]
+      const df e_ac = df_add(e_c, df_neg(ld(eps_v, a)));
+      df ta[3], vac[3];  // term v_P[b,c] t1[a];  v_P[a,c]
 #pragma unroll
       for (int P = 0; P < 3; ++P) {
-        const int o = kSingle[P];
-        const int64_t off = it.t1_off[0 * 3 + o];
-        ta[P] = off >= 0 ? kSign[P] * t1[off + (int64_t)al * it.occ_tsz[o] + it.occ_loc[o]] : 0.0;
+        ta[P] = t1s(0, P, al);
         const int64_t ov = it.voo_off[P * 3 + 1];
-        vac[P] = ov >= 0 ? voo[ov + ((int64_t)it.pair_pre[P] * na + al) * nc + cl] : 0.0;
+        vac[P] = ov >= 0 ? ld(voo, ov + ((int64_t)it.pair_pre[P] * na + al) * nc + cl) : df{0.0f, 0.0f};
       }
       for (int bl = 0; bl < nb; ++bl) {
         const int b = b0 + bl;
         if (b <= a) continue;
         if (b >= c) break;
-        const double w = U1[((int64_t)al * nb + bl) * nc + cl] - U2[((int64_t)al * nc + cl) * nb + bl] +
-                         U3[((int64_t)bl * nc + cl) * na + al];
-        double y = 0.0;
+        const df w = df_add(df_add(df_from(U1[((int64_t)al * nb + bl) * nc + cl]),
+                                   df_neg(df_from(U2[((int64_t)al * nc + cl) * nb + bl]))),
+                            df_from(U3[((int64_t)bl * nc + cl) * na + al]));
+        df y = {0.0f, 0.0f};
 #pragma unroll
         for (int P = 0; P < 3; ++P) {
-          const int o = kSingle[P];
-          const int64_t oab = it.voo_off[P * 3 + 0], obc = it.voo_off[P * 3 + 2], ot = it.t1_off[1 * 3 + o];
-          const double vab = oab >= 0 ? voo[oab + ((int64_t)it.pair_pre[P] * na + al) * nb + bl] : 0.0;
-          const double vbc = obc >= 0 ? voo[obc + ((int64_t)it.pair_pre[P] * nb + bl) * nc + cl] : 0.0;
-          const double tb = ot >= 0 ? kSign[P] * t1[ot + (int64_t)bl * it.occ_tsz[o] + it.occ_loc[o]] : 0.0;
-          y = fma(vab, tc[P], y);   // + v_P[a,b] t1[c]
-          y = fma(-vac[P], tb, y);  // - v_P[a,c] t1[b]
-          y = fma(vbc, ta[P], y);   // + v_P[b,c] t1[a]
+          const int64_t oab = it.voo_off[P * 3 + 0], obc = it.voo_off[P * 3 + 2];
+          const df vab = oab >= 0 ? ld(voo, oab + ((int64_t)it.pair_pre[P] * na + al) * nb + bl) : df{0.0f, 0.0f};
+          const df vbc = obc >= 0 ? ld(voo, obc + ((int64_t)it.pair_pre[P] * nb + bl) * nc + cl) : df{0.0f, 0.0f};
+          const df tb = t1s(1, P, bl);
+          y = df_add(y, df_mul(vab, tc[P]));           // + v_P[a,b] t1[c]
+          y = df_add(y, df_neg(df_mul(vac[P], tb)));   // - v_P[a,c] t1[b]
+          y = df_add(y, df_mul(vbc, ta[P]));           // + v_P[b,c] t1[a]
         }
-        const double d = e_ac - eps_v[b];  // e_i + e_j + e_k - e_a - e_b - e_c
-        acc = fma((w + y) * w, recip_newton(d), acc);
+        const df d = df_add(e_ac, df_neg(ld(eps_v, b)));  // e_i + e_j + e_k - e_a - e_b - e_c
+        acc = df_add(acc, df_div(df_mul(df_add(w, y), w), d));
       }
     }
   }
   __shared__ double red[8];
-  acc = warp_sum(acc);
-  if (threadIdx.x % 32 == 0) red[threadIdx.x / 32] = acc;
+  double v = (double)acc.hi + (double)acc.lo;
+  v = warp_sum(v);
+  if (threadIdx.x % 32 == 0) red[threadIdx.x / 32] = v;
   __syncthreads();
   if (threadIdx.x == 0) {
     double s = 0.0;
@@ -701,6 +760,15 @@ void run_triples(tamm_ctx* ctx, const tamm_tensor* T2, const tamm_tensor* T1, co
   const size_t ws_bytes = align((size_t)std::max<int64_t>(p->ws_elems, 1) * 8);
   const size_t part_bytes = align((size_t)std::max<int64_t>(p->n_eitems, 1) * 8);
   size_t total = ws_bytes + part_bytes;
+  // double-float copies of V_oovv, T1 and the orbital energies (8 bytes per element each)
+  const size_t off_dv = total;
+  total += align((size_t)std::max<int64_t>(Voo->n_elems, 1) * 8);
+  const size_t off_dt = total;
+  total += align((size_t)std::max<int64_t>(T1->n_elems, 1) * 8);
+  const size_t off_deo = total;
+  total += align((size_t)std::max<int64_t>(p->no, 1) * 8);
+  const size_t off_dev = total;
+  total += align((size_t)std::max<int64_t>(p->nv, 1) * 8);
   size_t off_a = 0, off_b = 0, off_ea = 0, off_eb = 0, off_sa = 0, off_sb = 0;
   if (precision == TAMM_PREC_OZAKI_BF16) {
     if (p->oz_shared) {
@@ -721,6 +789,14 @@ void run_triples(tamm_ctx* ctx, const tamm_tensor* T2, const tamm_tensor* T1, co
   char* scratch = (char*)ctx_scratch(ctx, total);
   double* U = (double*)scratch;
   double* partials = (double*)(scratch + ws_bytes);
+  float2* dvoo = (float2*)(scratch + off_dv);
+  float2* dt1 = (float2*)(scratch + off_dt);
+  float2* deo = (float2*)(scratch + off_deo);
+  float2* dev = (float2*)(scratch + off_dev);
+  cuda_check(launch_to_df(ctx, Voo->data, Voo->n_elems, dvoo), "triples double-float copy");
+  cuda_check(launch_to_df(ctx, T1->data, T1->n_elems, dt1), "triples double-float copy");
+  cuda_check(launch_to_df(ctx, eps_o, p->no, deo), "triples double-float copy");
+  cuda_check(launch_to_df(ctx, eps_v, p->nv, dev), "triples double-float copy");
   // GEMM-order copies of the inputs
   const double one = 1.0;
   p->copy_q->run(p->Tq->data, T2->data, 0.0, &one);
@@ -782,8 +858,7 @@ void run_triples(tamm_ctx* ctx, const tamm_tensor* T2, const tamm_tensor* T1, co
                  "triples gemm (split precision)");
     }
     const int64_t e0 = p->eitem_begin[(size_t)bch], e1 = p->eitem_begin[(size_t)bch + 1];
-    cuda_check(launch_triples_energy(ctx, U, p->d_eitems + e0, e1 - e0, Voo->data, T1->data, eps_o, eps_v,
-                                     partials + e0),
+    cuda_check(launch_triples_energy(ctx, U, p->d_eitems + e0, e1 - e0, dvoo, dt1, deo, dev, partials + e0),
                "triples energy");
   }
   cuda_check(launch_reduce_final(ctx, partials, p->n_eitems, 1.0, 0, energy), "triples reduction");
@@ -792,8 +867,17 @@ void run_triples(tamm_ctx* ctx, const tamm_tensor* T2, const tamm_tensor* T1, co
                "triples per-triple sums");
 }
 
+cudaError_t launch_to_df(tamm_ctx* ctx, const double* x, int64_t n, float2* out) {
+  if (n == 0) return cudaSuccess;
+  kernel_begin(ctx, TAMM_KERNEL_TRIPLES);
+  const int64_t blocks = std::min<int64_t>((n + 255) / 256, 8L * std::max(1, ctx->sm_count));
+  to_df_kernel<<<(unsigned)blocks, 256, 0, ctx->stream>>>(x, n, out);
+  kernel_end(ctx, TAMM_KERNEL_TRIPLES);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_triples_energy(tamm_ctx* ctx, const double* U, const void* items, int64_t n_items,
-                                  const double* voo, const double* t1, const double* eps_o, const double* eps_v,
+                                  const float2* voo, const float2* t1, const float2* eps_o, const float2* eps_v,
                                   double* partials) {
   if (n_items == 0) return cudaSuccess;
   kernel_begin(ctx, TAMM_KERNEL_TRIPLES);
