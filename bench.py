@@ -1136,6 +1136,137 @@ def run_gradients_case(args) -> dict:
     return out
 
 
+def _oracle_row(name: str) -> dict:
+    """One CPU-baseline row: the FP64 oracle, as it stands, on one workload (OMP_NUM_THREADS sets its cores)."""
+    import oracle as O
+    import tamm_synth
+    from tamm_synth import workloads as wl
+
+    def fill(w, T, names, blocks=None):
+        for n in names:
+            spec, X = w.tensors[n], T[n]
+            lo, ext = X.block_lo_ext()
+            idx = np.arange(X.n_blocks) if blocks is None or n not in blocks else np.array(sorted(blocks[n]))
+            if len(idx):
+                tamm_synth.fill_boxes(w.seed, spec.stream, spec.sigma, X.dense_shape(), spec.anti01, spec.anti23,
+                                      lo[idx], ext[idx], X.block_off[idx], X.data)
+
+    def tensors(w, names):
+        sp = {k: O.Space.from_spec(v) for k, v in w.spaces.items()}
+        return {n: O.Tensor([sp[m] for m in w.tensors[n].modes], w.tensors[n].n_upper, w.tensors[n].sym)
+                for n in names}
+
+    if name == "ladder_O8_V32":  # configuration 1, in full
+        w = wl.ladder_o8_v32()
+        T = tensors(w, ("V_vvvv", "T", "R"))
+        fill(w, T, ("V_vvvv", "T"))
+        t0 = time.perf_counter()
+        O.contract(0.5, T["R"], "abij", 0.0, T["V_vvvv"], "abef", T["T"], "efij")
+        return {"seconds": time.perf_counter() - t0, "flops": 2.097152e7}
+    if name == "oooo_O40_V240":  # the configuration-2 oooo ladder, in full
+        w = wl.ccsd_doubles_o40_v240()
+        T = tensors(w, ("T", "W0", "R"))
+        fill(w, T, ("T", "W0"))
+        t0 = time.perf_counter()
+        O.contract(0.25, T["R"], "abij", 0.0, T["T"], "abmn", T["W0"], "mnij")
+        return {"seconds": time.perf_counter() - t0, "flops": 4.608e10}
+    if name == "gradients_O32_V192":  # configuration 4: forward and the closed-form reference gradient
+        w = wl.ladder_energy_o32_v192()
+        T = tensors(w, ("V_vvvv", "T", "V_oovv"))
+        fill(w, T, ("V_vvvv", "T", "V_oovv"))
+        t0 = time.perf_counter()
+        Tp = O.Tensor(T["T"].modes, 2)
+        Tp.data[:] = T["T"].data
+        O.contract(0.5, Tp, "abij", 1.0, T["V_vvvv"], "abef", T["T"], "efij")
+        O.energy(0.25, T["V_oovv"], "ijab", Tp, "abij")
+        G = O.Tensor(T["T"].modes, 2)
+        O.add(0.25, G, "abij", 0.0, T["V_oovv"], "ijab")
+        dT = O.Tensor(T["T"].modes, 2)
+        dT.data[:] = G.data
+        O.contract(0.5, dT, "efij", 1.0, T["V_vvvv"], "abef", G, "abij")
+        dV = O.Tensor(T["V_vvvv"].modes, 2)
+        O.contract(0.5, dV, "abef", 0.0, G, "abij", T["T"], "efij")
+        return {"seconds": time.perf_counter() - t0, "flops": 3 * 4.349e11}
+    if name == "doubles_O80_V320_sample":  # configuration 5: 256 seeded 8^4 sub-blocks (ladder, ring, oooo)
+        w = wl.ccsd_doubles_o80_v320()
+        T = tensors(w, ("V_vvvv", "T", "W0", "V_ovvo", "R"))
+        rng = np.random.default_rng(5)
+        R = T["R"]
+        _, ext = R.block_lo_ext()
+        pool = [int(x) for x in rng.permutation(R.n_blocks)[:2]]  # boxes from two output blocks: few V blocks
+        terms = {"ladder": (0.5, "V_vvvv", "abef", "T", "efij"), "oooo": (0.25, "T", "abmn", "W0", "mnij"),
+                 "ring": (1.0, "T", "aeim", "V_ovvo", "mbej")}
+        boxes = {k: [] for k in terms}
+        for _ in range(256):
+            k = ["ladder", "ring", "oooo"][int(rng.integers(3))]
+            b = pool[int(rng.integers(len(pool)))]
+            boxes[k].append((b, [int(rng.integers(0, e - 8 + 1)) for e in ext[b]]))
+        need = {"V_vvvv": set()}
+        tv = [T["V_vvvv"].modes[0].tiles[t] for t in range(T["V_vvvv"].modes[0].n_tiles)]
+        for b, _ in boxes["ladder"]:
+            ta, tb = R.block_tiles[b][0], R.block_tiles[b][1]
+            for te in range(len(tv)):
+                for tf in range(len(tv)):
+                    vb = T["V_vvvv"].find_block([ta, tb, te, tf])
+                    if vb >= 0:
+                        need["V_vvvv"].add(vb)
+        fill(w, T, ("V_vvvv", "T", "W0", "V_ovvo"), need)
+        t0 = time.perf_counter()
+        fl = 0.0
+        for k, (al, a, la, bb, lb) in terms.items():
+            if boxes[k]:
+                O.contract_boxes(al, R, "abij", T[a], la, T[bb], lb, [x[0] for x in boxes[k]], [x[1] for x in boxes[k]],
+                                 [[8] * 4] * len(boxes[k]))
+        dt = time.perf_counter() - t0
+        # flops of the sample: 2 x 8^4 x (stored summed extent of the box's output block) per box
+        import itertools
+
+        for k, (al, a, la, bb, lb) in terms.items():
+            lab = {}
+            for X, l in ((R, "abij"), (T[a], la), (T[bb], lb)):
+                for m, ch in enumerate(l):
+                    lab[ch] = X.modes[m]
+            summed = [ch for ch in la if ch not in "abij"]
+            for b, _ in boxes[k]:
+                tile = {ch: int(R.block_tiles[b, m]) for m, ch in enumerate("abij")}
+                keff = 0
+                for kt in itertools.product(*[range(lab[ch].n_tiles) for ch in summed]):
+                    tile.update(dict(zip(summed, kt)))
+                    if T[a].find_block([tile[ch] for ch in la]) < 0 or T[bb].find_block([tile[ch] for ch in lb]) < 0:
+                        continue
+                    keff += int(np.prod([lab[ch].tiles[tile[ch]][1] for ch in summed]))
+                fl += 2.0 * 8 ** 4 * keff
+        full = 2.097e13 + 5.243e12 + 1.311e12  # ladder, ring, oooo over all stored blocks
+        return {"seconds": dt, "flops": fl, "full_flops": full, "extrapolated_full_seconds": dt * full / fl}
+    raise ValueError(name)
+
+
+def run_cpu_rows(args) -> dict:
+    """The CPU-baseline rows: the FP64 oracle, as it stands, on the machine's host cores (all of them, and one
+    core where asked): configuration 1 in full, the configuration-2 oooo ladder in full, configuration 4
+    forward and reference gradient, and configuration 5's 256 seeded 8^4 sub-blocks with the full time
+    extrapolated.  Each row runs in a child process so that OMP_NUM_THREADS takes effect."""
+    cores = os.cpu_count() or 1
+    rows = {}
+    plan = [("ladder_O8_V32", cores), ("ladder_O8_V32", 1), ("oooo_O40_V240", cores), ("oooo_O40_V240", 1),
+            ("gradients_O32_V192", cores), ("doubles_O80_V320_sample", cores)]
+    for name, n in plan:
+        env = dict(os.environ, OMP_NUM_THREADS=str(n))
+        r = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-row", name], env=env,
+                           capture_output=True, text=True, check=True)
+        d = json.loads(r.stdout.strip().splitlines()[-1])
+        d["cores"] = n
+        d["TFLOP/s"] = d["flops"] / d["seconds"] / 1e12
+        rows[f"{name}_{n}core" + ("s" if n > 1 else "")] = d
+    cpu = ""
+    try:
+        cpu = next(l.split(":", 1)[1].strip() for l in open("/proc/cpuinfo") if "model name" in l or "CPU part" in l)
+    except (OSError, StopIteration):
+        pass
+    return {"case": "FP64 oracle (C, OpenMP over output blocks) on the host", "nproc": cores, "cpu": cpu,
+            "rows": rows}
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -1156,6 +1287,8 @@ def main():
     ap.add_argument("--cholesky", action="store_true",
                     help="time the ladder with V_vvvv formed on the fly from Cholesky vectors instead")
     ap.add_argument("--slab-gb", type=float, default=0.0, help="with --cholesky: slab buffer bound (0 = default)")
+    ap.add_argument("--cpu-rows", action="store_true", help="time the oracle's CPU-baseline rows instead")
+    ap.add_argument("--cpu-row", default="", help=argparse.SUPPRESS)
     ap.add_argument("--gradients", action="store_true",
                     help="time the O=32 V=192 ladder-energy forward + backward through autograd instead")
     ap.add_argument("--residual", nargs="?", const="40,240,20,40", default="",
@@ -1185,6 +1318,10 @@ def main():
         out = run_residual_case(args)
     elif args.gradients:
         out = run_gradients_case(args)
+    elif args.cpu_rows:
+        out = run_cpu_rows(args)
+    elif args.cpu_row:
+        out = _oracle_row(args.cpu_row)
     elif args.impl == "reference":
         out = run_reference(args, rank)
     else:
