@@ -912,10 +912,12 @@ def run_doubles_term_case(args) -> dict:
     ctx.profile_read()
     ctx.profile(True)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.nvtx.range_push("timed")
     e0.record()
     for _ in range(args.steps):
         run.run("ozaki_bf16", 0, steps=[st])
     e1.record()
+    torch.cuda.nvtx.range_pop()
     ctx.sync()
     ctx.profile(False)
     prof = ctx.profile_read()
