@@ -40,10 +40,25 @@ __device__ __forceinline__ void digits_step(const AddBlock& B, Digits& d) {
   }
 }
 
-// First term of a sum: alpha * v without an FP64 multiply when alpha is +-1 (GB300's FP64 pipe is narrow;
-// a copy then moves bits only), then the further terms by fused multiply-adds.
-__device__ __forceinline__ double term0(double alpha, double v) {
-  return alpha == 1.0 ? v : (alpha == -1.0 ? -v : alpha * v);
+// GB300's FP64 pipe is narrow (about two operations per clock per SM), so the adds keep FP64 arithmetic
+// off the per-element path where they can: each term's factor is classified once per thread (bit t of
+// `plus` / `minus`: alpha_t is +1 / -1), a first term with alpha = +-1 is a move of bits (the sign by an
+// integer XOR) and a copy does no FP64 operation at all.
+__device__ __forceinline__ double neg(double v) {
+  return __longlong_as_double(__double_as_longlong(v) ^ (long long)0x8000000000000000ull);
+}
+__device__ __forceinline__ double term0(unsigned plus, unsigned minus, int t, double alpha, double v) {
+  return ((plus >> t) & 1u) ? v : (((minus >> t) & 1u) ? neg(v) : alpha * v);
+}
+__device__ __forceinline__ double term_n(unsigned plus, unsigned minus, int t, double alpha, double v, double acc) {
+  return ((plus >> t) & 1u) ? acc + v : (((minus >> t) & 1u) ? acc - v : fma(alpha, v, acc));
+}
+__device__ __forceinline__ void classify(const Alpha4& alpha, int n_terms, unsigned& plus, unsigned& minus) {
+  plus = minus = 0u;
+  for (int t = 0; t < n_terms; ++t) {
+    if (alpha.v[t] == 1.0) plus |= 1u << t;
+    if (alpha.v[t] == -1.0) minus |= 1u << t;
+  }
 }
 
 // dst = beta*dst + sum_t alpha_t * src(perm_t), one chunk of one block per CTA (any layout: each source
@@ -60,6 +75,9 @@ __global__ void __launch_bounds__(256) add_kernel(double* __restrict__ dst, cons
   }
   const AddBlock& B = blocks[it.block];
   const int64_t end = min(B.n, it.start + (int64_t)kChunk);
+  unsigned plus, minus;
+  classify(alpha, n_terms, plus, minus);
+  const bool accumulate = beta != 0.0;  // beta is 0 or 1
   Digits dg;
   digits_init(B, (int32_t)(it.start + threadIdx.x), (int32_t)blockDim.x, dg);
   for (int64_t e = it.start + threadIdx.x; e < end; e += blockDim.x, digits_step(B, dg)) {
@@ -71,78 +89,109 @@ __global__ void __launch_bounds__(256) add_kernel(double* __restrict__ dst, cons
 #pragma unroll
       for (int m = 0; m < NM; ++m) s += (int64_t)dg.idx[m] * B.sstride[t][m];
       const double v = src[s];
-      acc = any ? fma(alpha.v[t], v, acc) : term0(alpha.v[t], v);
+      acc = any ? term_n(plus, minus, t, alpha.v[t], v, acc) : term0(plus, minus, t, alpha.v[t], v);
       any = true;
     }
     double* d = dst + B.dst_off + e;
-    *d = beta != 0.0 ? *d + acc : acc;  // beta is 0 or 1
+    *d = accumulate ? *d + acc : acc;
   }
 }
 
 // The same sum for a block whose source terms read the destination's last mode q with a stride (a
 // transposition): the work item is a TP x TQ tile of the plane of q and the block's "row" mode p (the
-// mode every transposed term reads contiguously), for a run of indices of the other modes.  The
-// transposed terms are staged through shared memory with reads that run along p (coalesced), and the
-// destination and the untransposed terms are then read and written along q (coalesced).
+// mode every transposed term reads contiguously) for n_o indices of the other modes.  All n_o planes of
+// the transposed terms are staged through shared memory at once with reads that run along p
+// (coalesced); the destination and the untransposed terms are then read and written along q.  The
+// per-plane base offsets sit in shared memory, computed once per item.
 __global__ void __launch_bounds__(256) add_tiled_kernel(double* __restrict__ dst, const double* __restrict__ src,
                                                         const AddBlock* __restrict__ blocks,
                                                         const TileItem* __restrict__ items, int n_terms, double beta,
                                                         Alpha4 alpha, const double* __restrict__ scale) {
-  __shared__ double tile[kMaxAddTerms][kAddTile][kAddTile + 1];
+  __shared__ double tile[kAddTileSmem];
+  __shared__ int64_t sb[kMaxAddTerms][kAddMaxOuter];
+  __shared__ int64_t db[kAddMaxOuter];
   const TileItem it = items[blockIdx.x];
+  const AddBlock& B = blocks[it.block];
+  const int nm = B.nm, p = B.tmode, q = nm - 1, n_o = it.n_o;
+  const int TP = min(kAddTile, B.dim[p] - it.p0), TQ = min(kAddTile, B.dim[q] - it.q0), TQ1 = TQ + 1;
+  const int plane = TP * TQ;
   if (scale) {
     const double sc = *scale;
     for (int t = 0; t < n_terms; ++t) alpha.v[t] *= sc;
   }
-  const AddBlock& B = blocks[it.block];
-  const int nm = B.nm, p = B.tmode, q = nm - 1;
-  const int TP = min(kAddTile, B.dim[p] - it.p0), TQ = min(kAddTile, B.dim[q] - it.q0);
-  int64_t dstr[kMaxKernelModes];
-  {
-    int64_t st = 1;
-    for (int m = nm - 1; m >= 0; --m) {
-      dstr[m] = st;
-      st *= B.dim[m];
+  unsigned plus, minus;
+  classify(alpha, n_terms, plus, minus);
+  const bool accumulate = beta != 0.0;
+  unsigned trans = 0u, live = 0u;  // bit t: term t reads q with a stride / has a source block
+#pragma unroll
+  for (int t = 0; t < kMaxAddTerms; ++t) {
+    if (t < n_terms && B.src_off[t] >= 0) {
+      live |= 1u << t;
+      if (B.sstride[t][q] != 1) trans |= 1u << t;
     }
   }
-  bool trans[kMaxAddTerms];
-  for (int t = 0; t < kMaxAddTerms; ++t) trans[t] = t < n_terms && B.src_off[t] >= 0 && B.sstride[t][q] != 1;
-  for (int o = it.o0; o < it.o0 + it.n_o; ++o) {
-    // indices of the modes other than p and q, row-major over them
-    int64_t dbase = B.dst_off + (int64_t)it.p0 * dstr[p] + it.q0;
-    int64_t sbase[kMaxAddTerms];
-    for (int t = 0; t < n_terms; ++t)
-      sbase[t] = B.src_off[t] + (int64_t)it.p0 * B.sstride[t][p] + (int64_t)it.q0 * B.sstride[t][q];
-    int r = o;
+  int64_t dstr_p = 1;
+  for (int m = nm - 1; m > p; --m) dstr_p *= B.dim[m];
+  if (threadIdx.x < n_o) {  // base offsets of the item's planes
+    int r = it.o0 + threadIdx.x;
+    int64_t d = B.dst_off + (int64_t)it.p0 * dstr_p + it.q0, st = 1;
+    int64_t s[kMaxAddTerms];
+#pragma unroll
+    for (int t = 0; t < kMaxAddTerms; ++t)
+      s[t] = t < n_terms ? B.src_off[t] + (int64_t)it.p0 * B.sstride[t][p] + (int64_t)it.q0 * B.sstride[t][q] : 0;
     for (int m = nm - 1; m >= 0; --m) {
-      if (m == p || m == q) continue;
-      const int x = r % B.dim[m];
-      r /= B.dim[m];
-      dbase += x * dstr[m];
-      for (int t = 0; t < n_terms; ++t) sbase[t] += (int64_t)x * B.sstride[t][m];
+      if (m != p && m != q) {
+        const int x = r % B.dim[m];
+        r /= B.dim[m];
+        d += x * st;
+#pragma unroll
+        for (int t = 0; t < kMaxAddTerms; ++t)
+          if (t < n_terms) s[t] += (int64_t)x * B.sstride[t][m];
+      }
+      st *= B.dim[m];
     }
-    for (int t = 0; t < n_terms; ++t) {
-      if (!trans[t]) continue;
-      for (int u = threadIdx.x; u < TP * TQ; u += blockDim.x) {
+    db[threadIdx.x] = d;
+#pragma unroll
+    for (int t = 0; t < kMaxAddTerms; ++t) sb[t][threadIdx.x] = s[t];
+  }
+  __syncthreads();
+  // stage the transposed terms: slot k holds term t's n_o planes, [plane][pl][ql] with row pitch TQ + 1
+  int k = 0;
+  for (int t = 0; t < n_terms; ++t) {
+    if (!((trans >> t) & 1u)) continue;
+    const int64_t sq = B.sstride[t][q];
+    double* tk = tile + (size_t)k * n_o * TP * TQ1;
+    for (int o = 0; o < n_o; ++o) {
+      const int64_t base = sb[t][o];
+      for (int u = threadIdx.x; u < plane; u += blockDim.x) {
         const int pl = u % TP, ql = u / TP;  // along p: consecutive source addresses
-        tile[t][pl][ql] = src[sbase[t] + pl + (int64_t)ql * B.sstride[t][q]];
+        tk[(o * TP + pl) * TQ1 + ql] = src[base + pl + (int64_t)ql * sq];
       }
     }
-    __syncthreads();
-    for (int u = threadIdx.x; u < TP * TQ; u += blockDim.x) {
+    ++k;
+  }
+  __syncthreads();
+  for (int o = 0; o < n_o; ++o) {
+    for (int u = threadIdx.x; u < plane; u += blockDim.x) {
       const int ql = u % TQ, pl = u / TQ;  // along q: consecutive destination addresses
       double acc = 0.0;
       bool any = false;
+      int kk = 0;
       for (int t = 0; t < n_terms; ++t) {
-        if (B.src_off[t] < 0) continue;
-        const double v = trans[t] ? tile[t][pl][ql] : src[sbase[t] + (int64_t)pl * B.sstride[t][p] + ql];
-        acc = any ? fma(alpha.v[t], v, acc) : term0(alpha.v[t], v);
+        if (!((live >> t) & 1u)) continue;
+        double v;
+        if ((trans >> t) & 1u) {
+          v = tile[((size_t)kk * n_o * TP + o * TP + pl) * TQ1 + ql];
+          ++kk;
+        } else {
+          v = src[sb[t][o] + (int64_t)pl * B.sstride[t][p] + ql];
+        }
+        acc = any ? term_n(plus, minus, t, alpha.v[t], v, acc) : term0(plus, minus, t, alpha.v[t], v);
         any = true;
       }
-      double* d = dst + dbase + (int64_t)pl * dstr[p] + ql;
-      *d = beta != 0.0 ? *d + acc : acc;
+      double* d = dst + db[o] + (int64_t)pl * dstr_p + ql;
+      *d = accumulate ? *d + acc : acc;
     }
-    __syncthreads();
   }
 }
 

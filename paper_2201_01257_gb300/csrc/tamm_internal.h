@@ -40,6 +40,8 @@ struct AddBlock {
 // A tile of a transposed permuted add: rows [p0, p0 + kAddTile) of the block's mode tmode, columns
 // [q0, q0 + kAddTile) of its last mode, for the indices o0 .. o0 + n_o - 1 of its other modes (row-major).
 constexpr int kAddTile = 32;
+constexpr int kAddTileSmem = 5120;  // doubles of staged planes per CTA (40 KB)
+constexpr int kAddMaxOuter = 32;    // planes per item
 struct TileItem {
   int32_t block;
   int32_t p0, q0;

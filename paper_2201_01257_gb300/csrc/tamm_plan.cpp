@@ -120,13 +120,19 @@ static void build_add_items(const std::vector<AddBlock>& blocks, std::vector<Chu
       continue;
     }
     const int p = B.tmode, q = B.nm - 1;
+    int n_trans = 0;
+    for (int t = 0; t < kMaxAddTerms; ++t)
+      if (B.src_off[t] >= 0 && B.sstride[t][q] != 1) ++n_trans;
     int64_t outer = 1;
     for (int m = 0; m < B.nm; ++m)
       if (m != p && m != q) outer *= B.dim[m];
     for (int32_t p0 = 0; p0 < B.dim[p]; p0 += kAddTile)
       for (int32_t q0 = 0; q0 < B.dim[q]; q0 += kAddTile) {
         const int64_t tp = std::min<int64_t>(kAddTile, B.dim[p] - p0), tq = std::min<int64_t>(kAddTile, B.dim[q] - q0);
-        const int32_t per = (int32_t)std::max<int64_t>(1, 4096 / (tp * tq));  // about 4096 elements per item
+        // about 4096 elements per item, as many planes as the staging buffer holds
+        int64_t per = std::max<int64_t>(1, 4096 / (tp * tq));
+        per = std::min<int64_t>(per, kAddMaxOuter);
+        if (n_trans) per = std::max<int64_t>(1, std::min<int64_t>(per, kAddTileSmem / (n_trans * tp * (tq + 1))));
         for (int64_t o = 0; o < outer; o += per)
           tiles.push_back({(int32_t)b, p0, q0, (int32_t)o, (int32_t)std::min<int64_t>(per, outer - o), 0});
       }
