@@ -129,6 +129,12 @@ TAMM_API const char* tamm_last_error(const tamm_ctx* ctx);
                                          accumulation chunks run across block pairs (fewer accumulator
                                          drains when each pair's summed range is short; a pre-pass of row
                                          maxima and some precision for blocks far below their row's maximum) */
+#define TAMM_OPT_OZAKI_FUSED_A 8 /* split precision: 1 (default) = a contraction whose block pairs each sum at
+                                    most 48 indices and whose output blocks have at most 64 columns (a
+                                    singles amplitude against a 4-index block) runs through the GEMM that
+                                    slices its A operand from FP64 in its own pipeline and writes C through
+                                    C's strides (A read once, no A image, no output permutation); its rows
+                                    and columns keep their per-block scaling; 0 = the pre-sliced path */
 #define TAMM_OPT_WAIT_CYCLES 5 /* split precision: SM clock cycles a kernel waits for one dependency (an
                                   operand copy, an MMA batch, a drained accumulator) before it records
                                   TAMM_ETIMEOUT and stops; >= 1000, default 4,000,000,000 (about 2 s).

@@ -30,7 +30,8 @@ TAMM_SYM_DENSE, TAMM_SYM_SPIN, TAMM_SYM_SPIN_IRREP = 0, 1, 2
 TAMM_PREC_F64, TAMM_PREC_OZAKI_BF16, TAMM_PREC_OZAKI_I8, TAMM_PREC_BF16X3 = 0, 1, 2, 3
 KERNEL_CLASSES = ("add", "reduce", "gemm_f64", "slice", "gemm_ozaki", "split_reduce", "triples")
 (TAMM_OPT_OZAKI_CHUNK_K, TAMM_OPT_OZAKI_PERSISTENT, TAMM_OPT_OZAKI_TILE_POLICY, TAMM_OPT_OZAKI_PANELS,
- TAMM_OPT_OZAKI_SPLIT_K, TAMM_OPT_WAIT_CYCLES, TAMM_OPT_TEST_WITHHOLD_COPY, TAMM_OPT_OZAKI_SHARED_SCALE) = range(8)
+ TAMM_OPT_OZAKI_SPLIT_K, TAMM_OPT_WAIT_CYCLES, TAMM_OPT_TEST_WITHHOLD_COPY, TAMM_OPT_OZAKI_SHARED_SCALE,
+ TAMM_OPT_OZAKI_FUSED_A) = range(9)
 SYM = {"dense": TAMM_SYM_DENSE, "spin": TAMM_SYM_SPIN, "spin_irrep": TAMM_SYM_SPIN_IRREP}
 PREC = {"f64": TAMM_PREC_F64, "ozaki_bf16": TAMM_PREC_OZAKI_BF16, "ozaki_i8": TAMM_PREC_OZAKI_I8,
         "bf16x3": TAMM_PREC_BF16X3}

@@ -97,6 +97,12 @@ __global__ void __launch_bounds__(256) add_kernel(double* __restrict__ dst, cons
   }
 }
 
+// x / d for 0 <= x < 2^16 and 1 <= d <= 2^16 by a multiply-high with m = floor((2^32 - 1) / d) + 1: the
+// product overshoots x / d by less than x / 2^32 < 1 / d, so the floor is exact (d = 1 is taken apart: its
+// m does not fit 32 bits).
+__device__ __forceinline__ uint32_t div_magic(int d) { return d == 1 ? 0u : 0xFFFFFFFFu / (uint32_t)d + 1u; }
+__device__ __forceinline__ int div_small(int x, uint32_t m, int d) { return d == 1 ? x : (int)__umulhi((uint32_t)x, m); }
+
 // The same sum for a block whose source terms read the destination's last mode q with a stride (a
 // transposition): the work item is a TP x TQ tile of the plane of q and the block's "row" mode p (the
 // mode every transposed term reads contiguously) for n_o indices of the other modes.  All n_o planes of
@@ -155,25 +161,28 @@ __global__ void __launch_bounds__(256) add_tiled_kernel(double* __restrict__ dst
     for (int t = 0; t < kMaxAddTerms; ++t) sb[t][threadIdx.x] = s[t];
   }
   __syncthreads();
-  // stage the transposed terms: slot k holds term t's n_o planes, [plane][pl][ql] with row pitch TQ + 1
+  // stage the transposed terms: slot k holds term t's n_o planes, [plane][pl][ql] with row pitch TQ + 1.
+  // Both loops run over all n_o planes at once (no thread idles at a plane's end); the indices come
+  // from multiply-high divisions, exact for n_o * plane < 2^16 (at most kAddTileSmem elements).
+  const int total = n_o * plane;
+  const uint32_t m_plane = div_magic(plane), m_tp = div_magic(TP), m_tq = div_magic(TQ);
   int k = 0;
   for (int t = 0; t < n_terms; ++t) {
     if (!((trans >> t) & 1u)) continue;
     const int64_t sq = B.sstride[t][q];
     double* tk = tile + (size_t)k * n_o * TP * TQ1;
-    for (int o = 0; o < n_o; ++o) {
-      const int64_t base = sb[t][o];
-      for (int u = threadIdx.x; u < plane; u += blockDim.x) {
-        const int pl = u % TP, ql = u / TP;  // along p: consecutive source addresses
-        tk[(o * TP + pl) * TQ1 + ql] = src[base + pl + (int64_t)ql * sq];
-      }
+    for (int x = threadIdx.x; x < total; x += blockDim.x) {
+      const int o = div_small(x, m_plane, plane), u = x - o * plane;
+      const int ql = div_small(u, m_tp, TP), pl = u - ql * TP;  // along p: consecutive source addresses
+      tk[(o * TP + pl) * TQ1 + ql] = src[sb[t][o] + pl + (int64_t)ql * sq];
     }
     ++k;
   }
   __syncthreads();
-  for (int o = 0; o < n_o; ++o) {
-    for (int u = threadIdx.x; u < plane; u += blockDim.x) {
-      const int ql = u % TQ, pl = u / TQ;  // along q: consecutive destination addresses
+  for (int x = threadIdx.x; x < total; x += blockDim.x) {
+    const int o = div_small(x, m_plane, plane), u = x - o * plane;
+    {
+      const int pl = div_small(u, m_tq, TQ), ql = u - pl * TQ;  // along q: consecutive destination addresses
       double acc = 0.0;
       bool any = false;
       int kk = 0;

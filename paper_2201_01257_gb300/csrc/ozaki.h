@@ -200,6 +200,56 @@ inline int oz_tile_rows(int64_t rows, int policy) {
   return 128;
 }
 
+// Short-K, narrow-N contractions (every block pair sums at most kOzFaMaxK indices, every output block
+// has at most kOzFaMaxN columns; e.g. a singles amplitude against a 4-index integral block) run through
+// a second GEMM kernel that slices its A operand itself: worker warps read the FP64 block straight
+// from the tensor, take each row's exponent over the block pair's summed range and write the digits
+// into the shared-memory stages the MMAs read, so A is read once from HBM and never stored as an
+// image.  B is pre-sliced as usual.  The same warps drain the accumulators, one exact chunk per block
+// pair, and write C through its own strides (the output permutation is fused).
+constexpr int kOzFaMaxK = 48;  // summed indices per block pair (three K tiles)
+constexpr int kOzFaMaxN = 64;  // output columns per output block
+
+struct FaGroup {
+  int64_t c_off;     // output block in C
+  int32_t M, N;
+  int32_t task_begin, task_end;
+  int32_t n_tile;    // H: N rounded up to 16
+  int32_t nr, nc;    // output row / column modes
+  int32_t rdim[4], rstride[4];  // GEMM output row -> C offset (mixed radix over C's strides)
+  int32_t cdim[4], cstride[4];  // GEMM output column -> C offset
+};
+
+struct FaTask {
+  int64_t b_off, b_exp;  // pre-sliced B image of the block pair and its exponents
+  int32_t a_rec;         // FP64 geometry of the A block (a SliceBlock record)
+  int32_t k_tiles;
+};
+
+struct FaItem {
+  int32_t group, mt;  // output block and 128-row tile
+};
+
+struct FaParams {
+  int64_t n_items;
+  int* status;
+  long long wait_cycles;
+  int stages;
+  const FaItem* items;
+  const FaGroup* groups;
+  const FaTask* tasks;
+  const SliceBlock* a_recs;
+  const double* a_src;
+  const uint8_t* b_tiles;
+  const int32_t* b_exp;
+  double* c;
+  double alpha, beta;
+  int32_t alpha_pow2, alpha_exp;
+};
+
+// Persistent launch of the A-slicing GEMM (one CTA per SM).
+cudaError_t launch_ozaki_fused(tamm_ctx* ctx, FaParams& p, int S);
+
 // Slicing launch shape and items for an operand's records: record i covers image rows
 // [dst_row0, dst_row0 + extent[i]); sets the warps per CTA and the warp row buffer length.
 void oz_slicing_items(std::vector<SliceBlock>& recs, const std::vector<int32_t>& extent,

@@ -240,6 +240,11 @@ extern "C" tamm_status tamm_ctx_set_option(tamm_ctx* ctx, int option, int64_t va
       ctx->oz_shared = value != 0;
       return;
     }
+    if (option == TAMM_OPT_OZAKI_FUSED_A) {
+      if (value != 0 && value != 1) throw Error(TAMM_EINVAL, "fused A must be 0 or 1");
+      ctx->oz_fused_a = value != 0;
+      return;
+    }
     if (option == TAMM_OPT_WAIT_CYCLES) {
       if (value < 1000) throw Error(TAMM_EINVAL, "wait limit must be at least 1000 cycles");
       ctx->oz_wait_cycles = (long long)value;

@@ -118,12 +118,10 @@ __device__ __forceinline__ df ld(const float2* p, int64_t i) {
 }
 
 // One item per CTA.  A thread owns four consecutive a (one 32-byte sector of U[b,c,a]) and one c and
-// walks b once, carrying the four a as four independent accumulations (the chains of dependent
-// double-float additions are what limits this kernel, not its arithmetic): U[a,b,c] is read coalesced
-// across the warp (consecutive c), U[a,c,b] along one row per a and U[b,c,a] in whole sectors; the b-only
-// factors of Y are loaded once per b for all four a.  Y of Eq. tensort2 is nine products: each T1 factor
-// carries its pair's sign (pairs (ij)k, (ik)j, (jk)i: +, -, +) and the virtual split's (ab|c +, ac|b -,
-// bc|a +).  Double-float arithmetic; the CTA's sum goes to partials[blockIdx.x] in FP64.
+// walks b, so U[a,b,c] is read coalesced across the warp (consecutive c), U[a,c,b] along one row per
+// thread and U[b,c,a] in whole sectors.  Y of Eq. tensort2 is nine products: each T1 factor carries
+// its pair's sign (pairs (ij)k, (ik)j, (jk)i: +, -, +) and the virtual split's (ab|c +, ac|b -, bc|a +).
+// Double-float arithmetic; the CTA's sum goes to partials[blockIdx.x] in FP64.
 __global__ void __launch_bounds__(256) triples_energy_kernel(const double* __restrict__ U,
                                                              const TriplesItem* __restrict__ items,
                                                              const float2* __restrict__ voo,
@@ -149,70 +147,50 @@ __global__ void __launch_bounds__(256) triples_energy_kernel(const double* __res
     const df x = ld(t1, off + (int64_t)l * it.occ_tsz[o] + it.occ_loc[o]);
     return {kSign[P] * x.hi, kSign[P] * x.lo};
   };
-  df total = {0.0f, 0.0f};
+  df acc = {0.0f, 0.0f};
   for (int u = threadIdx.x; u < nquad * nc; u += blockDim.x) {
-    const int cl = u % nc, al0 = 4 * (q0 + u / nc);
+    const int cl = u % nc, q = q0 + u / nc;
     const int c = c0 + cl;
     const df e_c = df_add(e_occ, df_neg(ld(eps_v, c)));
     df tc[3];  // term v_P[a,b] t1[c]
 #pragma unroll
     for (int P = 0; P < 3; ++P) tc[P] = t1s(2, P, cl);
-    // per a of the quad: validity, e_c - e_a, T1[a] factors, V[a,c] factors, accumulator
-    bool ok[4];
-    df e_ac[4], ta[4][3], vac[4][3], acc[4];
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const int al = al0 + j;
-      ok[j] = al < it.a_end && a0 + al < c;
-      acc[j] = {0.0f, 0.0f};
-      e_ac[j] = ok[j] ? df_add(e_c, df_neg(ld(eps_v, a0 + al))) : df{0.0f, 0.0f};
+    for (int al = 4 * q; al < min(it.a_end, 4 * q + 4); ++al) {
+      const int a = a0 + al;
+      if (a >= c) break;
+      const df e_ac = df_add(e_c, df_neg(ld(eps_v, a)));
+      df ta[3], vac[3];  // term v_P[b,c] t1[a];  v_P[a,c]
 #pragma unroll
       for (int P = 0; P < 3; ++P) {
-        ta[j][P] = ok[j] ? t1s(0, P, al) : df{0.0f, 0.0f};
+        ta[P] = t1s(0, P, al);
         const int64_t ov = it.voo_off[P * 3 + 1];
-        vac[j][P] = ok[j] && ov >= 0 ? ld(voo, ov + ((int64_t)it.pair_pre[P] * na + al) * nc + cl) : df{0.0f, 0.0f};
+        vac[P] = ov >= 0 ? ld(voo, ov + ((int64_t)it.pair_pre[P] * na + al) * nc + cl) : df{0.0f, 0.0f};
       }
-    }
-    if (!ok[0]) continue;  // a grows along the quad: no valid a at all
-    for (int bl = 0; bl < nb; ++bl) {
-      const int b = b0 + bl;
-      if (b >= c) break;
-      if (b <= a0 + al0) continue;  // not above the quad's first a yet
-      // the factors that depend on b (and c) only
-      df vbc[3], tb[3];
-#pragma unroll
-      for (int P = 0; P < 3; ++P) {
-        const int64_t obc = it.voo_off[P * 3 + 2];
-        vbc[P] = obc >= 0 ? ld(voo, obc + ((int64_t)it.pair_pre[P] * nb + bl) * nc + cl) : df{0.0f, 0.0f};
-        tb[P] = t1s(1, P, bl);
-      }
-      const df d_b = df_neg(ld(eps_v, b));
-      const double* u3 = U3 + ((int64_t)bl * nc + cl) * na + al0;
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const int al = al0 + j;
-        if (!ok[j] || a0 + al >= b) continue;
+      for (int bl = 0; bl < nb; ++bl) {
+        const int b = b0 + bl;
+        if (b <= a) continue;
+        if (b >= c) break;
         const df w = df_add(df_add(df_from(U1[((int64_t)al * nb + bl) * nc + cl]),
                                    df_neg(df_from(U2[((int64_t)al * nc + cl) * nb + bl]))),
-                            df_from(u3[j]));
+                            df_from(U3[((int64_t)bl * nc + cl) * na + al]));
         df y = {0.0f, 0.0f};
 #pragma unroll
         for (int P = 0; P < 3; ++P) {
-          const int64_t oab = it.voo_off[P * 3 + 0];
+          const int64_t oab = it.voo_off[P * 3 + 0], obc = it.voo_off[P * 3 + 2];
           const df vab = oab >= 0 ? ld(voo, oab + ((int64_t)it.pair_pre[P] * na + al) * nb + bl) : df{0.0f, 0.0f};
-          y = df_add(y, df_mul(vab, tc[P]));              // + v_P[a,b] t1[c]
-          y = df_add(y, df_neg(df_mul(vac[j][P], tb[P])));  // - v_P[a,c] t1[b]
-          y = df_add(y, df_mul(vbc[P], ta[j][P]));        // + v_P[b,c] t1[a]
+          const df vbc = obc >= 0 ? ld(voo, obc + ((int64_t)it.pair_pre[P] * nb + bl) * nc + cl) : df{0.0f, 0.0f};
+          const df tb = t1s(1, P, bl);
+          y = df_add(y, df_mul(vab, tc[P]));           // + v_P[a,b] t1[c]
+          y = df_add(y, df_neg(df_mul(vac[P], tb)));   // - v_P[a,c] t1[b]
+          y = df_add(y, df_mul(vbc, ta[P]));           // + v_P[b,c] t1[a]
         }
-        const df d = df_add(e_ac[j], d_b);  // e_i + e_j + e_k - e_a - e_b - e_c
-        acc[j] = df_add(acc[j], df_div(df_mul(df_add(w, y), w), d));
+        const df d = df_add(e_ac, df_neg(ld(eps_v, b)));  // e_i + e_j + e_k - e_a - e_b - e_c
+        acc = df_add(acc, df_div(df_mul(df_add(w, y), w), d));
       }
     }
-#pragma unroll
-    for (int j = 0; j < 4; ++j) total = df_add(total, acc[j]);
   }
   __shared__ double red[8];
-  double v = (double)total.hi + (double)total.lo;
+  double v = (double)acc.hi + (double)acc.lo;
   v = warp_sum(v);
   if (threadIdx.x % 32 == 0) red[threadIdx.x / 32] = v;
   __syncthreads();
