@@ -418,6 +418,7 @@ def run_ours(args, rank: int, world: int) -> dict | None:
             "slices": ({k: v["slices"] for k, v in tuned.items()} if tuned else oz_slices),
             "autotuned": ({k: {"slices": v["slices"], "chunk_k": v["chunk_k"], "tile_policy": v["tile_policy"],
                                "persistent": v["persistent"], "shared_scale": v["shared_scale"],
+                               "fused_a": v["fused_a"],
                                "rel_err_vs_f64_gpu": v["rel_err"],
                                "ms": round(v["ms"], 3)}
                            for k, v in tuned.items()} if tuned else None),

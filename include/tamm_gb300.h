@@ -129,12 +129,13 @@ TAMM_API const char* tamm_last_error(const tamm_ctx* ctx);
                                          accumulation chunks run across block pairs (fewer accumulator
                                          drains when each pair's summed range is short; a pre-pass of row
                                          maxima and some precision for blocks far below their row's maximum) */
-#define TAMM_OPT_OZAKI_FUSED_A 8 /* split precision: 1 (default) = a contraction whose block pairs each sum at
-                                    most 48 indices and whose output blocks have at most 64 columns (a
-                                    singles amplitude against a 4-index block) runs through the GEMM that
-                                    slices its A operand from FP64 in its own pipeline and writes C through
-                                    C's strides (A read once, no A image, no output permutation); its rows
-                                    and columns keep their per-block scaling; 0 = the pre-sliced path */
+#define TAMM_OPT_OZAKI_FUSED_A 8 /* split precision: 1 = a contraction whose block pairs each sum at most
+                                    48 indices and whose output blocks have at most 64 columns (a singles
+                                    amplitude against a 4-index block) runs through the GEMM that slices
+                                    its A operand from FP64 in its own pipeline and writes C through C's
+                                    strides (A read once, no A image, no output permutation); its rows and
+                                    columns keep their per-block scaling; 0 (default) = the pre-sliced path.
+                                    The autotuner times both where the first applies */
 #define TAMM_OPT_WAIT_CYCLES 5 /* split precision: SM clock cycles a kernel waits for one dependency (an
                                   operand copy, an MMA batch, a drained accumulator) before it records
                                   TAMM_ETIMEOUT and stops; >= 1000, default 4,000,000,000 (about 2 s).
@@ -425,8 +426,9 @@ TAMM_API tamm_status tamm_fp64_peak(tamm_ctx* ctx, int kind, double* tflops);
 /* Autotuner of the split-precision path (TAMM_PREC_OZAKI_BF16) for one
  * contraction, the same tensors and labels as tamm_contract.  It runs the FP64
  * contraction once as the reference, then for each exact-chunk length (1280,
- * 640, 320 summed indices) and for each scaling (TAMM_OPT_OZAKI_SHARED_SCALE
- * 0 and 1) the smallest slice count (3..8) whose normwise relative error
+ * 640, 320 summed indices) and for each scaling mode (TAMM_OPT_OZAKI_SHARED_SCALE
+ * 0 and 1, and, where it applies, TAMM_OPT_OZAKI_FUSED_A = 1 at one chunk length)
+ * the smallest slice count (3..8) whose normwise relative error
  * against that reference is at most target_rel_err / 2 on the given operands,
  * times each such candidate under every tile policy
  * (TAMM_OPT_OZAKI_TILE_POLICY) and grid kind (TAMM_OPT_OZAKI_PERSISTENT;
@@ -437,7 +439,8 @@ TAMM_API tamm_status tamm_fp64_peak(tamm_ctx* ctx, int kind, double* tflops);
  * context and used by every later tamm_contract of the same tensors and
  * labels with precision TAMM_PREC_OZAKI_BF16 and slices = 0.  Outputs (each
  * may be NULL): the slice count, the chunk length, the tile policy, the grid
- * kind (1 = persistent), the scaling (1 = shared), the measured error and the
+ * kind (1 = persistent), the scaling mode (0 = per block, 1 = shared, 2 = per block
+ * with A sliced inside the GEMM), the measured error and the
  * mean time in ms of the chosen configuration.  Tune
  * on representative operands: a zero product is refused (TAMM_EINVAL).  Synchronises.  Errors: TAMM_EINVAL, TAMM_ENOMEM,
  * TAMM_ECUDA, TAMM_EUNSUPPORTED (no candidate reaches the target). */

@@ -341,7 +341,8 @@ class Context:
                                           ctypes.byref(ms)),
                    "tamm_autotune")
         return {"slices": s.value, "chunk_k": ck.value, "tile_policy": tp.value, "persistent": pe.value,
-                "shared_scale": sh.value, "rel_err": err.value, "ms": ms.value}
+                "shared_scale": int(sh.value == 1), "fused_a": int(sh.value == 2), "rel_err": err.value,
+                "ms": ms.value}
 
     # grouped execution ---------------------------------------------------
     def group_begin(self) -> None:

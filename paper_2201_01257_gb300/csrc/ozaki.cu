@@ -793,6 +793,17 @@ void oz_slicing_items(std::vector<SliceBlock>& recs, const std::vector<int32_t>&
   }
 }
 
+// Every block pair sums at most kOzFaMaxK indices and every output block has at most kOzFaMaxN columns.
+bool oz_fused_eligible(const ContractLayout& lay) {
+  if (lay.free_left.size() > 4 || lay.free_right.size() > 4 || lay.summed.size() > 4) return false;
+  if (lay.groups.empty()) return false;
+  for (const auto& g : lay.groups)
+    if (g.N < 1 || g.N > kOzFaMaxN || g.M < 1 || g.M > (int64_t(1) << 30)) return false;
+  for (const auto& t : lay.tasks)
+    if (t.K < 1 || t.K > kOzFaMaxK) return false;
+  return true;
+}
+
 struct OzakiPlan : Plan {
   ContractLayout lay;
   int S;
@@ -874,16 +885,7 @@ struct OzakiPlan : Plan {
     return B;
   }
 
-  // Every block pair sums at most kOzFaMaxK indices and every output block has at most kOzFaMaxN columns.
-  bool fused_eligible() const {
-    if (lay.free_left.size() > 4 || lay.free_right.size() > 4 || lay.summed.size() > 4) return false;
-    if (lay.groups.empty()) return false;
-    for (const auto& g : lay.groups)
-      if (g.N < 1 || g.N > kOzFaMaxN || g.M < 1 || g.M > (int64_t(1) << 30)) return false;
-    for (const auto& t : lay.tasks)
-      if (t.K < 1 || t.K > kOzFaMaxK) return false;
-    return true;
-  }
+  bool fused_eligible() const { return oz_fused_eligible(lay); }
 
   void build_fused(const tamm_tensor& Lg, const tamm_tensor& Rg, const std::vector<int>& perm_l,
                    const std::vector<int>& perm_r, const std::vector<int>& perm_c) {
@@ -1228,6 +1230,7 @@ void run_contract_ozaki(tamm_ctx* ctx, double alpha, tamm_tensor* C, const char*
   const bool panels = ctx->oz_panels;
   const bool allow_split = ctx->oz_split;
   bool shared = ctx->oz_shared;
+  bool fused_opt = ctx->oz_fused_a;
   if (slices == 0) {
     slices = kOzDefaultSlices;
     if (!float_split) {
@@ -1238,12 +1241,13 @@ void run_contract_ozaki(tamm_ctx* ctx, double alpha, tamm_tensor* C, const char*
         tile_policy = t->second.tile_policy;
         persistent = t->second.persistent;
         shared = t->second.shared;
+        fused_opt = t->second.fused;
       }
     }
   }
   if (slices < kOzMinSlices || slices > kOzMaxSlices)
     throw Error(TAMM_EINVAL, "ozaki: slices must be %d..%d (0 = %d)", kOzMinSlices, kOzMaxSlices, kOzDefaultSlices);
-  const bool fused_a = ctx->oz_fused_a && !float_split && !(shared && !float_split);
+  const bool fused_a = fused_opt && !float_split && !(shared && !float_split);
   const std::string key = "oz" + std::to_string(slices) + "|" + std::to_string(tile_policy) +
                           (panels ? "p" : "") + (allow_split ? "s" : "") + (shared && !float_split ? "h" : "") +
                           (fused_a ? "f|" : "|") +

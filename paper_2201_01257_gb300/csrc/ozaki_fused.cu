@@ -30,8 +30,45 @@ __device__ __forceinline__ void fa_barrier() { asm volatile("bar.sync 2, %0;" ::
 // Generic-proxy shared-memory writes made visible to the tensor core's (async proxy) reads.
 __device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
-__device__ __forceinline__ int64_t k_offset(const SliceBlock& B, int32_t k) {
-  return B.nk == 1 ? (int64_t)k * B.kstride[0] : mixed_offset(k, B.nk, B.kdim, B.kstride);
+// The two worker warps of one TMEM lane quadrant (the two halves of every row) synchronise on their own
+// named barrier (ids 3..6), so the four quadrants do not wait for each other.
+__device__ __forceinline__ void pair_barrier(int q) { asm volatile("bar.sync %0, 64;" ::"r"(3 + q) : "memory"); }
+
+// Dependency wait without back-off: the chunks here are short, so a sleeping waiter would add its sleep
+// to every hand-off between the workers, the copy warp and the MMA issuer.  Bounded like wait_bounded.
+__device__ __forceinline__ bool wait_hot(uint64_t* bar, uint32_t parity, volatile int* abort_flag, int* status,
+                                         long long limit) {
+  const long long t0 = clock64();
+  while (!sm100::mbar_try_wait(bar, parity)) {
+    if (*abort_flag) return false;
+    if (clock64() - t0 > limit) {
+      *abort_flag = 1;
+      atomicExch(status, TAMM_ETIMEOUT);
+      return false;
+    }
+  }
+  return true;
+}
+
+// This thread's FP64 values of block pair t for item i: K tiles kt, summed indices 16 kt + 8 h + u (zero past
+// the block's rows and summed range).
+__device__ __forceinline__ void fa_load(const FaParams& p, int64_t i, int t, int row, int h, double (&x)[3][8]) {
+  const FaItem it = p.items[i];
+  const FaTask tk = p.tasks[t];
+  const SliceBlock& A = p.a_recs[tk.a_rec];
+  const int32_t grow = it.mt * kOzTileM + row;
+  const int64_t roff = grow < A.rows ? A.src_off + mixed_offset(grow, A.nr, A.rdim, A.rstride) : -1;
+  const int32_t K = A.K, nk = A.nk;
+  const int64_t ks0 = A.kstride[0];
+#pragma unroll
+  for (int kt = 0; kt < 3; ++kt)
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int32_t k = 16 * kt + 8 * h + u;
+      x[kt][u] = (roff >= 0 && kt < tk.k_tiles && k < K)
+                     ? __ldg(p.a_src + roff + (nk == 1 ? (int64_t)k * ks0 : mixed_offset(k, nk, A.kdim, A.kstride)))
+                     : 0.0;
+    }
 }
 
 template <int S>
@@ -89,7 +126,7 @@ __global__ void __launch_bounds__(kThreads, 1) ozaki_gemm_fused_a_kernel(const _
         for (int t = g.task_begin; t < g.task_end && !*abort_flag; ++t) {
           const FaTask tk = p.tasks[t];
           for (int kt = 0; kt < tk.k_tiles; ++kt) {
-            if (!wait_bounded(&empty[stage], phase ^ 1u, abort_flag, p.status, p.wait_cycles)) break;
+            if (!wait_hot(&empty[stage], phase ^ 1u, abort_flag, p.status, p.wait_cycles)) break;
             uint8_t* sb = smem + (size_t)stage * 2 * half_bytes + half_bytes;
             sm100::mbar_arrive_expect_tx(&full[stage], b_bytes);
             sm100::bulk_g2s(sb, p.b_tiles + tk.b_off + (size_t)kt * b_bytes, b_bytes, &full[stage]);
@@ -119,13 +156,14 @@ __global__ void __launch_bounds__(kThreads, 1) ozaki_gemm_fused_a_kernel(const _
       bool ok = true;
       for (int64_t i = blockIdx.x; i < p.n_items && ok; i += gridDim.x) {
         const FaGroup& g = p.groups[p.items[i].group];
+        if (g.task_begin == g.task_end) continue;  // no chunk: the workers write such an item alone
         const uint32_t H = (uint32_t)g.n_tile;
         const uint32_t nbuf = acc_buffers(H);
         if (H != cur_H) {
           // another buffer layout: every buffer still being drained must be free first
           for (int b = 0; b < kAccBufs && ok; ++b)
             if ((acc_used >> b) & 1u)
-              ok = wait_bounded(&acc_empty[b], ((acc_parity >> b) & 1u) ^ 1u, abort_flag, p.status, p.wait_cycles);
+              ok = wait_hot(&acc_empty[b], ((acc_parity >> b) & 1u) ^ 1u, abort_flag, p.status, p.wait_cycles);
           if (!ok) break;
           buf = 0;
           cur_H = H;
@@ -138,14 +176,14 @@ __global__ void __launch_bounds__(kThreads, 1) ozaki_gemm_fused_a_kernel(const _
           for (int kt = 0; kt < k_tiles; ++kt) {
             const bool first = kt == 0, last = kt + 1 == k_tiles;
             if (first) {
-              if (!wait_bounded(&acc_empty[buf], ((acc_parity >> buf) & 1u) ^ 1u, abort_flag, p.status,
-                                p.wait_cycles)) {
+              if (!wait_hot(&acc_empty[buf], ((acc_parity >> buf) & 1u) ^ 1u, abort_flag, p.status,
+                            p.wait_cycles)) {
                 ok = false;
                 break;
               }
               sm100::tc_fence_after();
             }
-            if (!wait_bounded(&full[stage], phase, abort_flag, p.status, p.wait_cycles)) {
+            if (!wait_hot(&full[stage], phase, abort_flag, p.status, p.wait_cycles)) {
               ok = false;
               break;
             }
@@ -208,7 +246,7 @@ __global__ void __launch_bounds__(kThreads, 1) ozaki_gemm_fused_a_kernel(const _
         dbuf = 0;
         drain_H = H;
       }
-      if (ok && !wait_bounded(&acc_full[dbuf], (acc_parity >> dbuf) & 1u, abort_flag, p.status, p.wait_cycles))
+      if (ok && !wait_hot(&acc_full[dbuf], (acc_parity >> dbuf) & 1u, abort_flag, p.status, p.wait_cycles))
         ok = false;
       const int hc = H >> 1;  // columns per worker: [h hc, h hc + hc)
       const int c0 = h * hc;
@@ -283,6 +321,12 @@ __global__ void __launch_bounds__(kThreads, 1) ozaki_gemm_fused_a_kernel(const _
     };
 
     int item_count = 0, chunk = 0;
+    // The values of the next block pair are loaded as soon as the current pair is converted, before the
+    // previous pair's drain, so HBM latency overlaps the drain and the next row-maximum exchange.
+    double x[3][8];
+    bool have = false;  // x holds the values of (have_i, have_t)
+    int64_t have_i = -1;
+    int have_t = -1;
     for (int64_t i = blockIdx.x; i < p.n_items; i += gridDim.x, ++item_count) {
       const int ip = item_count & 1;
       const FaItem it = p.items[i];
@@ -305,29 +349,28 @@ __global__ void __launch_bounds__(kThreads, 1) ozaki_gemm_fused_a_kernel(const _
       const int32_t grow = it.mt * kOzTileM + row;
       const bool live = grow < g.M;
       const int64_t rowoff = live ? g.c_off + mixed_offset(grow, g.nr, g.rdim, g.rstride) : -1;
+      if (g.task_begin == g.task_end) {
+        // no block pair feeds this output block: C = beta C + alpha * 0
+        if (ok && live && p.beta == 0.0) {
+          const int hc = H >> 1;
+          for (int c = h * hc; c < h * hc + hc && c < N; ++c) p.c[rowoff + mixed_offset(c, g.nc, g.cdim, g.cstride)] = p.alpha * 0.0;
+        }
+        continue;
+      }
       int Eref = kOzExpZero;  // the row's first nonzero block exponent: the item's reference
       for (int t = g.task_begin; t < g.task_end; ++t, ++chunk) {
-        const FaTask tk = p.tasks[t];
-        const SliceBlock& A = p.a_recs[tk.a_rec];
+        const int k_tiles = p.tasks[t].k_tiles;
         const int cp = chunk & 1;
-        // this thread's values: K tiles kt, indices 16 kt + 8 h + u
-        double x[3][8];
+        if (!(have && have_i == i && have_t == t)) fa_load(p, i, t, row, h, x);
         unsigned long long m = 0ull;
-        {
-          const int64_t roff = live ? A.src_off + mixed_offset(grow, A.nr, A.rdim, A.rstride) : -1;
-          const int32_t K = A.K;
 #pragma unroll
-          for (int kt = 0; kt < 3; ++kt)
+        for (int kt = 0; kt < 3; ++kt)
 #pragma unroll
-            for (int u = 0; u < 8; ++u) {
-              const int32_t k = 16 * kt + 8 * h + u;
-              x[kt][u] = (roff >= 0 && kt < tk.k_tiles && k < K) ? __ldg(p.a_src + roff + k_offset(A, k)) : 0.0;
-              m = max(m, (unsigned long long)__double_as_longlong(x[kt][u]) & 0x7FFFFFFFFFFFFFFFull);
-            }
-        }
+          for (int u = 0; u < 8; ++u)
+            m = max(m, (unsigned long long)__double_as_longlong(x[kt][u]) & 0x7FFFFFFFFFFFFFFFull);
         // the row maximum over both halves
         rmax[(cp * 2 + h) * 128 + row] = m;
-        fa_barrier();
+        pair_barrier(q);
         m = max(m, rmax[(cp * 2 + (h ^ 1)) * 128 + row]);
         int e = kOzExpZero;
         if (m != 0ull) (void)frexp(__longlong_as_double((long long)m), &e);
@@ -335,8 +378,8 @@ __global__ void __launch_bounds__(kThreads, 1) ozaki_gemm_fused_a_kernel(const _
         // digits into the stages
 #pragma unroll
         for (int kt = 0; kt < 3; ++kt) {
-          if (kt >= tk.k_tiles) break;
-          if (ok && !wait_bounded(&empty[stage], phase ^ 1u, abort_flag, p.status, p.wait_cycles)) ok = false;
+          if (kt >= k_tiles) break;
+          if (ok && !wait_hot(&empty[stage], phase ^ 1u, abort_flag, p.status, p.wait_cycles)) ok = false;
           if (ok) {
             uint32_t w[4][S];
 #pragma unroll
@@ -361,7 +404,22 @@ __global__ void __launch_bounds__(kThreads, 1) ozaki_gemm_fused_a_kernel(const _
             phase ^= 1u;
           }
         }
-        // the previous chunk's drain overlaps this chunk's MMAs
+        // the next block pair's values: the next pair of this item, else the first of the next item
+        have = false;
+        if (t + 1 < g.task_end) {
+          have_i = i;
+          have_t = t + 1;
+          have = true;
+        } else if (i + gridDim.x < p.n_items) {
+          const FaGroup& gn = p.groups[p.items[i + gridDim.x].group];
+          if (gn.task_begin < gn.task_end) {
+            have_i = i + gridDim.x;
+            have_t = gn.task_begin;
+            have = true;
+          }
+        }
+        if (have) fa_load(p, have_i, have_t, row, h, x);
+        // the previous chunk's drain overlaps this chunk's MMAs and the loads just issued
         if (pend) drain_pending();
         pend = true;
         pend_ea = e;

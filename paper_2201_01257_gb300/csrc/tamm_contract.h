@@ -85,6 +85,9 @@ void run_contract_ozaki(tamm_ctx* ctx, double alpha, tamm_tensor* C, const char*
 // Run recorded split-precision contractions: all slicing, then their GEMMs as few launches as the
 // slice counts and the per-launch problem limit allow, then output permutations.
 void execute_ozaki(tamm_ctx* ctx, const std::vector<OzOpRecord>& ops);
+// Whether the split path may run a contraction through the GEMM that slices A itself (short summed ranges,
+// narrow outputs: see ozaki.h).
+bool oz_fused_eligible(const ContractLayout& lay);
 // Key of a contraction (tensors and labels) in the autotuner's table.
 std::string tune_key(const tamm_tensor* C, const char* lc, const tamm_tensor* A, const char* la,
                      const tamm_tensor* B, const char* lb);

@@ -125,6 +125,7 @@ struct TunedConfig {
   int tile_policy;
   bool persistent;
   bool shared;  // shared row/column scaling (TAMM_OPT_OZAKI_SHARED_SCALE)
+  bool fused;   // A sliced inside the GEMM (TAMM_OPT_OZAKI_FUSED_A)
 };
 
 }  // namespace tamm
@@ -184,7 +185,7 @@ struct tamm_ctx {
   bool oz_panels = true;       // split precision: concatenate output blocks sharing their A blocks
   bool oz_split = true;        // split precision: split long summed ranges of small contractions
   bool oz_shared = false;      // split precision: shared row/column scaling (TAMM_OPT_OZAKI_SHARED_SCALE)
-  bool oz_fused_a = true;      // split precision: short-K narrow-N contractions slice A in the GEMM (TAMM_OPT_OZAKI_FUSED_A)
+  bool oz_fused_a = false;     // split precision: short-K narrow-N contractions slice A in the GEMM (TAMM_OPT_OZAKI_FUSED_A)
   long long oz_wait_cycles = 4000000000ll;  // limit of a kernel's dependency waits (TAMM_OPT_WAIT_CYCLES)
   int oz_test_withhold = 0;    // failure-path test hook (TAMM_OPT_TEST_WITHHOLD_COPY), one launch
   int64_t launches = 0;    // kernels launched by this context

@@ -88,6 +88,7 @@ extern "C" tamm_status tamm_autotune(tamm_ctx* ctx, const tamm_tensor* C, const 
   const int saved_policy = ctx->oz_tile_policy;
   const bool saved_persistent = ctx->oz_persistent;
   const bool saved_shared = ctx->oz_shared;
+  const bool saved_fused = ctx->oz_fused_a;
   tamm_status st = TAMM_OK;
   try {
     if (ctx->host_only) throw Error(TAMM_ECUDA, "host-only context (device -1) cannot run device work");
@@ -108,12 +109,18 @@ extern "C" tamm_status tamm_autotune(tamm_ctx* ctx, const tamm_tensor* C, const 
     const double denom = ref_norm;
     cuda_check(cudaEventCreate(&e0), "cudaEventCreate");
     cuda_check(cudaEventCreate(&e1), "cudaEventCreate");
-    int best_s = 0, best_chunk = 0, best_policy = 0;
-    bool best_persistent = false, best_shared = false;
+    int best_s = 0, best_chunk = 0, best_policy = 0, best_mode = 0;
+    bool best_persistent = false;
     double best_ms = 0.0, best_err = 0.0;
-    for (int sh = 0; sh < 2; ++sh)
+    // scaling modes: 0 = each block's own row/column scaling, 1 = shared scaling, 2 = own scaling with
+    // the A operand sliced inside the GEMM (only for contractions that path takes; its chunk is one block
+    // pair and its grid persistent, so one chunk length and one timing)
+    const bool fused_ok = oz_fused_eligible(ContractLayout(ctx, C, lc, A, la, B, lb));
+    for (int sh = 0; sh < 3; ++sh)
     for (int chunk : kChunks) {
-      ctx->oz_shared = sh != 0;
+      if (sh == 2 && (!fused_ok || chunk != kChunks[0])) continue;
+      ctx->oz_shared = sh == 1;
+      ctx->oz_fused_a = sh == 2;
       ctx->oz_chunk_k = chunk;
       ctx->oz_tile_policy = saved_policy;
       ctx->oz_persistent = saved_persistent;
@@ -130,7 +137,8 @@ extern "C" tamm_status tamm_autotune(tamm_ctx* ctx, const tamm_tensor* C, const 
       if (!s_ok) continue;
       // the tile policy and the grid kind change the work split, not the arithmetic of an output
       // element: time each combination
-      for (int combo = 0; combo < 2 * (int)(sizeof(kPolicies) / sizeof(kPolicies[0])); ++combo) {
+      const int n_combos = sh == 2 ? 1 : 2 * (int)(sizeof(kPolicies) / sizeof(kPolicies[0]));
+      for (int combo = 0; combo < n_combos; ++combo) {
         const int policy = kPolicies[combo / 2];
         const bool persistent = combo % 2 == 1;
         ctx->oz_tile_policy = policy;
@@ -149,7 +157,7 @@ extern "C" tamm_status tamm_autotune(tamm_ctx* ctx, const tamm_tensor* C, const 
           best_chunk = chunk;
           best_policy = policy;
           best_persistent = persistent;
-          best_shared = sh != 0;
+          best_mode = sh;
           best_ms = t;
           best_err = err_ok;
         }
@@ -158,9 +166,10 @@ extern "C" tamm_status tamm_autotune(tamm_ctx* ctx, const tamm_tensor* C, const 
     if (best_s == 0)
       throw Error(TAMM_EUNSUPPORTED, "autotune: no slice count (<= %d) reaches %.3g on these operands", kOzMaxSlices,
                   target_rel_err);
-    ctx->tuned[tune_key(C, lc, A, la, B, lb)] = {best_s, best_chunk, best_policy, best_persistent, best_shared};
+    ctx->tuned[tune_key(C, lc, A, la, B, lb)] = {best_s, best_chunk, best_policy, best_persistent, best_mode == 1,
+                                                  best_mode == 2};
     if (slices) *slices = best_s;
-    if (shared_scale) *shared_scale = best_shared ? 1 : 0;
+    if (shared_scale) *shared_scale = best_mode;
     if (chunk_k) *chunk_k = best_chunk;
     if (tile_policy) *tile_policy = best_policy;
     if (persistent) *persistent = best_persistent ? 1 : 0;
@@ -178,6 +187,7 @@ extern "C" tamm_status tamm_autotune(tamm_ctx* ctx, const tamm_tensor* C, const 
   ctx->oz_tile_policy = saved_policy;
   ctx->oz_persistent = saved_persistent;
   ctx->oz_shared = saved_shared;
+  ctx->oz_fused_a = saved_fused;
   if (e0) cudaEventDestroy(e0);
   if (e1) cudaEventDestroy(e1);
   if (ref) ctx_free(ctx, ref, bytes);

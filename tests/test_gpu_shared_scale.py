@@ -99,11 +99,13 @@ def test_autotune_reports_and_reuses_scaling(gpu_lib):
     gsp, gt = gw.build(ctx, w)
     st = next(s for s in w.steps if s.name == "t1")
     tuned = gw.Runner(ctx, w, gsp, gt).autotune(1e-10, steps=[st])["t1"]
-    assert tuned["shared_scale"] in (0, 1)
+    assert tuned["shared_scale"] in (0, 1) and tuned["fused_a"] in (0, 1)
+    assert not (tuned["shared_scale"] and tuned["fused_a"])
     R = gt["R"]
     ctx.contract(1.0, R, "abij", 0.0, gt["V_vvvo"], "abej", gt["t1"], "ei", "ozaki_bf16", 0)
     a = R.download()
     for opt, val in ((gpu_lib.TAMM_OPT_OZAKI_SHARED_SCALE, tuned["shared_scale"]),
+                     (gpu_lib.TAMM_OPT_OZAKI_FUSED_A, tuned["fused_a"]),
                      (gpu_lib.TAMM_OPT_OZAKI_CHUNK_K, tuned["chunk_k"]),
                      (gpu_lib.TAMM_OPT_OZAKI_TILE_POLICY, tuned["tile_policy"]),
                      (gpu_lib.TAMM_OPT_OZAKI_PERSISTENT, tuned["persistent"])):
