@@ -41,7 +41,7 @@ SLICES = 6
 # launches of an O=40 V=240 doubles step, from an ncu capture of this bench command's GEMM launches,
 # keyed by the hash of the kernel sources it was taken on; a changed kernel reports null until it is
 # captured again.
-MEASURED_TRAFFIC = {"911d88a71fa162e1": 6.945e9}
+MEASURED_TRAFFIC = {"76ded0dcc6dd8b12": 7.035e9}
 
 
 def kernel_source_hash() -> str:
@@ -921,9 +921,19 @@ def run_doubles_term_case(args) -> dict:
     run = gw.Runner(ctx, w, sp, T)
     run.run("f64")
     st = next(x for x in w.steps if x.name == name)
-    tuned = run.autotune(1e-10, steps=[st])[st.name]  # slices, chunk, tile policy, grid and scaling
+    if args.term_config:
+        chunk, policy, persistent, mode = (int(x) for x in args.term_config.split(","))
+        for opt, val in ((tg.TAMM_OPT_OZAKI_CHUNK_K, chunk), (tg.TAMM_OPT_OZAKI_TILE_POLICY, policy),
+                         (tg.TAMM_OPT_OZAKI_PERSISTENT, persistent), (tg.TAMM_OPT_OZAKI_SHARED_SCALE, int(mode == 1)),
+                         (tg.TAMM_OPT_OZAKI_FUSED_A, int(mode == 2))):
+            ctx.set_option(opt, val)
+        slices = 6
+        tuned = {"slices": 6, "chunk_k": chunk, "tile_policy": policy, "persistent": persistent, "mode": mode}
+    else:
+        tuned = run.autotune(1e-10, steps=[st])[st.name]  # slices, chunk, tile policy, grid and scaling
+        slices = 0
     for _ in range(max(1, args.warmup)):
-        run.run("ozaki_bf16", 0, steps=[st])
+        run.run("ozaki_bf16", slices, steps=[st])
     ctx.sync()
     ctx.profile_read()
     ctx.profile(True)
@@ -931,14 +941,15 @@ def run_doubles_term_case(args) -> dict:
     torch.cuda.nvtx.range_push("timed")
     e0.record()
     for _ in range(args.steps):
-        run.run("ozaki_bf16", 0, steps=[st])
+        run.run("ozaki_bf16", slices, steps=[st])
     e1.record()
     torch.cuda.nvtx.range_pop()
     ctx.sync()
     ctx.profile(False)
     prof = ctx.profile_read()
     ms = e0.elapsed_time(e1) / args.steps
-    return {"case": f"{w.name} {name}, split precision, autotuned", "ms": round(ms, 3),
+    return {"case": f"{w.name} {name}, split precision, " + ("fixed configuration" if args.term_config else "autotuned"),
+            "ms": round(ms, 3),
             "TFLOP/s": round(run.flops(st) / ms / 1e9, 3), "nonzero_block_flops": run.flops(st), "tuned": tuned,
             "kernel_ms": {k: round(v[0] / args.steps, 4) for k, v in prof.items() if v[1]}}
 
@@ -1302,6 +1313,9 @@ def main():
     ap.add_argument("--doubles-o80", action="store_true", help="time the O=80 V=320 contractions alone instead")
     ap.add_argument("--dense4d", default="", help="N,tile: time the dense 4-D contraction instead")
     ap.add_argument("--term", default="", help="O,V,name: time one doubles contraction of that size instead")
+    ap.add_argument("--term-config", default="", help="chunk,policy,persistent,mode: with --term, this split "
+                    "configuration (6 slices; mode 0 per-block scaling, 1 shared, 2 A sliced in the GEMM) "
+                    "instead of the autotuner's")
     ap.add_argument("--cholesky", action="store_true",
                     help="time the ladder with V_vvvv formed on the fly from Cholesky vectors instead")
     ap.add_argument("--slab-gb", type=float, default=0.0, help="with --cholesky: slab buffer bound (0 = default)")

@@ -117,11 +117,16 @@ __device__ __forceinline__ df ld(const float2* p, int64_t i) {
   return {v.x, v.y};
 }
 
-// One item per CTA.  A thread owns four consecutive a (one 32-byte sector of U[b,c,a]) and one c and
-// walks b, so U[a,b,c] is read coalesced across the warp (consecutive c), U[a,c,b] along one row per
-// thread and U[b,c,a] in whole sectors.  Y of Eq. tensort2 is nine products: each T1 factor carries
-// its pair's sign (pairs (ij)k, (ik)j, (jk)i: +, -, +) and the virtual split's (ab|c +, ac|b -, bc|a +).
-// Double-float arithmetic; the CTA's sum goes to partials[blockIdx.x] in FP64.
+constexpr int kEnergyB = 16;  // consecutive b per unit of the fused energy kernel
+
+// One item per CTA.  The item's (a, b, c) are cut into units of four consecutive a (one 32-byte sector of
+// U[b,c,a]), one c and a run of kEnergyB consecutive b, the units spread over the threads with c fastest,
+// so U[a,b,c] is read coalesced across the warp (consecutive c), U[a,c,b] along one row per thread and
+// U[b,c,a] in whole sectors, and every thread carries about the same number of (a, b, c) (a thread that
+// owned all b of its (a, c) left most of the CTA waiting on the longest walk).  Y of Eq. tensort2 is
+// nine products: each T1 factor carries its pair's sign (pairs (ij)k, (ik)j, (jk)i: +, -, +) and the
+// virtual split's (ab|c +, ac|b -, bc|a +).  Double-float arithmetic; the CTA's sum goes to
+// partials[blockIdx.x] in FP64.
 __global__ void __launch_bounds__(256) triples_energy_kernel(const double* __restrict__ U,
                                                              const TriplesItem* __restrict__ items,
                                                              const float2* __restrict__ voo,
@@ -148,9 +153,12 @@ __global__ void __launch_bounds__(256) triples_energy_kernel(const double* __res
     return {kSign[P] * x.hi, kSign[P] * x.lo};
   };
   df acc = {0.0f, 0.0f};
-  for (int u = threadIdx.x; u < nquad * nc; u += blockDim.x) {
-    const int cl = u % nc, q = q0 + u / nc;
+  const int nbr = (nb + kEnergyB - 1) / kEnergyB;  // runs of b
+  for (int u = threadIdx.x; u < nquad * nbr * nc; u += blockDim.x) {
+    const int cl = u % nc, r = u / nc, br = r % nbr, q = q0 + r / nbr;
     const int c = c0 + cl;
+    const int bl0 = br * kEnergyB, bl1 = min(nb, bl0 + kEnergyB);
+    if (b0 + bl0 >= c || b0 + bl1 - 1 <= a0 + 4 * q) continue;  // no b of this run lies in (a, c)
     const df e_c = df_add(e_occ, df_neg(ld(eps_v, c)));
     df tc[3];  // term v_P[a,b] t1[c]
 #pragma unroll
@@ -166,7 +174,7 @@ __global__ void __launch_bounds__(256) triples_energy_kernel(const double* __res
         const int64_t ov = it.voo_off[P * 3 + 1];
         vac[P] = ov >= 0 ? ld(voo, ov + ((int64_t)it.pair_pre[P] * na + al) * nc + cl) : df{0.0f, 0.0f};
       }
-      for (int bl = 0; bl < nb; ++bl) {
+      for (int bl = bl0; bl < bl1; ++bl) {
         const int b = b0 + bl;
         if (b <= a) continue;
         if (b >= c) break;
