@@ -11,8 +11,6 @@
 namespace tamm {
 namespace {
 
-constexpr int kAddBatch = 4;  // elements per thread whose loads are in flight together
-
 struct Alpha4 {
   double v[kMaxAddTerms];
 };
@@ -30,30 +28,6 @@ __device__ __forceinline__ void digits_init(const AddBlock& B, int32_t x, int32_
     x /= B.dim[m];
     d.stp[m] = q % B.dim[m];
     q /= B.dim[m];
-  }
-}
-
-// The same with the mode count known at compile time (the permuted add's blocks have exactly NM modes), so
-// the digits stay in registers.
-template <int NM>
-__device__ __forceinline__ void digits_init_n(const AddBlock& B, int32_t x, int32_t q, Digits& d) {
-#pragma unroll
-  for (int m = NM - 1; m >= 0; --m) {
-    d.idx[m] = x % B.dim[m];
-    x /= B.dim[m];
-    d.stp[m] = q % B.dim[m];
-    q /= B.dim[m];
-  }
-}
-
-template <int NM>
-__device__ __forceinline__ void digits_step_n(const AddBlock& B, Digits& d) {
-  int32_t carry = 0;
-#pragma unroll
-  for (int m = NM - 1; m >= 0; --m) {
-    int32_t v = d.idx[m] + d.stp[m] + carry;
-    carry = v >= B.dim[m] ? 1 : 0;
-    d.idx[m] = carry ? v - B.dim[m] : v;
   }
 }
 
@@ -105,41 +79,21 @@ __global__ void __launch_bounds__(256) add_kernel(double* __restrict__ dst, cons
   classify(alpha, n_terms, plus, minus);
   const bool accumulate = beta != 0.0;  // beta is 0 or 1
   Digits dg;
-  digits_init_n<NM>(B, (int32_t)(it.start + threadIdx.x), (int32_t)blockDim.x, dg);
-  // kAddBatch elements per thread and pass, every load of the batch issued before any arithmetic, so that
-  // enough bytes are in flight to cover HBM latency (one element at a time left the kernel latency-bound)
-  for (int64_t e0 = it.start + threadIdx.x; e0 < end; e0 += (int64_t)kAddBatch * blockDim.x) {
-    double v[kAddBatch][kMaxAddTerms], dv[kAddBatch];
+  digits_init(B, (int32_t)(it.start + threadIdx.x), (int32_t)blockDim.x, dg);
+  for (int64_t e = it.start + threadIdx.x; e < end; e += blockDim.x, digits_step(B, dg)) {
+    double acc = 0.0;
+    bool any = false;
+    for (int t = 0; t < n_terms; ++t) {
+      if (B.src_off[t] < 0) continue;
+      int64_t s = B.src_off[t];
 #pragma unroll
-    for (int j = 0; j < kAddBatch; ++j) {
-      const int64_t e = e0 + (int64_t)j * blockDim.x;
-#pragma unroll
-      for (int t = 0; t < kMaxAddTerms; ++t) {
-        v[j][t] = 0.0;
-        if (e < end && t < n_terms && B.src_off[t] >= 0) {
-          int64_t s = B.src_off[t];
-#pragma unroll
-          for (int m = 0; m < NM; ++m) s += (int64_t)dg.idx[m] * B.sstride[t][m];
-          v[j][t] = src[s];
-        }
-      }
-      dv[j] = (e < end && accumulate) ? dst[B.dst_off + e] : 0.0;
-      digits_step_n<NM>(B, dg);
+      for (int m = 0; m < NM; ++m) s += (int64_t)dg.idx[m] * B.sstride[t][m];
+      const double v = src[s];
+      acc = any ? term_n(plus, minus, t, alpha.v[t], v, acc) : term0(plus, minus, t, alpha.v[t], v);
+      any = true;
     }
-#pragma unroll
-    for (int j = 0; j < kAddBatch; ++j) {
-      const int64_t e = e0 + (int64_t)j * blockDim.x;
-      if (e >= end) break;
-      double acc = 0.0;
-      bool any = false;
-#pragma unroll
-      for (int t = 0; t < kMaxAddTerms; ++t) {
-        if (t >= n_terms || B.src_off[t] < 0) continue;
-        acc = any ? term_n(plus, minus, t, alpha.v[t], v[j][t], acc) : term0(plus, minus, t, alpha.v[t], v[j][t]);
-        any = true;
-      }
-      dst[B.dst_off + e] = accumulate ? dv[j] + acc : acc;
-    }
+    double* d = dst + B.dst_off + e;
+    *d = accumulate ? *d + acc : acc;
   }
 }
 
@@ -217,64 +171,35 @@ __global__ void __launch_bounds__(256) add_tiled_kernel(double* __restrict__ dst
     if (!((trans >> t) & 1u)) continue;
     const int64_t sq = B.sstride[t][q];
     double* tk = tile + (size_t)k * n_o * TP * TQ1;
-    for (int x0 = threadIdx.x; x0 < total; x0 += kAddBatch * blockDim.x) {
-      double v[kAddBatch];
-      int slot[kAddBatch];
-#pragma unroll
-      for (int j = 0; j < kAddBatch; ++j) {
-        const int x = x0 + j * blockDim.x;
-        slot[j] = -1;
-        if (x < total) {
-          const int o = div_small(x, m_plane, plane), u = x - o * plane;
-          const int ql = div_small(u, m_tp, TP), pl = u - ql * TP;  // along p: consecutive source addresses
-          v[j] = src[sb[t][o] + pl + (int64_t)ql * sq];
-          slot[j] = (o * TP + pl) * TQ1 + ql;
-        }
-      }
-#pragma unroll
-      for (int j = 0; j < kAddBatch; ++j)
-        if (slot[j] >= 0) tk[slot[j]] = v[j];
+    for (int x = threadIdx.x; x < total; x += blockDim.x) {
+      const int o = div_small(x, m_plane, plane), u = x - o * plane;
+      const int ql = div_small(u, m_tp, TP), pl = u - ql * TP;  // along p: consecutive source addresses
+      tk[(o * TP + pl) * TQ1 + ql] = src[sb[t][o] + pl + (int64_t)ql * sq];
     }
     ++k;
   }
   __syncthreads();
-  for (int x0 = threadIdx.x; x0 < total; x0 += kAddBatch * blockDim.x) {
-    double v[kAddBatch][kMaxAddTerms], dv[kAddBatch];
-    int64_t doff[kAddBatch];
-#pragma unroll
-    for (int j = 0; j < kAddBatch; ++j) {
-      const int x = x0 + j * blockDim.x;
-      doff[j] = -1;
-      if (x >= total) continue;
-      const int o = div_small(x, m_plane, plane), u = x - o * plane;
+  for (int x = threadIdx.x; x < total; x += blockDim.x) {
+    const int o = div_small(x, m_plane, plane), u = x - o * plane;
+    {
       const int pl = div_small(u, m_tq, TQ), ql = u - pl * TQ;  // along q: consecutive destination addresses
-      int kk = 0;
-#pragma unroll
-      for (int t = 0; t < kMaxAddTerms; ++t) {
-        v[j][t] = 0.0;
-        if (t >= n_terms || !((live >> t) & 1u)) continue;
-        if ((trans >> t) & 1u) {
-          v[j][t] = tile[((size_t)kk * n_o * TP + o * TP + pl) * TQ1 + ql];
-          ++kk;
-        } else {
-          v[j][t] = src[sb[t][o] + (int64_t)pl * B.sstride[t][p] + ql];
-        }
-      }
-      doff[j] = db[o] + (int64_t)pl * dstr_p + ql;
-      dv[j] = accumulate ? dst[doff[j]] : 0.0;
-    }
-#pragma unroll
-    for (int j = 0; j < kAddBatch; ++j) {
-      if (doff[j] < 0) continue;
       double acc = 0.0;
       bool any = false;
-#pragma unroll
-      for (int t = 0; t < kMaxAddTerms; ++t) {
-        if (t >= n_terms || !((live >> t) & 1u)) continue;
-        acc = any ? term_n(plus, minus, t, alpha.v[t], v[j][t], acc) : term0(plus, minus, t, alpha.v[t], v[j][t]);
+      int kk = 0;
+      for (int t = 0; t < n_terms; ++t) {
+        if (!((live >> t) & 1u)) continue;
+        double v;
+        if ((trans >> t) & 1u) {
+          v = tile[((size_t)kk * n_o * TP + o * TP + pl) * TQ1 + ql];
+          ++kk;
+        } else {
+          v = src[sb[t][o] + (int64_t)pl * B.sstride[t][p] + ql];
+        }
+        acc = any ? term_n(plus, minus, t, alpha.v[t], v, acc) : term0(plus, minus, t, alpha.v[t], v);
         any = true;
       }
-      dst[doff[j]] = accumulate ? dv[j] + acc : acc;
+      double* d = dst + db[o] + (int64_t)pl * dstr_p + ql;
+      *d = accumulate ? *d + acc : acc;
     }
   }
 }
@@ -338,24 +263,10 @@ __global__ void __launch_bounds__(256) energy_partials_kernel(const double* __re
   if (B.src_off[0] >= 0) {
     Digits dg;
     digits_init(B, (int32_t)(it.start + threadIdx.x), (int32_t)blockDim.x, dg);
-    // kAddBatch elements' loads in flight together; the products are added in element order as before
-    for (int64_t e0 = it.start + threadIdx.x; e0 < end; e0 += (int64_t)kAddBatch * blockDim.x) {
-      double av[kAddBatch], bv[kAddBatch];
-#pragma unroll
-      for (int j = 0; j < kAddBatch; ++j) {
-        const int64_t e = e0 + (int64_t)j * blockDim.x;
-        av[j] = bv[j] = 0.0;
-        if (e < end) {
-          int64_t s = B.src_off[0];
-          for (int m = 0; m < nm; ++m) s += (int64_t)dg.idx[m] * B.sstride[0][m];
-          av[j] = a[B.dst_off + e];
-          bv[j] = b[s];
-        }
-        digits_step(B, dg);
-      }
-#pragma unroll
-      for (int j = 0; j < kAddBatch; ++j)
-        if (e0 + (int64_t)j * blockDim.x < end) acc = fma(av[j], bv[j], acc);
+    for (int64_t e = it.start + threadIdx.x; e < end; e += blockDim.x, digits_step(B, dg)) {
+      int64_t s = B.src_off[0];
+      for (int m = 0; m < nm; ++m) s += (int64_t)dg.idx[m] * B.sstride[0][m];
+      acc = fma(a[B.dst_off + e], b[s], acc);
     }
   }
   double s = block_sum<256>(acc);
