@@ -475,10 +475,6 @@ __global__ void __launch_bounds__(kThreads, 1) ozaki_gemm_kernel(const __grid_co
       if (g.colmap >= 0 && has_col && bcol < g.N) {
         col_base[etid] = p.problems[q].col_base[g.colmap + bcol];
         col_stride[etid] = p.problems[q].col_stride[g.colmap + bcol];
-      } else if (g.outmap >= 0 && has_col && bcol < g.N) {
-        const OzOutMap& om = p.problems[q].outmaps[g.outmap];
-        col_base[etid] = g.c_off + mixed_offset((int32_t)bcol, om.nc, om.cdim, om.cstride);
-        col_stride[etid] = 0;
       }
       float hi[64], lo[64];
 #pragma unroll
@@ -572,13 +568,7 @@ __global__ void __launch_bounds__(kThreads, 1) ozaki_gemm_kernel(const __grid_co
           double* c = p.problems[q].c;
           double* crow = c + g.c_off + (int64_t)grow * g.N + (int64_t)it.nt * H;
           const double alpha = p.problems[q].alpha, beta = p.problems[q].beta;
-          // column panels and fused output permutations write through the column map (plus, for the
-          // latter, the row's own offset in C)
-          const bool panel = g.colmap >= 0 || g.outmap >= 0;
-          const int64_t rbase =
-              g.outmap >= 0 ? mixed_offset(grow, p.problems[q].outmaps[g.outmap].nr, p.problems[q].outmaps[g.outmap].rdim,
-                                           p.problems[q].outmaps[g.outmap].rstride)
-                            : 0;
+          const bool panel = g.colmap >= 0;
           // alpha = +-2^ae folds into the exponent: alpha 2^sc (hi + lo) costs one FP64 add, and
           // C + that one more; the result is the same rounding as the FP64 route below
           const int ae = p.problems[q].alpha_exp;
@@ -598,7 +588,7 @@ __global__ void __launch_bounds__(kThreads, 1) ozaki_gemm_kernel(const __grid_co
               } else {
                 av = alpha * 0.0;
               }
-              double* cp = panel ? c + col_base[col] + rbase + (int64_t)grow * col_stride[col] : crow + col;
+              double* cp = panel ? c + col_base[col] + (int64_t)grow * col_stride[col] : crow + col;
               *cp = beta != 0.0 ? fma(beta, *cp, av) : av;
             }
           }
@@ -828,7 +818,6 @@ struct OzakiPlan : Plan {
   OzItem* d_items = nullptr;
   int64_t* d_col_base = nullptr;
   int32_t* d_col_stride = nullptr;
-  OzOutMap* d_outmap = nullptr;  // output maps when the output permutation is fused into the epilogue
   int64_t n_items = 0;
   OzReduceItem* d_red = nullptr;  // reduction chunks of the split groups
   int64_t n_red = 0;
@@ -1075,7 +1064,7 @@ struct OzakiPlan : Plan {
       gg.n_tile = H;
       gg.nsplit = 1;
       gg.shared = shared ? 1 : 0;
-      gg.outmap = -1;
+      gg.pad = 0;
       gg.ws_off = 0;
       if (mem.size() == 1) {
         gg.c_off = O.off[(size_t)g0.out_block];
@@ -1155,6 +1144,12 @@ struct OzakiPlan : Plan {
     scratch_bytes += align((size_t)ea * 4);
     off_eb = scratch_bytes;
     scratch_bytes += align((size_t)eb * 4);
+    if (lay.out_perm) {
+      const char* ls[1] = {lay.out_gemm.c_str()};
+      perm_out.reset(new AddPlan(c, *C, lay.label_c.c_str(), *lay.out_perm, 1, ls));
+      off_x = scratch_bytes;
+      scratch_bytes += align((size_t)lay.out_perm->n_elems * 8);
+    }
     // Split summed ranges when the contraction has too few output tiles to fill the GPU (two
     // 128 x 128 tiles per SM): every group's tasks are cut into the same number of consecutive
     // ranges (at most 8, at most one per task).  The count depends only on the block structure,
@@ -1176,38 +1171,6 @@ struct OzakiPlan : Plan {
         const int64_t MN = (int64_t)gg.M * gg.N;
         ws_doubles += gg.nsplit * MN;
         for (int64_t e = 0; e < MN; e += 4096) red.push_back({(int32_t)gi, 0, e, std::min<int64_t>(MN, e + 4096)});
-      }
-    }
-    // C's label order differs from the GEMM's: when every group is one output block written in one range,
-    // the epilogue writes C through its own strides (the permutation fused); otherwise the GEMM writes a
-    // GEMM-order scratch that a permuted add moves into C
-    std::vector<OzOutMap> outmaps;
-    if (lay.out_perm) {
-      bool fuse = true;
-      for (const OzGroup& gg : groups) fuse = fuse && gg.nsplit == 1 && gg.colmap < 0;
-      if (fuse) {
-        const std::vector<int> perm_c = perm_of(lay.out_gemm, lay.label_c);
-        for (size_t gi = 0; gi < groups.size(); ++gi) {
-          const SliceBlock Cg = block_geometry(*lay.c, O, perm_c, 0, nfl, nfl, nfr, lay.groups[(size_t)members[gi][0]].out_block);
-          OzOutMap m;
-          memset(&m, 0, sizeof(m));
-          m.nr = Cg.nr;
-          m.nc = Cg.nk;
-          for (int q = 0; q < 4; ++q) {
-            m.rdim[q] = Cg.rdim[q];
-            m.rstride[q] = Cg.rstride[q];
-            m.cdim[q] = Cg.kdim[q];
-            m.cstride[q] = Cg.kstride[q];
-          }
-          groups[gi].c_off = Cg.src_off;
-          groups[gi].outmap = (int32_t)outmaps.size();
-          outmaps.push_back(m);
-        }
-      } else {
-        const char* ls[1] = {lay.out_gemm.c_str()};
-        perm_out.reset(new AddPlan(c, *C, lay.label_c.c_str(), *lay.out_perm, 1, ls));
-        off_x = scratch_bytes;
-        scratch_bytes += align((size_t)lay.out_perm->n_elems * 8);
       }
     }
     // work items, the groups with the longest summed range first (the grid then ends on short
@@ -1253,7 +1216,6 @@ struct OzakiPlan : Plan {
       d_col_base = upload(col_base);
       d_col_stride = upload(col_stride);
     }
-    if (!outmaps.empty()) d_outmap = upload(outmaps);
     n_red = (int64_t)red.size();
     if (n_red) d_red = upload(red);
   }
@@ -1402,7 +1364,6 @@ void execute_ozaki(tamm_ctx* ctx, const std::vector<OzOpRecord>& ops) {
     pr.items = p->d_items;
     pr.col_base = p->d_col_base;
     pr.col_stride = p->d_col_stride;
-    pr.outmaps = p->d_outmap;
     pr.ws = (double*)(s + p->off_ws);
     pr.c = p->perm_out ? (double*)(s + p->off_x) : ops[i].c;
     pr.alpha = ops[i].alpha;

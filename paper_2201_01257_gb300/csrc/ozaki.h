@@ -95,16 +95,7 @@ struct OzGroup {
   int32_t nsplit;
   int32_t shared;  // every task of the group has the same row and column exponents (shared scaling): the
                    // exact accumulation chunks run across task boundaries
-  int32_t outmap;  // >= 0: the output block is C's own block, written through the map outmaps[outmap]
-                   // (the output permutation fused into the epilogue; c_off is then C's block offset)
-};
-
-// Where a GEMM output element (row r, column c) of an output block lives in C when C's label order differs
-// from the GEMM order: c_off + sum of r's mixed-radix digits (rdim, row-major) times rstride + the same for c.
-struct OzOutMap {
-  int32_t nr, nc;
-  int32_t rdim[4], rstride[4];
-  int32_t cdim[4], cstride[4];
+  int32_t pad;
 };
 
 struct OzTask {
@@ -126,7 +117,6 @@ struct OzProblem {
   const struct OzItem* items;
   const int64_t* col_base;    // column maps of the panels
   const int32_t* col_stride;
-  const OzOutMap* outmaps;    // output maps of groups written straight into C in its own label order
   double* ws;                 // partials of split groups
   int64_t item_begin;
   double* c;

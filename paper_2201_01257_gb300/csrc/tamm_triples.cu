@@ -637,7 +637,6 @@ struct TriplesPlan : Plan {
           memset(&gg, 0, sizeof(gg));
           gg.c_off = triple_ws[(size_t)n] + bt.off[g];
           gg.colmap = -1;
-          gg.outmap = -1;
           gg.M = (int32_t)(nx * ny);
           gg.N = (int32_t)nz;
           gg.n_tile = H;
