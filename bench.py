@@ -661,6 +661,18 @@ def run_irrep_case(args) -> dict:
     out = {"case": f"{w.name}: vvvv ladder + ring with P(ab)P(ij), D2h irreps, tiles U{{8..96}}",
            "nonzero_block_flops": flops, "blocks": {k: T[k].n_blocks for k in ("V_vvvv", "T", "R")}}
     with torch.cuda.stream(stream):
+        # the one-time cost of a plan (block-pair enumeration, slicing and work-item records, their upload):
+        # the first grouped call on a fresh context against the next one, host wall clock, synchronised
+        ctx.set_option(tg.TAMM_OPT_OZAKI_TILE_POLICY, 1)
+        walls = []
+        for _ in range(2):
+            ctx.sync()
+            t0 = time.perf_counter()
+            run.run_grouped(w.steps, "ozaki_bf16", SLICES)
+            ctx.sync()
+            walls.append((time.perf_counter() - t0) * 1e3)
+        out["plan_once"] = {"first_call_ms": round(walls[0], 2), "next_call_ms": round(walls[1], 2),
+                            "plan_ms": round(walls[0] - walls[1], 2)}
         for policy in (0, 1, 2):
             ctx.set_option(tg.TAMM_OPT_OZAKI_TILE_POLICY, policy)
             ms_g = timed(lambda: run.run_grouped(w.steps, "ozaki_bf16", SLICES), args.steps)
