@@ -421,10 +421,9 @@ __global__ void __launch_bounds__(kThreads, 1) ozaki_gemm_kernel(const __grid_co
     // ----------------------------------------------------------- epilogue
     asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(kRegsHigh));
     const int q = warp & 3;                 // TMEM lane quadrant of this warp
-    const int h = (warp - 4) >> 2;          // column half: [64h, 64h+64)
+    const int h = (warp - 4) >> 2;          // column half of the item's tile
     const int etid = threadIdx.x - 128;     // 0..255
     const int row = q * 32 + lane;
-    const int c0 = 64 * h;
     const uint32_t trow = tmem + ((uint32_t)(q * 32) << 16);
     uint32_t task_count = 0;
     uint32_t acc_parity = 0, buf = 0;  // same buffer sequence as the MMA issuer
@@ -440,6 +439,9 @@ __global__ void __launch_bounds__(kThreads, 1) ozaki_gemm_kernel(const __grid_co
       const OzGroup g = p.problems[q].groups[it.group];
       const int H = g.n_tile;
       const int n_valid = min(H, g.N - it.nt * H);
+      // the two column halves split the tile's H columns evenly (H is a multiple of 16), so a narrow tile
+      // (H = 80: 40 + 40) does not leave one half of the epilogue with most of the drain
+      const int c0 = h * (H >> 1), c_end = min(c0 + (H >> 1), n_valid);
       const uint32_t nbuf = acc_buffers((uint32_t)H);
       if (H != cur_H) {
         buf = 0;
@@ -517,7 +519,7 @@ __global__ void __launch_bounds__(kThreads, 1) ozaki_gemm_kernel(const __grid_co
 #pragma unroll
           for (int g8 = 0; g8 < 8; ++g8) {
             const int col = c0 + 8 * g8;
-            if (col >= n_valid) break;  // columns past a ragged tile's width were not computed
+            if (col >= c_end) break;  // this half's end; columns past a ragged tile's width were not computed
             float r0[8], r1[8], r2[8], r3[8];
             sm100::tmem_ld8(tb + 0 * H + col, r0);
             sm100::tmem_ld8(tb + 1 * H + col, r1);
@@ -551,7 +553,7 @@ __global__ void __launch_bounds__(kThreads, 1) ozaki_gemm_kernel(const __grid_co
 #pragma unroll
           for (int j = 0; j < 64; ++j) {
             const int col = c0 + j;
-            if (col < n_valid) {
+            if (col < c_end) {
               double v = 0.0;
               if (Eref != kOzExpZero && fref[col] != kOzExpZero) {
                 const int sc = Eref + fref[col] - 12;
@@ -576,7 +578,7 @@ __global__ void __launch_bounds__(kThreads, 1) ozaki_gemm_kernel(const __grid_co
 #pragma unroll
           for (int j = 0; j < 64; ++j) {
             const int col = c0 + j;
-            if (col < n_valid) {
+            if (col < c_end) {
               double av = 0.0;  // alpha * (product)
               if (Eref != kOzExpZero && fref[col] != kOzExpZero) {
                 const int sc = Eref + fref[col] - 12;
