@@ -41,7 +41,7 @@ SLICES = 6
 # launches of an O=40 V=240 doubles step, from an ncu capture of this bench command's GEMM launches,
 # keyed by the hash of the kernel sources it was taken on; a changed kernel reports null until it is
 # captured again.
-MEASURED_TRAFFIC = {"76ded0dcc6dd8b12": 7.035e9}
+MEASURED_TRAFFIC = {"2c7bdc1ea544cab5": 8.035e9}
 
 
 def kernel_source_hash() -> str:
