@@ -426,7 +426,7 @@ TAMM_API tamm_status tamm_fp64_peak(tamm_ctx* ctx, int kind, double* tflops);
 /* Autotuner of the split-precision path (TAMM_PREC_OZAKI_BF16) for one
  * contraction, the same tensors and labels as tamm_contract.  It runs the FP64
  * contraction once as the reference, then for each exact-chunk length (1280,
- * 640, 320 summed indices) and for each scaling mode (TAMM_OPT_OZAKI_SHARED_SCALE
+ * 800, 640, 320 summed indices) and for each scaling mode (TAMM_OPT_OZAKI_SHARED_SCALE
  * 0 and 1, and, where it applies, TAMM_OPT_OZAKI_FUSED_A = 1 at one chunk length)
  * the smallest slice count (3..8) whose normwise relative error
  * against that reference is at most target_rel_err / 2 on the given operands,

@@ -43,7 +43,7 @@ using namespace tamm;
 namespace {
 
 constexpr double kSafety = 0.5;  // margin for other data of the same contraction
-constexpr int kChunks[] = {1280, 640, 320};
+constexpr int kChunks[] = {1280, 800, 640, 320};  // 800: half of a 40 x 40 block pair's summed range
 constexpr int kPolicies[] = {0, 1, 2, 3};  // tile policies (TAMM_OPT_OZAKI_TILE_POLICY)
 constexpr int kTimedRuns = 3;
 
