@@ -60,7 +60,8 @@ def test_autotune_meets_target_and_is_used(ladder_energy):
     print("autotune 1e-10:", tight, " 1e-4:", loose)
     assert tight["rel_err"] <= 0.5e-10 and loose["rel_err"] <= 0.5e-4
     assert loose["slices"] <= tight["slices"]
-    assert 3 <= tight["slices"] <= 8 and tight["chunk_k"] in (320, 640, 1280) and tight["tile_policy"] in (0, 1, 2)
+    assert 3 <= tight["slices"] <= 8 and tight["chunk_k"] in (320, 640, 800, 1280)
+    assert tight["tile_policy"] in (0, 1, 2, 3)
     # the last tuning (1e-4) is the remembered one: re-tune at 1e-10 and use it through slices = 0
     tight = ctx.autotune(R, "abij", V, "abef", T, "efij", 1e-10)
     ctx.contract(0.5, R, "abij", 0.0, V, "abef", T, "efij", "ozaki_bf16", 0)
@@ -68,11 +69,15 @@ def test_autotune_meets_target_and_is_used(ladder_energy):
     ctx.set_option(tg.TAMM_OPT_OZAKI_CHUNK_K, tight["chunk_k"])
     ctx.set_option(tg.TAMM_OPT_OZAKI_TILE_POLICY, tight["tile_policy"])
     ctx.set_option(tg.TAMM_OPT_OZAKI_PERSISTENT, tight["persistent"])
+    ctx.set_option(tg.TAMM_OPT_OZAKI_SHARED_SCALE, tight["shared_scale"])
+    ctx.set_option(tg.TAMM_OPT_OZAKI_FUSED_A, tight["fused_a"])
     ctx.contract(0.5, R, "abij", 0.0, V, "abef", T, "efij", "ozaki_bf16", tight["slices"])
     explicit = R.download()
     ctx.set_option(tg.TAMM_OPT_OZAKI_CHUNK_K, 640)
     ctx.set_option(tg.TAMM_OPT_OZAKI_TILE_POLICY, 1)
     ctx.set_option(tg.TAMM_OPT_OZAKI_PERSISTENT, 0)
+    ctx.set_option(tg.TAMM_OPT_OZAKI_SHARED_SCALE, 0)
+    ctx.set_option(tg.TAMM_OPT_OZAKI_FUSED_A, 0)
     assert np.array_equal(auto, explicit)
     _, ot = O.build_workload(wl.Workload(w.name, w.seed, w.spaces,
                                          {k: w.tensors[k] for k in ("V_vvvv", "T", "Tp")}))
