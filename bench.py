@@ -245,15 +245,27 @@ def run_ours(args, rank: int, world: int) -> dict | None:
             go = lambda: run.run("ozaki_bf16" if prec == "oz" else "f64", oz_slices if prec == "oz" else 0,
                                  steps=[st])
             go()
+            ctx.profile_read()
+            ctx.profile(True)
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
             for _ in range(reps):
                 go()
             e1.record(stream)
             torch.cuda.synchronize()
+            ctx.profile(False)
+            kp = ctx.profile_read()
             t = e0.elapsed_time(e1) / reps
             res["split_ms" if prec == "oz" else "f64_ms"] = round(t, 3)
             res["split_TFLOP/s" if prec == "oz" else "f64_TFLOP/s"] = round(res["nonzero_block_flops"] / t / 1e9, 3)
+            if prec == "oz" and kp["gemm_ozaki"][0] > 0:
+                # this contraction's own GEMM launches against the sustained BF16 peak, in slice products
+                s_used = tuned[st.name]["slices"] if tuned else oz_slices
+                g_ms = kp["gemm_ozaki"][0] / reps
+                res["split_gemm_ms"] = round(g_ms, 3)
+                res["split_gemm_frac_of_sustained_bf16"] = round(
+                    res["nonzero_block_flops"] * (s_used * (s_used + 1) // 2) / (g_ms * 1e-3) / 1e12
+                    / measured_peaks().get("bf16_tflops_sustained", 1700.0), 4)
         per_contraction[st.name] = res
 
     # --- the two transposed permuted adds of the step alone (tiled through shared memory): GB/s ---
