@@ -1071,8 +1071,8 @@ def run_residual_case(args) -> dict:
     """One full CCSD residual (T1 and T2 equations, Stanton-Gauss intermediates, the energy and the
     residual norms: 55 library operations in 11 dependency levels) at O=40 V=240, tiles 20/40 by default:
     operation by operation, through the scheduler (each level's split-precision contractions as one
-    grouped launch), and that scheduled run captured in one CUDA graph; split precision (6 slices) and
-    FP64.  Inputs are seeded normals drawn on the device.  Throughput counts the nonzero-block flops of
+    grouped launch), and that scheduled run captured in one CUDA graph; split precision (every contraction
+    autotuned for 1e-10; also six slices with the default options, operation by operation) and FP64.  Inputs are seeded normals drawn on the device.  Throughput counts the nonzero-block flops of
     the 36 contractions."""
     import torch
 
@@ -1108,8 +1108,20 @@ def run_residual_case(args) -> dict:
         out = {"case": f"{w.name}: CCSD T1 + T2 residual, energy and norms, tiles {to}/{tv}", "operations": len(w.steps),
                "contractions": sum(isinstance(st, wl.ContractSpec) for st in w.steps), "nonzero_block_flops": flops}
         k = max(1, args.steps)
-        ms_seq = timed(lambda: run.run("ozaki_bf16", SLICES, energy_out=e.data_ptr()), k, max(1, args.warmup))
-        sch = run.scheduled("ozaki_bf16", SLICES, energy_out=e.data_ptr())
+        # FP64 first: the reference, and the values every intermediate holds when the autotuner looks at it
+        ms64 = timed(lambda: run.run("f64", 0, energy_out=e.data_ptr()), 1, 1)
+        r2_64 = T["R2"].download()
+        e_64 = e.cpu().numpy()[:4].copy()
+        # six slices with the context's default options, operation by operation
+        ms_fixed = timed(lambda: run.run("ozaki_bf16", SLICES, energy_out=e.data_ptr()), k, max(1, args.warmup))
+        # every contraction autotuned (slices, chunk, tile policy, grid, scaling) for 1e-10, then slices = 0
+        run.run("f64", 0, energy_out=e.data_ptr())
+        t0 = time.time()
+        tuned = run.autotune(1e-10)
+        out["autotune_seconds"] = round(time.time() - t0, 2)
+        out["autotuned_slices"] = sorted({v["slices"] for v in tuned.values()})
+        ms_seq = timed(lambda: run.run("ozaki_bf16", 0, energy_out=e.data_ptr()), k, max(1, args.warmup))
+        sch = run.scheduled("ozaki_bf16", 0, energy_out=e.data_ptr())
         out["levels"] = max(sch.levels()) + 1
         ms_sch = timed(sch.execute, k, 1)
         ctx.profile_read()
@@ -1124,10 +1136,9 @@ def run_residual_case(args) -> dict:
         ms_graph = timed(g.launch, k, 1)
         r2_split = T["R2"].download()
         e_split = e.cpu().numpy()[:4].copy()
-        ms64 = timed(lambda: run.run("f64", 0, energy_out=e.data_ptr()), 1, 1)
-        r2_64 = T["R2"].download()
-        e_64 = e.cpu().numpy()[:4].copy()
     out.update({
+        "split_fixed6_sequential_ms": round(ms_fixed, 3),
+        "split_fixed6_sequential_TFLOP/s": round(flops / ms_fixed / 1e9, 3),
         "split_sequential_ms": round(ms_seq, 3), "split_scheduled_ms": round(ms_sch, 3),
         "split_graph_ms": round(ms_graph, 3), "graph_kernels": g.kernel_launches,
         "split_sequential_TFLOP/s": round(flops / ms_seq / 1e9, 3),
