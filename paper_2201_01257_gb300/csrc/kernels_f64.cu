@@ -31,6 +31,30 @@ __device__ __forceinline__ void digits_init(const AddBlock& B, int32_t x, int32_
   }
 }
 
+// The same with the mode count known at compile time (a permuted add's blocks all have the destination's
+// NM modes): the loops unroll and the digits stay in registers instead of local memory.
+template <int NM>
+__device__ __forceinline__ void digits_init_n(const AddBlock& B, int32_t x, int32_t q, Digits& d) {
+#pragma unroll
+  for (int m = NM - 1; m >= 0; --m) {
+    d.idx[m] = x % B.dim[m];
+    x /= B.dim[m];
+    d.stp[m] = q % B.dim[m];
+    q /= B.dim[m];
+  }
+}
+
+template <int NM>
+__device__ __forceinline__ void digits_step_n(const AddBlock& B, Digits& d) {
+  int32_t carry = 0;
+#pragma unroll
+  for (int m = NM - 1; m >= 0; --m) {
+    int32_t v = d.idx[m] + d.stp[m] + carry;
+    carry = v >= B.dim[m] ? 1 : 0;
+    d.idx[m] = carry ? v - B.dim[m] : v;
+  }
+}
+
 __device__ __forceinline__ void digits_step(const AddBlock& B, Digits& d) {
   int32_t carry = 0;
   for (int m = B.nm - 1; m >= 0; --m) {
@@ -55,9 +79,10 @@ __device__ __forceinline__ double term_n(unsigned plus, unsigned minus, int t, d
 }
 __device__ __forceinline__ void classify(const Alpha4& alpha, int n_terms, unsigned& plus, unsigned& minus) {
   plus = minus = 0u;
-  for (int t = 0; t < n_terms; ++t) {
-    if (alpha.v[t] == 1.0) plus |= 1u << t;
-    if (alpha.v[t] == -1.0) minus |= 1u << t;
+#pragma unroll
+  for (int t = 0; t < kMaxAddTerms; ++t) {
+    if (t < n_terms && alpha.v[t] == 1.0) plus |= 1u << t;
+    if (t < n_terms && alpha.v[t] == -1.0) minus |= 1u << t;
   }
 }
 
@@ -71,7 +96,9 @@ __global__ void __launch_bounds__(256) add_kernel(double* __restrict__ dst, cons
   const ChunkItem it = items[blockIdx.x];
   if (scale) {  // alpha_t * (*scale), read once per thread
     const double sc = *scale;
-    for (int t = 0; t < n_terms; ++t) alpha.v[t] *= sc;
+#pragma unroll
+    for (int t = 0; t < kMaxAddTerms; ++t)
+      if (t < n_terms) alpha.v[t] *= sc;
   }
   const AddBlock& B = blocks[it.block];
   const int64_t end = min(B.n, it.start + (int64_t)kChunk);
@@ -79,12 +106,13 @@ __global__ void __launch_bounds__(256) add_kernel(double* __restrict__ dst, cons
   classify(alpha, n_terms, plus, minus);
   const bool accumulate = beta != 0.0;  // beta is 0 or 1
   Digits dg;
-  digits_init(B, (int32_t)(it.start + threadIdx.x), (int32_t)blockDim.x, dg);
-  for (int64_t e = it.start + threadIdx.x; e < end; e += blockDim.x, digits_step(B, dg)) {
+  digits_init_n<NM>(B, (int32_t)(it.start + threadIdx.x), (int32_t)blockDim.x, dg);
+  for (int64_t e = it.start + threadIdx.x; e < end; e += blockDim.x, digits_step_n<NM>(B, dg)) {
     double acc = 0.0;
     bool any = false;
-    for (int t = 0; t < n_terms; ++t) {
-      if (B.src_off[t] < 0) continue;
+#pragma unroll
+    for (int t = 0; t < kMaxAddTerms; ++t) {
+      if (t >= n_terms || B.src_off[t] < 0) continue;
       int64_t s = B.src_off[t];
 #pragma unroll
       for (int m = 0; m < NM; ++m) s += (int64_t)dg.idx[m] * B.sstride[t][m];
@@ -123,7 +151,9 @@ __global__ void __launch_bounds__(256) add_tiled_kernel(double* __restrict__ dst
   const int plane = TP * TQ;
   if (scale) {
     const double sc = *scale;
-    for (int t = 0; t < n_terms; ++t) alpha.v[t] *= sc;
+#pragma unroll
+    for (int t = 0; t < kMaxAddTerms; ++t)
+      if (t < n_terms) alpha.v[t] *= sc;
   }
   unsigned plus, minus;
   classify(alpha, n_terms, plus, minus);
@@ -186,8 +216,9 @@ __global__ void __launch_bounds__(256) add_tiled_kernel(double* __restrict__ dst
       double acc = 0.0;
       bool any = false;
       int kk = 0;
-      for (int t = 0; t < n_terms; ++t) {
-        if (!((live >> t) & 1u)) continue;
+#pragma unroll
+      for (int t = 0; t < kMaxAddTerms; ++t) {
+        if (t >= n_terms || !((live >> t) & 1u)) continue;
         double v;
         if ((trans >> t) & 1u) {
           v = tile[((size_t)kk * n_o * TP + o * TP + pl) * TQ1 + ql];
