@@ -1031,10 +1031,11 @@ def run_triples_case(args) -> dict:
     # by timing like the autotuner, among the configurations whose E(T) is within half the 1e-10 target of
     # the FP64 value (the slice count and the scaling change the arithmetic; the rest only the work split)
     cfg_ms, cfg_err = {}, {}
-    for slices in (6, 5, 4):
-        for policy in (1, 3):
-            for persistent in (0, 1):
-                for shared in (0, 1):
+    fixed = tuple(int(x) for x in args.triples_config.split(",")) if getattr(args, "triples_config", "") else None
+    for slices in ((fixed[0],) if fixed else (6, 5, 4)):
+        for policy in ((fixed[1],) if fixed else (1, 3)):
+            for persistent in ((fixed[2],) if fixed else (0, 1)):
+                for shared in ((fixed[3],) if fixed else (0, 1)):
                     ctx.set_option(tg.TAMM_OPT_OZAKI_TILE_POLICY, policy)
                     ctx.set_option(tg.TAMM_OPT_OZAKI_PERSISTENT, persistent)
                     ctx.set_option(tg.TAMM_OPT_OZAKI_SHARED_SCALE, shared)
@@ -1366,6 +1367,8 @@ def main():
                     help="time the O=32 V=192 ladder-energy forward + backward through autograd instead")
     ap.add_argument("--residual", nargs="?", const="40,240,20,40", default="",
                     help="O,V,to,tv: time one full CCSD residual, sequential vs scheduled vs graph, instead")
+    ap.add_argument("--triples-config", default="", help="slices,policy,persistent,shared: with --triples, this "
+                    "split configuration instead of the sweep")
     ap.add_argument("--triples", nargs="?", const="32,160,16,80", default="",
                     help="O,V,to,tv: time the (T) correction instead (default 32,160,16,80)")
     args = ap.parse_args()
