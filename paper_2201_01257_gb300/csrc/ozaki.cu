@@ -575,25 +575,23 @@ __global__ void __launch_bounds__(kThreads, 1) ozaki_gemm_kernel(const __grid_co
           // C + that one more; the result is the same rounding as the FP64 route below
           const int ae = p.problems[q].alpha_exp;
           const bool a_p2 = p.problems[q].alpha_pow2 != 0, a_neg = alpha < 0.0;
-          // per-item constants, so that the FP64 pipe (narrow on this chip) sees one add per output
-          // element and no compares or products on the common path
-          const bool accumulate = beta != 0.0;
-          const double zero_out = alpha * 0.0;
 #pragma unroll
           for (int j = 0; j < 64; ++j) {
             const int col = c0 + j;
             if (col < c_end) {
-              double av = zero_out;  // alpha * (product)
+              double av = 0.0;  // alpha * (product)
               if (Eref != kOzExpZero && fref[col] != kOzExpZero) {
                 const int sc = Eref + fref[col] - 12;
                 double dh, dl;
                 if (a_p2 && f2d_scaled(hi[j], sc + ae, a_neg, dh) && f2d_scaled(lo[j], sc + ae, a_neg, dl))
-                  av = lo[j] == 0.0f ? dh : dh + dl;
+                  av = dh + dl;
                 else
                   av = alpha * (((double)hi[j] + (double)lo[j]) * pow2d(sc));
+              } else {
+                av = alpha * 0.0;
               }
               double* cp = panel ? c + col_base[col] + (int64_t)grow * col_stride[col] : crow + col;
-              *cp = accumulate ? fma(beta, *cp, av) : av;
+              *cp = beta != 0.0 ? fma(beta, *cp, av) : av;
             }
           }
         }
