@@ -117,7 +117,8 @@ __device__ __forceinline__ df ld(const float2* p, int64_t i) {
   return {v.x, v.y};
 }
 
-constexpr int kEnergyB = 16;  // consecutive b per unit of the fused energy kernel
+constexpr int kEnergyB = 16;     // consecutive b per unit of the fused energy kernel
+constexpr int kEnergyWarps = 8;  // warps per CTA of the fused energy kernel: one partial each
 
 // One item per CTA.  The item's (a, b, c) are cut into units of four consecutive a (one 32-byte sector of
 // U[b,c,a]), one c and a run of kEnergyB consecutive b, the units spread over the threads with c fastest,
@@ -125,8 +126,8 @@ constexpr int kEnergyB = 16;  // consecutive b per unit of the fused energy kern
 // U[b,c,a] in whole sectors, and every thread carries about the same number of (a, b, c) (a thread that
 // owned all b of its (a, c) left most of the CTA waiting on the longest walk).  Y of Eq. tensort2 is
 // nine products: each T1 factor carries its pair's sign (pairs (ij)k, (ik)j, (jk)i: +, -, +) and the
-// virtual split's (ab|c +, ac|b -, bc|a +).  Double-float arithmetic; the CTA's sum goes to
-// partials[blockIdx.x] in FP64.
+// virtual split's (ab|c +, ac|b -, bc|a +).  Double-float arithmetic; each warp's sum goes to
+// partials[blockIdx.x * kEnergyWarps + warp] in FP64.
 __global__ void __launch_bounds__(256) triples_energy_kernel(const double* __restrict__ U,
                                                              const TriplesItem* __restrict__ items,
                                                              const float2* __restrict__ voo,
@@ -197,25 +198,20 @@ __global__ void __launch_bounds__(256) triples_energy_kernel(const double* __res
       }
     }
   }
-  __shared__ double red[8];
+  // one partial per warp (no CTA-wide barrier: a warp that is done leaves instead of waiting for the
+  // CTA's longest walk); the partials are summed in a fixed order afterwards
   double v = (double)acc.hi + (double)acc.lo;
   v = warp_sum(v);
-  if (threadIdx.x % 32 == 0) red[threadIdx.x / 32] = v;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double s = 0.0;
-    for (int w = 0; w < (int)(blockDim.x / 32); ++w) s += red[w];
-    partials[blockIdx.x] = s;
-  }
+  if (threadIdx.x % 32 == 0) partials[(int64_t)blockIdx.x * kEnergyWarps + threadIdx.x / 32] = v;
 }
 
-// out[t] = sum of partials[seg[t] .. seg[t+1]) in order (one thread per triple).
+// out[t] = sum of the partials of items seg[t] .. seg[t+1] (kEnergyWarps each) in order (one thread per triple).
 __global__ void triples_segment_kernel(const double* __restrict__ partials, const int64_t* __restrict__ seg,
                                        int64_t n, double* __restrict__ out) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= n) return;
   double s = 0.0;
-  for (int64_t i = seg[t]; i < seg[t + 1]; ++i) s += partials[i];
+  for (int64_t i = seg[t] * kEnergyWarps; i < seg[t + 1] * kEnergyWarps; ++i) s += partials[i];
   out[t] = s;
 }
 
@@ -766,7 +762,7 @@ void run_triples(tamm_ctx* ctx, const tamm_tensor* T2, const tamm_tensor* T1, co
   // scratch: U workspace, partials, then (split path) images and exponents
   auto align = [](size_t x) { return (x + 1023) & ~size_t(1023); };
   const size_t ws_bytes = align((size_t)std::max<int64_t>(p->ws_elems, 1) * 8);
-  const size_t part_bytes = align((size_t)std::max<int64_t>(p->n_eitems, 1) * 8);
+  const size_t part_bytes = align((size_t)std::max<int64_t>(p->n_eitems, 1) * kEnergyWarps * 8);
   size_t total = ws_bytes + part_bytes;
   // double-float copies of V_oovv, T1 and the orbital energies (8 bytes per element each)
   const size_t off_dv = total;
@@ -866,10 +862,11 @@ void run_triples(tamm_ctx* ctx, const tamm_tensor* T2, const tamm_tensor* T1, co
                  "triples gemm (split precision)");
     }
     const int64_t e0 = p->eitem_begin[(size_t)bch], e1 = p->eitem_begin[(size_t)bch + 1];
-    cuda_check(launch_triples_energy(ctx, U, p->d_eitems + e0, e1 - e0, dvoo, dt1, deo, dev, partials + e0),
+    cuda_check(launch_triples_energy(ctx, U, p->d_eitems + e0, e1 - e0, dvoo, dt1, deo, dev,
+                                     partials + e0 * kEnergyWarps),
                "triples energy");
   }
-  cuda_check(launch_reduce_final(ctx, partials, p->n_eitems, 1.0, 0, energy), "triples reduction");
+  cuda_check(launch_reduce_final(ctx, partials, p->n_eitems * kEnergyWarps, 1.0, 0, energy), "triples reduction");
   if (triple_energies && !p->triples.empty())
     cuda_check(launch_triples_segments(ctx, partials, p->d_seg, (int64_t)p->triples.size(), triple_energies),
                "triples per-triple sums");
@@ -889,8 +886,8 @@ cudaError_t launch_triples_energy(tamm_ctx* ctx, const double* U, const void* it
                                   double* partials) {
   if (n_items == 0) return cudaSuccess;
   kernel_begin(ctx, TAMM_KERNEL_TRIPLES);
-  triples_energy_kernel<<<(unsigned)n_items, 256, 0, ctx->stream>>>(U, (const TriplesItem*)items, voo, t1, eps_o,
-                                                                      eps_v, partials);
+  triples_energy_kernel<<<(unsigned)n_items, 32 * kEnergyWarps, 0, ctx->stream>>>(U, (const TriplesItem*)items, voo,
+                                                                                  t1, eps_o, eps_v, partials);
   kernel_end(ctx, TAMM_KERNEL_TRIPLES);
   return cudaGetLastError();
 }
