@@ -20,6 +20,10 @@
 //   * all of the above once with each block's own row/column scaling and once
 //     with shared scaling (one exponent per output row and column, so that
 //     short block pairs share accumulation chunks), whose error differs;
+//   * where the contraction qualifies (block pairs of at most 48 summed
+//     indices, output blocks of at most 64 columns), once more with the A
+//     operand sliced inside the GEMM: one chunk per block pair and the
+//     persistent grid, so one timing;
 // and keeps the fastest.  The result is remembered per (tensors, labels) and
 // used by tamm_contract whenever slices = 0.
 #include <algorithm>
@@ -140,7 +144,7 @@ extern "C" tamm_status tamm_autotune(tamm_ctx* ctx, const tamm_tensor* C, const 
       const int n_combos = sh == 2 ? 1 : 2 * (int)(sizeof(kPolicies) / sizeof(kPolicies[0]));
       for (int combo = 0; combo < n_combos; ++combo) {
         const int policy = kPolicies[combo / 2];
-        const bool persistent = combo % 2 == 1;
+        const bool persistent = sh == 2 || combo % 2 == 1;  // the A-slicing GEMM always walks its items
         ctx->oz_tile_policy = policy;
         ctx->oz_persistent = persistent;
         run_contract(ctx, 1.0, &X.t, lc, 0.0, A, la, B, lb, TAMM_PREC_OZAKI_BF16, s_ok);  // builds the plan
