@@ -806,69 +806,6 @@ bool oz_fused_eligible(const ContractLayout& lay) {
   return true;
 }
 
-// Work-item order for the persistent grid, where CTA c of G walks items c, c + G, c + 2G, ...
-// Taken in the plan's order, each round of G consecutive items sends item k to CTA k.  Costs
-// vary: groups differ in their summed range, and a block's last column tile is narrower.  So with
-// a few rounds per CTA, the CTAs that keep drawing the costly items set the launch time.  Here each
-// round keeps its items, which sit next to the items sharing their A row tiles.  The round's items
-// are dealt costliest first to the CTAs with the least work so far.  The CTAs that take an item in
-// the last, partial round are then given the labels the kernel walks there (0 .. m-1).  Cost of an
-// item: its K tiles plus a fixed share for the output stage, times its valid columns rounded up to
-// the MMA's 16.  Every item lands at exactly one position; the kernel sees only a reordered array.
-static std::vector<OzItem> balanced_items(const std::vector<OzItem>& items, const std::vector<OzGroup>& groups,
-                                          const std::vector<OzTask>& tasks, int G) {
-  constexpr int64_t kOutputTiles = 2;  // the output stage, in K tiles of MMA time
-  const int64_t n = (int64_t)items.size();
-  if (G <= 1 || n <= G) return items;
-  std::vector<double> cost((size_t)n);
-  for (int64_t i = 0; i < n; ++i) {
-    const OzItem& it = items[(size_t)i];
-    const OzGroup& g = groups[(size_t)it.group];
-    int64_t kt = 0;
-    for (int32_t t = it.t0; t < it.t1; ++t) kt += tasks[(size_t)t].k_tiles;
-    const int32_t w = std::max(1, std::min(g.n_tile, g.N - it.nt * g.n_tile));
-    cost[(size_t)i] = (double)(kt + kOutputTiles) * (double)((w + 15) / 16 * 16);
-  }
-  std::vector<double> load((size_t)G, 0.0);
-  std::vector<std::vector<int64_t>> walk((size_t)G);
-  std::vector<int> by_cost, by_load((size_t)G);
-  for (int64_t b = 0; b < n; b += G) {
-    const int m = (int)std::min<int64_t>(G, n - b);
-    by_cost.resize((size_t)m);
-    for (int k = 0; k < m; ++k) by_cost[(size_t)k] = k;
-    std::stable_sort(by_cost.begin(), by_cost.end(),
-                     [&](int x, int y) { return cost[(size_t)(b + x)] > cost[(size_t)(b + y)]; });
-    for (int c = 0; c < G; ++c) by_load[(size_t)c] = c;
-    std::stable_sort(by_load.begin(), by_load.end(), [&](int x, int y) { return load[(size_t)x] < load[(size_t)y]; });
-    for (int k = 0; k < m; ++k) {
-      const int c = by_load[(size_t)k];
-      const int64_t i = b + by_cost[(size_t)k];
-      walk[(size_t)c].push_back(i);
-      load[(size_t)c] += cost[(size_t)i];
-    }
-  }
-  // the walks with one item more (those that took part in the last round) take the lowest labels
-  std::vector<int> label((size_t)G);
-  for (int c = 0; c < G; ++c) label[(size_t)c] = c;
-  std::stable_sort(label.begin(), label.end(),
-                   [&](int x, int y) { return walk[(size_t)x].size() > walk[(size_t)y].size(); });
-  std::vector<OzItem> out((size_t)n);
-  std::vector<char> placed((size_t)n, 0);
-  int64_t filled = 0;
-  for (int L = 0; L < G; ++L) {
-    const std::vector<int64_t>& w = walk[(size_t)label[(size_t)L]];
-    for (size_t k = 0; k < w.size(); ++k) {
-      const int64_t pos = (int64_t)k * G + L;
-      if (pos >= n || placed[(size_t)pos]) throw Error(TAMM_EINVAL, "ozaki: work-item balancing is not a permutation");
-      placed[(size_t)pos] = 1;
-      out[(size_t)pos] = items[(size_t)w[k]];
-      ++filled;
-    }
-  }
-  if (filled != n) throw Error(TAMM_EINVAL, "ozaki: work-item balancing is not a permutation");
-  return out;
-}
-
 struct OzakiPlan : Plan {
   ContractLayout lay;
   int S;
@@ -881,7 +818,6 @@ struct OzakiPlan : Plan {
   OzGroup* d_groups = nullptr;
   OzTask* d_tasks = nullptr;
   OzItem* d_items = nullptr;
-  OzItem* d_items_bal = nullptr;  // the same items balanced for a persistent grid of one CTA per SM
   int64_t* d_col_base = nullptr;
   int32_t* d_col_stride = nullptr;
   int64_t n_items = 0;
@@ -1278,10 +1214,6 @@ struct OzakiPlan : Plan {
     d_groups = upload(groups);
     d_tasks = upload(tasks);
     d_items = upload(items);
-    {
-      const int G = (int)std::min<int64_t>(n_items, std::max(1, c->sm_count));
-      d_items_bal = n_items > G && G > 1 ? upload(balanced_items(items, groups, tasks, G)) : d_items;
-    }
     if (!col_base.empty()) {
       d_col_base = upload(col_base);
       d_col_stride = upload(col_stride);
@@ -1368,7 +1300,6 @@ void execute_ozaki(tamm_ctx* ctx, const std::vector<OzOpRecord>& ops) {
   char* scratch = (char*)ctx_scratch(ctx, total);
   std::vector<OzProblem> probs(ops.size());
   std::vector<int64_t> counts(ops.size());
-  std::vector<const OzItem*> balanced(ops.size(), nullptr);
   for (size_t i = 0; i < ops.size(); ++i) {
     const OzakiPlan* p = static_cast<const OzakiPlan*>(ops[i].plan);
     char* s = scratch + base[i];
@@ -1446,7 +1377,6 @@ void execute_ozaki(tamm_ctx* ctx, const std::vector<OzOpRecord>& ops) {
     }
     pr.beta = p->perm_out ? 0.0 : ops[i].beta;
     counts[i] = p->n_items;
-    balanced[i] = p->d_items_bal;
   }
   // one GEMM launch per (slice count, chunk length, grid kind), at most kOzMaxProblems problems each
   std::vector<bool> done(ops.size(), false);
@@ -1463,9 +1393,6 @@ void execute_ozaki(tamm_ctx* ctx, const std::vector<OzOpRecord>& ops) {
       n.push_back(counts[j]);
       done[j] = true;
     }
-    // a contraction alone on the persistent grid walks its items in the balanced order (the grid is
-    // then min(items, SMs) CTAs, the count that order was built for)
-    if (batch.size() == 1 && ops[i].persistent && balanced[i]) batch[0].items = balanced[i];
     cuda_check(launch_ozaki_gemm(ctx, batch.data(), n.data(), (int)batch.size(), ops[i].slices,
                                  ops[i].chunk_k / kOzTileK, ops[i].persistent),
                "ozaki gemm");
