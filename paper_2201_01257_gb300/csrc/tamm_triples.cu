@@ -14,7 +14,7 @@
 // split-precision tcgen05 kernel whose operand images are sliced once per evaluation.  U exists only
 // for one batch of triples (a workspace of bounded size); the fused kernel below then forms W, Y and
 // the denominators for every a<b<c of every spin-allowed tile triple and reduces (W + Y) W / D to one
-// partial per work item; the partials are summed in a fixed order.
+// FP64 partial per warp of each work item; the partials are summed in a fixed order.
 #include <algorithm>
 #include <array>
 #include <cstring>
