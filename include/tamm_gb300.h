@@ -439,8 +439,9 @@ TAMM_API tamm_status tamm_fp64_peak(tamm_ctx* ctx, int kind, double* tflops);
  * context and used by every later tamm_contract of the same tensors and
  * labels with precision TAMM_PREC_OZAKI_BF16 and slices = 0.  Outputs (each
  * may be NULL): the slice count, the chunk length, the tile policy, the grid
- * kind (1 = persistent), the scaling mode (0 = per block, 1 = shared, 2 = per block
- * with A sliced inside the GEMM), the measured error and the
+ * kind (1 = persistent; always 1 in mode 2, whose GEMM walks its items), the
+ * scaling mode (0 = per block, 1 = shared, 2 = per block with A sliced inside
+ * the GEMM, timed once where the contraction qualifies), the measured error and the
  * mean time in ms of the chosen configuration.  Tune
  * on representative operands: a zero product is refused (TAMM_EINVAL).  Synchronises.  Errors: TAMM_EINVAL, TAMM_ENOMEM,
  * TAMM_ECUDA, TAMM_EUNSUPPORTED (no candidate reaches the target). */
